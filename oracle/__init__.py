@@ -1,0 +1,342 @@
+"""Plain FP64 CPU oracle for 4D space-time box screening (Bak & Hobbs,
+"Efficient n-to-n Collision Detection for Space Debris using 4D AABB Trees").
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA library: the C part (``oracle.c``) is compiled by ``build()``
+below with gcc and driven through ctypes; the step-network part is numpy.
+
+Element arrays are float64 with shape (n, 7): a [km], e, i, RAAN, argument of
+perigee, mean anomaly at t=0 [rad], radius [km].  Time is integer ticks.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "lib", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CELL_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("tlo", "<i4"), ("thi", "<i4")])
+WITNESS_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("t", "<i4")])
+
+STEP_FIXED, STEP_PERIOD_FRACTION, STEP_BAND_TABLE = 0, 1, 2
+BOX_SPEED, BOX_INTERVAL = 0, 1
+MU = 398600.4418
+RE = 6378.137
+EPS_KM = 1e-6
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into lib/liboracle.so (gcc, FP contraction off so
+    that a*b+c is never fused: the same decisions on x86 and Arm)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(src),
+                                                   os.path.getmtime(os.path.join(_HERE, "oracle.h")))):
+        return _LIB_PATH
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-o", tmp, src, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB_PATH)
+            d, i64, i32, vp = ctypes.c_double, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p
+            sig = {
+                "or_mean_motion": (d, [vp]), "or_period": (d, [vp]), "or_max_speed": (d, [vp]),
+                "or_solve_kepler": (d, [d, d, vp]),
+                "or_true_anomaly": (d, [vp, d]),
+                "or_position": (None, [vp, d, vp]),
+                "or_position_from_nu": (None, [vp, d, vp]),
+                "or_velocity_fd": (None, [vp, d, d, vp]),
+                "or_nu_rk4": (d, [vp, d, d]),
+                "or_step_ticks": (i64, [vp, i32, i64, d, vp, vp, i32, d]),
+                "or_iv_add": (None, [vp, vp, vp]), "or_iv_mul": (None, [vp, vp, vp]),
+                "or_iv_scale": (None, [d, vp, vp]),
+                "or_iv_cos": (None, [vp, vp]), "or_iv_sin": (None, [vp, vp]),
+                "or_box": (None, [vp, i32, i64, i64, d, vp, vp, vp, vp]),
+                "or_boxes": (i64, [vp, i64, i64, d, vp, i32, vp, vp, vp, i64]),
+                "or_raw_cells_bruteforce": (i64, [vp, vp, vp, i64, vp, i64]),
+                "or_raw_cells_sweep": (i64, [vp, vp, vp, i64, vp, i64]),
+                "or_raw_cells_selected": (i64, [vp, vp, vp, i64, vp, vp, i64]),
+                "or_canonicalize": (i64, [vp, i64]),
+                "or_alg1_witnesses": (i64, [vp, i64, i64, d, vp, i64]),
+                "or_alg3": (i32, [vp, i64, i64, d, i32, i64, vp, vp, vp, vp]),
+                "or_radial_range": (None, [vp, vp]),
+                "or_band_edges": (None, [vp, i64, i32, vp]),
+                "or_band_counts": (None, [vp, i64, i32, vp]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _els(els) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(els, dtype=np.float64))
+    if a.ndim == 1:
+        a = a.reshape(1, 7)
+    assert a.shape[1] == 7
+    return a
+
+
+# --- dynamics (Sec. 6.1, Eq. 1) -------------------------------------------
+
+def mean_motion(el) -> float:
+    return lib().or_mean_motion(_p(_els(el)))
+
+
+def period(el) -> float:
+    return lib().or_period(_p(_els(el)))
+
+
+def max_speed(el) -> float:
+    return lib().or_max_speed(_p(_els(el)))
+
+
+def solve_kepler(M: float, e: float):
+    it = ctypes.c_int(0)
+    E = lib().or_solve_kepler(M, e, ctypes.byref(it))
+    return E, it.value
+
+
+def true_anomaly(el, t_s: float) -> float:
+    return lib().or_true_anomaly(_p(_els(el)), float(t_s))
+
+
+def position(el, t_s: float) -> np.ndarray:
+    out = np.zeros(3)
+    lib().or_position(_p(_els(el)), float(t_s), _p(out))
+    return out
+
+
+def position_from_nu(el, nu: float) -> np.ndarray:
+    out = np.zeros(3)
+    lib().or_position_from_nu(_p(_els(el)), float(nu), _p(out))
+    return out
+
+
+def positions(els, obj_idx, t_s) -> np.ndarray:
+    """FP64 positions of objects obj_idx[q] at times t_s[q] (seconds)."""
+    E = _els(els)
+    obj_idx = np.asarray(obj_idx)
+    t_s = np.asarray(t_s, dtype=np.float64)
+    out = np.zeros((len(obj_idx), 3))
+    L = lib()
+    tmp = np.zeros(3)
+    for q in range(len(obj_idx)):
+        L.or_position(_p(E[int(obj_idx[q])]), float(t_s[q]), _p(tmp))
+        out[q] = tmp
+    return out
+
+
+def velocity_fd(el, t_s: float, h_s: float = 1e-3) -> np.ndarray:
+    out = np.zeros(3)
+    lib().or_velocity_fd(_p(_els(el)), float(t_s), float(h_s), _p(out))
+    return out
+
+
+def nu_rk4(el, t_s: float, h_s: float) -> float:
+    return lib().or_nu_rk4(_p(_els(el)), float(t_s), float(h_s))
+
+
+# --- step policy -----------------------------------------------------------
+
+def step_ticks(els, kind: int, tick_s: float, fixed_ticks: int = 1, frac: float = 100.0,
+               band_edges_km=(), band_fracs=(100.0,)) -> np.ndarray:
+    E = _els(els)
+    be = np.ascontiguousarray(np.asarray(band_edges_km, dtype=np.float64).reshape(-1))
+    bf = np.ascontiguousarray(np.asarray(band_fracs, dtype=np.float64).reshape(-1))
+    if be.size == 0:
+        be = np.zeros(1)
+    L = lib()
+    return np.array([L.or_step_ticks(_p(E[i]), kind, int(fixed_ticks), float(frac), _p(be), _p(bf),
+                                     int(len(bf)), float(tick_s)) for i in range(len(E))],
+                    dtype=np.int64)
+
+
+# --- interval arithmetic (Sec. 4.5) -----------------------------------------
+
+def _iv2(fn, *args):
+    out = np.zeros(2)
+    keep, conv = [], []  # arrays stay referenced until the call returns
+    for a in args:
+        if isinstance(a, (list, tuple, np.ndarray)):
+            keep.append(np.ascontiguousarray(a, dtype=np.float64))
+            conv.append(_p(keep[-1]))
+        else:
+            conv.append(float(a))
+    fn(*conv, _p(out))
+    return out
+
+
+def iv_add(a, b):
+    return _iv2(lib().or_iv_add, a, b)
+
+
+def iv_mul(a, b):
+    return _iv2(lib().or_iv_mul, a, b)
+
+
+def iv_scale(k, a):
+    return _iv2(lib().or_iv_scale, k, a)
+
+
+def iv_cos(x):
+    return _iv2(lib().or_iv_cos, x)
+
+
+def iv_sin(x):
+    return _iv2(lib().or_iv_sin, x)
+
+
+# --- boxes (Defs 7-8) ------------------------------------------------------
+
+def box(el, mode: int, tlo: int, thi: int, tick_s: float):
+    lo = np.zeros(4, np.float32)
+    hi = np.zeros(4, np.float32)
+    c = np.zeros(3)
+    hw = np.zeros(1)
+    lib().or_box(_p(_els(el)), mode, int(tlo), int(thi), float(tick_s), _p(lo), _p(hi), _p(c), _p(hw))
+    return lo, hi, c, float(hw[0])
+
+
+def boxes(els, T: int, tick_s: float, k, mode: int = BOX_SPEED):
+    """All boxes, object-major then segment order: (lo4, hi4, obj)."""
+    E = _els(els)
+    k = np.ascontiguousarray(np.asarray(k, dtype=np.int64))
+    N = int(np.sum((T + 1 + k - 1) // k))
+    lo = np.zeros((N, 4), np.float32)
+    hi = np.zeros((N, 4), np.float32)
+    obj = np.zeros(N, np.uint32)
+    got = lib().or_boxes(_p(E), len(E), int(T), float(tick_s), _p(k), mode, _p(lo), _p(hi), _p(obj), N)
+    assert got == N
+    return lo, hi, obj
+
+
+# --- pair sets -------------------------------------------------------------
+
+def _cells_call(fn, *args):
+    cap = 1 << 16
+    while True:
+        out = np.zeros(cap, CELL_DTYPE)
+        n = fn(*args, _p(out), cap)
+        if n <= cap:
+            return out[:n].copy()
+        cap = int(n)
+
+
+def raw_cells_bruteforce(lo4, hi4, obj):
+    lo4 = np.ascontiguousarray(lo4, np.float32)
+    hi4 = np.ascontiguousarray(hi4, np.float32)
+    obj = np.ascontiguousarray(obj, np.uint32)
+    return _cells_call(lib().or_raw_cells_bruteforce, _p(lo4), _p(hi4), _p(obj), len(obj))
+
+
+def raw_cells_sweep(lo4, hi4, obj):
+    lo4 = np.ascontiguousarray(lo4, np.float32)
+    hi4 = np.ascontiguousarray(hi4, np.float32)
+    obj = np.ascontiguousarray(obj, np.uint32)
+    return _cells_call(lib().or_raw_cells_sweep, _p(lo4), _p(hi4), _p(obj), len(obj))
+
+
+def raw_cells_selected(lo4, hi4, obj, sel):
+    lo4 = np.ascontiguousarray(lo4, np.float32)
+    hi4 = np.ascontiguousarray(hi4, np.float32)
+    obj = np.ascontiguousarray(obj, np.uint32)
+    sel = np.ascontiguousarray(sel, np.uint8)
+    return _cells_call(lib().or_raw_cells_selected, _p(lo4), _p(hi4), _p(obj), len(obj), _p(sel))
+
+
+def canonicalize(cells) -> np.ndarray:
+    c = np.ascontiguousarray(np.array(cells, dtype=CELL_DTYPE, copy=True))
+    n = lib().or_canonicalize(_p(c), len(c))
+    return c[:n].copy()
+
+
+def screen(els, T: int, tick_s: float, k, mode: int = BOX_SPEED):
+    """The whole method on the CPU: boxes, every overlapping box pair, then
+    the canonical sorted and merged list."""
+    lo, hi, obj = boxes(els, T, tick_s, k, mode)
+    return canonicalize(raw_cells_sweep(lo, hi, obj))
+
+
+# --- the paper's algorithms ------------------------------------------------
+
+def alg1_witnesses(els, T: int, tick_s: float) -> np.ndarray:
+    E = _els(els)
+    return _cells_call_w(lib().or_alg1_witnesses, _p(E), len(E), int(T), float(tick_s))
+
+
+def _cells_call_w(fn, *args):
+    cap = 1 << 12
+    while True:
+        out = np.zeros(cap, WITNESS_DTYPE)
+        n = fn(*args, _p(out), cap)
+        if n <= cap:
+            return out[:n].copy()
+        cap = int(n)
+
+
+def alg3(els, T: int, tick_s: float, mode: int = BOX_SPEED, t_first: int = -1):
+    """Serial Alg 3.  Returns (rc, (i, j, t) or None, iterations)."""
+    E = _els(els)
+    wi, wj = ctypes.c_uint32(0), ctypes.c_uint32(0)
+    wt, it = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = lib().or_alg3(_p(E), len(E), int(T), float(tick_s), mode, int(t_first), ctypes.byref(wi),
+                       ctypes.byref(wj), ctypes.byref(wt), ctypes.byref(it))
+    w = (wi.value, wj.value, wt.value) if rc == 1 else None
+    return rc, w, it.value
+
+
+# --- decomposition (Sec. 5, Sec. 6.1) ----------------------------------------
+
+def radial_range(el) -> np.ndarray:
+    out = np.zeros(2)
+    lib().or_radial_range(_p(_els(el)), _p(out))
+    return out
+
+
+def band_edges(els, p: int) -> np.ndarray:
+    E = _els(els)
+    out = np.zeros(max(p - 1, 1))
+    lib().or_band_edges(_p(E), len(E), int(p), _p(out))
+    return out[:p - 1]
+
+
+def band_counts(els, p: int) -> np.ndarray:
+    E = _els(els)
+    out = np.zeros(p, np.int64)
+    lib().or_band_counts(_p(E), len(E), int(p), _p(out))
+    return out
+
+
+def potential_collision_filter(els, cells) -> np.ndarray:
+    """Keep the cells whose objects share an edge of the potential-collision
+    graph (Def 9): padded radial ranges that intersect."""
+    E = _els(els)
+    rr = np.array([radial_range(E[i]) for i in range(len(E))])
+    i = cells["i"].astype(np.int64)
+    j = cells["j"].astype(np.int64)
+    keep = np.maximum(rr[i, 0], rr[j, 0]) <= np.minimum(rr[i, 1], rr[j, 1])
+    return cells[keep]

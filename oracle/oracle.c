@@ -1,0 +1,639 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle for 4D space-time box screening.
+ *
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).  Slow on purpose: every routine is
+ * the textbook or paper form of what it computes, with no blocking, fusion or
+ * reordering, so that it can be read against the paper.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define TWO_PI 6.283185307179586
+#define PI 3.141592653589793
+
+/* ------------------------------------------------------------------------ */
+/* Dynamics: Sec. 6.1.  Eq. 1 gives nu-dot; its solution nu(t) is obtained  */
+/* through Kepler's equation (mean anomaly M = M0 + n t, eccentric anomaly  */
+/* E with E - e sin E = M, then nu from E).  Three rotations (argument of   */
+/* perigee, inclination, RAAN) take the perifocal point to ECI.             */
+/* ------------------------------------------------------------------------ */
+
+double or_mean_motion(const double *el) {
+  double a = el[0];
+  return sqrt(OR_MU / (a * a * a));
+}
+
+double or_period(const double *el) {
+  /* P = 2 pi sqrt(a^3 / mu), evaluated in this fixed order so that the
+   * integer step count floor(P / (f dt)) is reproducible. */
+  double a = el[0];
+  double a3 = a * a * a;
+  return TWO_PI * sqrt(a3 / OR_MU);
+}
+
+double or_max_speed(const double *el) {
+  /* vis-viva at perigee r = a(1-e): v^2 = mu (2/r - 1/a) = mu/a (1+e)/(1-e) */
+  double a = el[0], e = el[1];
+  return sqrt(OR_MU / a * (1.0 + e) / (1.0 - e));
+}
+
+static double kepler_f(double E, double e, double M) { return E - e * sin(E) - M; }
+
+double or_solve_kepler(double M, double e, int *iters) {
+  /* Kepler's equation E - e sin E = M for M in any range.  f(E) is strictly
+   * increasing (f' = 1 - e cos E > 0 for e < 1) and f(M-e) <= 0 <= f(M+e),
+   * so bisection on [M-e, M+e] always brackets the root; Newton steps then
+   * polish it to the last bit. */
+  double lo = M - e, hi = M + e;
+  int it = 0;
+  if (e == 0.0) {
+    if (iters) *iters = 0;
+    return M;
+  }
+  for (; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (kepler_f(mid, e, M) > 0.0) hi = mid; else lo = mid;
+  }
+  double E = 0.5 * (lo + hi);
+  for (int k = 0; k < 3; ++k) {
+    double d = kepler_f(E, e, M) / (1.0 - e * cos(E));
+    E -= d;
+    ++it;
+  }
+  if (iters) *iters = it;
+  return E;
+}
+
+double or_true_anomaly(const double *el, double t_s) {
+  /* nu(t): the closed-form solution of Eq. 1.  Continuous in t (no wrap). */
+  double e = el[1];
+  double M = el[5] + or_mean_motion(el) * t_s;
+  double E = or_solve_kepler(M, e, NULL);
+  /* tan(nu/2) = sqrt((1+e)/(1-e)) tan(E/2), on the branch of E */
+  double half = atan2(sqrt(1.0 + e) * sin(0.5 * E), sqrt(1.0 - e) * cos(0.5 * E));
+  double nu = 2.0 * half;
+  /* put nu on the same revolution as E */
+  double k = floor((E - nu) / TWO_PI + 0.5);
+  return nu + k * TWO_PI;
+}
+
+static void rot_z(double th, const double v[3], double out[3]) {
+  double c = cos(th), s = sin(th);
+  double x = v[0] * c - v[1] * s;
+  double y = v[0] * s + v[1] * c;
+  out[0] = x; out[1] = y; out[2] = v[2];
+}
+
+static void rot_x(double th, const double v[3], double out[3]) {
+  double c = cos(th), s = sin(th);
+  double y = v[1] * c - v[2] * s;
+  double z = v[1] * s + v[2] * c;
+  out[0] = v[0]; out[1] = y; out[2] = z;
+}
+
+/* perifocal -> ECI: rotate by the argument of perigee about z, by the
+ * inclination about x, then by the RAAN about z (Sec. 6.1). */
+static void perifocal_to_eci(const double *el, const double pf[3], double out[3]) {
+  double t1[3], t2[3];
+  rot_z(el[4], pf, t1);
+  rot_x(el[2], t1, t2);
+  rot_z(el[3], t2, out);
+}
+
+void or_position_from_nu(const double *el, double nu, double out[3]) {
+  double a = el[0], e = el[1];
+  double p = a * (1.0 - e * e);
+  double r = p / (1.0 + e * cos(nu));
+  double pf[3] = {r * cos(nu), r * sin(nu), 0.0};
+  perifocal_to_eci(el, pf, out);
+}
+
+void or_position(const double *el, double t_s, double out[3]) {
+  or_position_from_nu(el, or_true_anomaly(el, t_s), out);
+}
+
+void or_velocity_fd(const double *el, double t_s, double h_s, double out[3]) {
+  double p1[3], p0[3];
+  or_position(el, t_s + h_s, p1);
+  or_position(el, t_s - h_s, p0);
+  for (int k = 0; k < 3; ++k) out[k] = (p1[k] - p0[k]) / (2.0 * h_s);
+}
+
+static double nu_dot(const double *el, double nu) {
+  /* Eq. 1: nu' = sqrt(mu / (a(1-e^2))^3) (1 + e cos nu)^2 */
+  double a = el[0], e = el[1];
+  double p = a * (1.0 - e * e);
+  double q = 1.0 + e * cos(nu);
+  return sqrt(OR_MU / (p * p * p)) * q * q;
+}
+
+double or_nu_rk4(const double *el, double t_s, double h_s) {
+  /* classical Runge-Kutta integration of Eq. 1 from nu(0) to nu(t) */
+  double nu = or_true_anomaly(el, 0.0);
+  int64_t steps = (int64_t)ceil(fabs(t_s) / h_s);
+  if (steps == 0) return nu;
+  double h = t_s / (double)steps;
+  for (int64_t s = 0; s < steps; ++s) {
+    double k1 = nu_dot(el, nu);
+    double k2 = nu_dot(el, nu + 0.5 * h * k1);
+    double k3 = nu_dot(el, nu + 0.5 * h * k2);
+    double k4 = nu_dot(el, nu + h * k3);
+    nu += h / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+  }
+  return nu;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-object time step (Sec. 4.3: time is tracked per object).            */
+/* ------------------------------------------------------------------------ */
+
+int64_t or_step_ticks(const double *el, int kind, int64_t fixed_ticks,
+                      double frac, const double *band_edges_km,
+                      const double *band_fracs, int n_bands, double tick_s) {
+  if (kind == OR_STEP_FIXED) return fixed_ticks < 1 ? 1 : fixed_ticks;
+  double f = frac;
+  if (kind == OR_STEP_BAND_TABLE) {
+    /* bands over perigee altitude a(1-e) - R_E; n_bands-1 ascending edges */
+    double hp = el[0] * (1.0 - el[1]) - OR_RE;
+    int b = 0;
+    while (b < n_bands - 1 && hp >= band_edges_km[b]) ++b;
+    f = band_fracs[b];
+  }
+  double P = or_period(el);
+  double k = floor(P / (f * tick_s));
+  return k < 1.0 ? 1 : (int64_t)k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Interval arithmetic (Sec. 4.5).  Closed intervals [lo, hi].             */
+/* ------------------------------------------------------------------------ */
+
+void or_iv_add(const double a[2], const double b[2], double out[2]) {
+  out[0] = a[0] + b[0];
+  out[1] = a[1] + b[1];
+}
+
+void or_iv_mul(const double a[2], const double b[2], double out[2]) {
+  double p[4] = {a[0] * b[0], a[0] * b[1], a[1] * b[0], a[1] * b[1]};
+  double lo = p[0], hi = p[0];
+  for (int k = 1; k < 4; ++k) {
+    if (p[k] < lo) lo = p[k];
+    if (p[k] > hi) hi = p[k];
+  }
+  out[0] = lo;
+  out[1] = hi;
+}
+
+void or_iv_scale(double k, const double a[2], double out[2]) {
+  double x = k * a[0], y = k * a[1];
+  out[0] = x < y ? x : y;
+  out[1] = x < y ? y : x;
+}
+
+/* exact range of cos over [x0, x1]: the end values, widened to +-1 wherever
+ * the interval contains a multiple of 2 pi (max) or an odd multiple of pi
+ * (min). */
+void or_iv_cos(const double x[2], double out[2]) {
+  double c0 = cos(x[0]), c1 = cos(x[1]);
+  double lo = c0 < c1 ? c0 : c1, hi = c0 < c1 ? c1 : c0;
+  if (x[1] - x[0] >= TWO_PI) { out[0] = -1.0; out[1] = 1.0; return; }
+  /* smallest multiple of pi that is >= x0 */
+  double m = ceil(x[0] / PI);
+  for (double k = m; k * PI <= x[1]; k += 1.0) {
+    long kk = (long)k;
+    if (kk % 2 == 0) hi = 1.0; else lo = -1.0;
+  }
+  out[0] = lo;
+  out[1] = hi;
+}
+
+void or_iv_sin(const double x[2], double out[2]) {
+  /* sin x = cos(x - pi/2) */
+  double y[2] = {x[0] - 0.5 * PI, x[1] - 0.5 * PI};
+  or_iv_cos(y, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Interval occupancy region (Def 7) and 4D occupancy region (Def 8).      */
+/* ------------------------------------------------------------------------ */
+
+static float to_float_down(double x) {
+  float f = (float)x;
+  if ((double)f > x) f = nextafterf(f, -INFINITY);
+  return f;
+}
+
+static float to_float_up(double x) {
+  float f = (float)x;
+  if ((double)f < x) f = nextafterf(f, INFINITY);
+  return f;
+}
+
+static double eccentric_anomaly_at(const double *el, double t_s) {
+  double M = el[5] + or_mean_motion(el) * t_s;
+  return or_solve_kepler(M, el[1], NULL);
+}
+
+void or_box(const double *el, int mode, int64_t tlo, int64_t thi,
+            double tick_s, float lo4[4], float hi4[4], double c_out[3],
+            double *hw_out) {
+  double r = el[6];
+  double lo[3], hi[3];
+  if (mode == OR_BOX_SPEED) {
+    /* Every point of the arc over [t0, t1] lies within vmax |t - tc| of the
+     * midpoint position (speed never exceeds the perigee speed), and the
+     * 2-norm bounds the infinity norm, so the cube of half-width
+     * r + vmax (t1 - t0)/2 around pos(tc) contains occ(w, t) for all t. */
+    double tc = 0.5 * (double)(tlo + thi) * tick_s;
+    double c[3];
+    or_position(el, tc, c);
+    double hw = r + or_max_speed(el) * (double)(thi - tlo) * tick_s * 0.5 + OR_EPS_KM;
+    for (int k = 0; k < 3; ++k) { lo[k] = c[k] - hw; hi[k] = c[k] + hw; }
+    if (c_out) { c_out[0] = c[0]; c_out[1] = c[1]; c_out[2] = c[2]; }
+    if (hw_out) *hw_out = hw;
+  } else {
+    /* Sec. 4.5: the single orbital variable is monotone in time, so its
+     * values at the two ends bound it over the interval; the position is
+     * then bounded by interval evaluation of
+     *   pos(E) = a (cos E - e) P + a sqrt(1-e^2) sin E Q,
+     * P and Q the perifocal unit axes in ECI. */
+    double a = el[0], e = el[1];
+    double E[2] = {eccentric_anomaly_at(el, (double)tlo * tick_s),
+                   eccentric_anomaly_at(el, (double)thi * tick_s)};
+    double cE[2], sE[2];
+    or_iv_cos(E, cE);
+    or_iv_sin(E, sE);
+    double ux[3] = {1.0, 0.0, 0.0}, uy[3] = {0.0, 1.0, 0.0};
+    double P[3], Q[3];
+    perifocal_to_eci(el, ux, P);
+    perifocal_to_eci(el, uy, Q);
+    double b = a * sqrt(1.0 - e * e);
+    double cm[2] = {cE[0] - e, cE[1] - e};
+    for (int k = 0; k < 3; ++k) {
+      double t1[2], t2[2], s[2];
+      or_iv_scale(a * P[k], cm, t1);
+      or_iv_scale(b * Q[k], sE, t2);
+      or_iv_add(t1, t2, s);
+      lo[k] = s[0] - r - OR_EPS_KM;
+      hi[k] = s[1] + r + OR_EPS_KM;
+    }
+    if (c_out) or_position(el, (double)tlo * tick_s, c_out);
+    if (hw_out) *hw_out = NAN;
+  }
+  for (int k = 0; k < 3; ++k) {
+    lo4[k] = to_float_down(lo[k]);
+    hi4[k] = to_float_up(hi[k]);
+  }
+  lo4[3] = (float)tlo;
+  hi4[3] = (float)thi;
+}
+
+int64_t or_boxes(const double *els, int64_t n, int64_t T, double tick_s,
+                 const int64_t *k, int mode, float *lo4, float *hi4,
+                 uint32_t *obj, int64_t cap) {
+  int64_t N = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t ki = k[i];
+    int64_t S = (T + 1 + ki - 1) / ki;
+    for (int64_t m = 0; m < S; ++m) {
+      if (N < cap) {
+        int64_t tlo = m * ki;
+        int64_t thi = (m + 1) * ki - 1;
+        if (thi > T) thi = T;
+        or_box(els + 7 * i, mode, tlo, thi, tick_s, lo4 + 4 * N, hi4 + 4 * N, NULL, NULL);
+        obj[N] = (uint32_t)i;
+      }
+      ++N;
+    }
+  }
+  return N;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pair sets.                                                               */
+/* ------------------------------------------------------------------------ */
+
+static int boxes_overlap(const float *la, const float *ha, const float *lb, const float *hb) {
+  /* closed boxes (Def 2 uses <=) overlap iff they overlap on every axis */
+  for (int k = 0; k < 4; ++k)
+    if (!(la[k] <= hb[k] && lb[k] <= ha[k])) return 0;
+  return 1;
+}
+
+static void make_cell(const float *lo4, const float *hi4, const uint32_t *obj,
+                      int64_t a, int64_t b, or_cell *c) {
+  uint32_t oa = obj[a], ob = obj[b];
+  c->i = oa < ob ? oa : ob;
+  c->j = oa < ob ? ob : oa;
+  int32_t ta0 = (int32_t)lo4[4 * a + 3], ta1 = (int32_t)hi4[4 * a + 3];
+  int32_t tb0 = (int32_t)lo4[4 * b + 3], tb1 = (int32_t)hi4[4 * b + 3];
+  c->tlo = ta0 > tb0 ? ta0 : tb0;
+  c->thi = ta1 < tb1 ? ta1 : tb1;
+}
+
+int64_t or_raw_cells_bruteforce(const float *lo4, const float *hi4,
+                                const uint32_t *obj, int64_t N,
+                                or_cell *out, int64_t cap) {
+  int64_t c = 0;
+  for (int64_t a = 0; a < N; ++a)
+    for (int64_t b = a + 1; b < N; ++b) {
+      if (obj[a] == obj[b]) continue;
+      if (!boxes_overlap(lo4 + 4 * a, hi4 + 4 * a, lo4 + 4 * b, hi4 + 4 * b)) continue;
+      if (c < cap) make_cell(lo4, hi4, obj, a, b, out + c);
+      ++c;
+    }
+  return c;
+}
+
+static const float *g_sort_lo;
+static int cmp_by_tlo(const void *x, const void *y) {
+  int64_t a = *(const int64_t *)x, b = *(const int64_t *)y;
+  float ta = g_sort_lo[4 * a + 3], tb = g_sort_lo[4 * b + 3];
+  if (ta < tb) return -1;
+  if (ta > tb) return 1;
+  return (a > b) - (a < b);
+}
+
+static int64_t *sorted_by_tlo(const float *lo4, int64_t N) {
+  int64_t *ord = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+  for (int64_t a = 0; a < N; ++a) ord[a] = a;
+  g_sort_lo = lo4;
+  qsort(ord, (size_t)N, sizeof(int64_t), cmp_by_tlo);
+  return ord;
+}
+
+int64_t or_raw_cells_sweep(const float *lo4, const float *hi4,
+                           const uint32_t *obj, int64_t N,
+                           or_cell *out, int64_t cap) {
+  int64_t *ord = sorted_by_tlo(lo4, N);
+  int64_t c = 0;
+  for (int64_t p = 0; p < N; ++p) {
+    int64_t a = ord[p];
+    float tend = hi4[4 * a + 3];
+    for (int64_t q = p + 1; q < N && lo4[4 * ord[q] + 3] <= tend; ++q) {
+      int64_t b = ord[q];
+      if (obj[a] == obj[b]) continue;
+      if (!boxes_overlap(lo4 + 4 * a, hi4 + 4 * a, lo4 + 4 * b, hi4 + 4 * b)) continue;
+      if (c < cap) make_cell(lo4, hi4, obj, a, b, out + c);
+      ++c;
+    }
+  }
+  free(ord);
+  return c;
+}
+
+int64_t or_raw_cells_selected(const float *lo4, const float *hi4,
+                              const uint32_t *obj, int64_t N,
+                              const uint8_t *sel, or_cell *out, int64_t cap) {
+  int64_t *ord = sorted_by_tlo(lo4, N);
+  /* longest box in ticks: a box b can meet box a only if
+   * tlo_b in [tlo_a - maxlen, thi_a] */
+  float maxlen = 0.0f;
+  for (int64_t a = 0; a < N; ++a) {
+    float L = hi4[4 * a + 3] - lo4[4 * a + 3];
+    if (L > maxlen) maxlen = L;
+  }
+  int64_t c = 0;
+  for (int64_t a = 0; a < N; ++a) {
+    if (!sel[obj[a]]) continue;
+    float t0 = lo4[4 * a + 3] - maxlen, t1 = hi4[4 * a + 3];
+    /* first sorted position with tlo >= t0 */
+    int64_t lo = 0, hi = N;
+    while (lo < hi) {
+      int64_t mid = (lo + hi) / 2;
+      if (lo4[4 * ord[mid] + 3] < t0) lo = mid + 1; else hi = mid;
+    }
+    for (int64_t q = lo; q < N && lo4[4 * ord[q] + 3] <= t1; ++q) {
+      int64_t b = ord[q];
+      if (obj[a] == obj[b]) continue;
+      if (sel[obj[b]] && b < a) continue; /* counted from b's side */
+      if (!boxes_overlap(lo4 + 4 * a, hi4 + 4 * a, lo4 + 4 * b, hi4 + 4 * b)) continue;
+      if (c < cap) make_cell(lo4, hi4, obj, a, b, out + c);
+      ++c;
+    }
+  }
+  free(ord);
+  return c;
+}
+
+static int cmp_cell(const void *x, const void *y) {
+  const or_cell *a = (const or_cell *)x, *b = (const or_cell *)y;
+  if (a->i != b->i) return a->i < b->i ? -1 : 1;
+  if (a->j != b->j) return a->j < b->j ? -1 : 1;
+  if (a->tlo != b->tlo) return a->tlo < b->tlo ? -1 : 1;
+  if (a->thi != b->thi) return a->thi < b->thi ? -1 : 1;
+  return 0;
+}
+
+int64_t or_canonicalize(or_cell *cells, int64_t n) {
+  if (n <= 0) return 0;
+  qsort(cells, (size_t)n, sizeof(or_cell), cmp_cell);
+  int64_t w = 0;
+  for (int64_t r = 1; r < n; ++r) {
+    or_cell *cur = cells + w;
+    const or_cell *nx = cells + r;
+    if (nx->i == cur->i && nx->j == cur->j && (int64_t)nx->tlo <= (int64_t)cur->thi + 1) {
+      if (nx->thi > cur->thi) cur->thi = nx->thi;
+    } else {
+      cells[++w] = *nx;
+    }
+  }
+  return w + 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg 1: brute force over every tick and every pair.                      */
+/* ------------------------------------------------------------------------ */
+
+static int occ_collide(const double *pi, double ri, const double *pj, double rj) {
+  /* Def 3 with Def 2: two closed cubes meet iff their centres are within
+   * r_i + r_j in the infinity norm */
+  for (int k = 0; k < 3; ++k)
+    if (fabs(pi[k] - pj[k]) > ri + rj) return 0;
+  return 1;
+}
+
+int64_t or_alg1_witnesses(const double *els, int64_t n, int64_t T,
+                          double tick_s, or_witness *out, int64_t cap) {
+  double *pos = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  int64_t c = 0;
+  for (int64_t t = 0; t <= T; ++t) {
+    for (int64_t i = 0; i < n; ++i) or_position(els + 7 * i, (double)t * tick_s, pos + 3 * i);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = i + 1; j < n; ++j)
+        if (occ_collide(pos + 3 * i, els[7 * i + 6], pos + 3 * j, els[7 * j + 6])) {
+          if (c < cap) {
+            out[c].i = (uint32_t)i;
+            out[c].j = (uint32_t)j;
+            out[c].t = (int32_t)t;
+          }
+          ++c;
+        }
+  }
+  free(pos);
+  return c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alg 3 with Alg 4 (initializeTree), getSmallestMaxTimeObject, Alg 5      */
+/* (advanceTime) and Alg 6 (resolveCollisions).  The AABB tree's job is to  */
+/* answer "which boxes meet this box"; a flat list answers the same query. */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  const double *els;
+  int64_t n;
+  double tick_s;
+  int mode;
+  int64_t *tmin, *tmax;
+  float *lo, *hi; /* current occ-4d box of each object */
+} alg3_state;
+
+static void a3_update(alg3_state *s, int64_t w) {
+  or_box(s->els + 7 * w, s->mode, s->tmin[w], s->tmax[w], s->tick_s,
+         s->lo + 4 * w, s->hi + 4 * w, NULL, NULL);
+}
+
+static int a3_meet(const alg3_state *s, int64_t a, int64_t b) {
+  return boxes_overlap(s->lo + 4 * a, s->hi + 4 * a, s->lo + 4 * b, s->hi + 4 * b);
+}
+
+/* queryObject: all objects whose box meets v's box, v excluded */
+static int64_t a3_query(const alg3_state *s, int64_t v, int64_t *out) {
+  int64_t c = 0;
+  for (int64_t y = 0; y < s->n; ++y)
+    if (y != v && a3_meet(s, v, y)) out[c++] = y;
+  return c;
+}
+
+int or_alg3(const double *els, int64_t n, int64_t T, double tick_s, int mode,
+            int64_t t_first, uint32_t *wi, uint32_t *wj, int64_t *wt,
+            int64_t *iterations) {
+  alg3_state s;
+  s.els = els; s.n = n; s.tick_s = tick_s; s.mode = mode;
+  s.tmin = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+  s.tmax = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+  s.lo = (float *)malloc(sizeof(float) * 4 * (size_t)n);
+  s.hi = (float *)malloc(sizeof(float) * 4 * (size_t)n);
+  int64_t *l = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  int rc = 0;
+  int64_t iters = 0;
+
+  /* Alg 4: insert every object at [0, 0]; an overlap is a collision at 0 */
+  for (int64_t i = 0; i < n; ++i) {
+    s.tmin[i] = 0; s.tmax[i] = 0;
+    a3_update(&s, i);
+    for (int64_t y = 0; y < i; ++y)
+      if (a3_meet(&s, i, y)) {
+        *wi = (uint32_t)y; *wj = (uint32_t)i; *wt = 0;
+        rc = 1;
+        goto done;
+      }
+  }
+
+  for (;;) {
+    /* getSmallestMaxTimeObject: ties go to the lowest index */
+    int64_t v = 0;
+    for (int64_t z = 1; z < n; ++z)
+      if (s.tmax[z] < s.tmax[v]) v = z;
+    int64_t tp = s.tmax[v];
+    /* Loop Invariant 1: every t_min <= t' + delta */
+    for (int64_t z = 0; z < n; ++z)
+      if (s.tmin[z] > tp + 1) { rc = -1; goto done; }
+    /* Loop Invariant 2: no actual collision up to t' */
+    if (t_first >= 0 && t_first <= tp) { rc = -2; goto done; }
+    if (tp >= T) break;
+    if (++iters > 100000000) { rc = -3; goto done; }
+
+    /* Alg 5: advanceTime */
+    int64_t prev = s.tmax[v] - s.tmin[v];
+    int64_t next = prev > 0 ? 2 * prev : 1;
+    s.tmin[v] = s.tmax[v] + 1;
+    s.tmax[v] = s.tmin[v] + next;
+    if (s.tmax[v] > T) s.tmax[v] = T;
+    a3_update(&s, v);
+
+    /* Alg 6: resolveCollisions */
+    int64_t nl = a3_query(&s, v, l);
+    while (nl > 0) {
+      for (int64_t q = 0; q < nl; ++q) {
+        int64_t y = l[q];
+        if (!a3_meet(&s, y, v)) continue;
+        int64_t sy = s.tmax[y] - s.tmin[y];
+        int64_t sv = s.tmax[v] - s.tmin[v];
+        if (sy == 0 && sv == 0) {
+          *wi = (uint32_t)(v < y ? v : y);
+          *wj = (uint32_t)(v < y ? y : v);
+          *wt = s.tmin[v];
+          rc = 1;
+          goto done;
+        } else if (s.tmin[y] < s.tmin[v]) {
+          /* the branch raises y's t_min to v's (the text of Sec. 4.4) */
+          s.tmin[y] = s.tmin[v];
+          a3_update(&s, y);
+        } else if (sv <= sy) {
+          s.tmax[y] = s.tmin[y] + sy / 2;
+          a3_update(&s, y);
+        } else {
+          s.tmax[v] = s.tmin[v] + sv / 2;
+          a3_update(&s, v);
+        }
+      }
+      nl = a3_query(&s, v, l);
+    }
+  }
+done:
+  if (iterations) *iterations = iters;
+  free(s.tmin); free(s.tmax); free(s.lo); free(s.hi); free(l);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Static decomposition: potential-collision graph from perigee/apogee      */
+/* (Sec. 6.1) and altitude bands from every (n/p)-th sorted semi-major axis.*/
+/* ------------------------------------------------------------------------ */
+
+void or_radial_range(const double *el, double out[2]) {
+  /* a true collision needs ||dpos||_inf <= r_i + r_j, hence
+   * | |pos_i| - |pos_j| | <= sqrt(3) (r_i + r_j): padding each object's
+   * [perigee, apogee] radius range by sqrt(3) r keeps every such pair. */
+  double a = el[0], e = el[1], r = el[6];
+  double pad = sqrt(3.0) * r;
+  out[0] = a * (1.0 - e) - pad;
+  out[1] = a * (1.0 + e) + pad;
+}
+
+static int cmp_double(const void *x, const void *y) {
+  double a = *(const double *)x, b = *(const double *)y;
+  return (a > b) - (a < b);
+}
+
+void or_band_edges(const double *els, int64_t n, int p, double *edges) {
+  double *a = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) a[i] = els[7 * i];
+  qsort(a, (size_t)n, sizeof(double), cmp_double);
+  int64_t d = n / p;
+  for (int k = 1; k < p; ++k) edges[k - 1] = a[(int64_t)k * d];
+  free(a);
+}
+
+void or_band_counts(const double *els, int64_t n, int p, int64_t *counts) {
+  double *edges = (double *)malloc(sizeof(double) * (size_t)(p > 1 ? p - 1 : 1));
+  if (p > 1) or_band_edges(els, n, p, edges);
+  for (int k = 0; k < p; ++k) counts[k] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    double rr[2];
+    or_radial_range(els + 7 * i, rr);
+    for (int k = 0; k < p; ++k) {
+      double lo = k == 0 ? -INFINITY : edges[k - 1];
+      double hi = k == p - 1 ? INFINITY : edges[k];
+      /* [rr0, rr1] meets [lo, hi) */
+      if (rr[0] < hi && rr[1] >= lo) counts[k]++;
+    }
+  }
+  free(edges);
+}

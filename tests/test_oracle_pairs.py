@@ -1,0 +1,150 @@
+"""Pins of the oracle's pair sets: the closed 4D overlap set (Defs 2, 8),
+its canonical merged form, and coverage of every true collision found by the
+paper's brute force Alg 1 (soundness, Sec. 7.2)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import population as P
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _cells(rows):
+    return np.array([tuple(int(x) for x in r) for r in rows], dtype=O.CELL_DTYPE)
+
+
+def test_merge_golden():
+    raw, want = [], []
+    with open(os.path.join(GOLD, "merge_example.txt")) as f:
+        for line in f:
+            s = line.split()
+            if not s or s[0].startswith("#"):
+                continue
+            (raw if s[0] == "raw" else want).append(s[1:])
+    got = O.canonicalize(_cells(raw))
+    assert got.tolist() == _cells(want).tolist()
+
+
+def _random_boxes(g, N, nobj, span=100.0, size=10.0, T=200):
+    lo = np.zeros((N, 4), np.float32)
+    hi = np.zeros((N, 4), np.float32)
+    c = g.uniform(-span, span, (N, 3)).astype(np.float32)
+    w = g.uniform(0, size, (N, 3)).astype(np.float32)
+    # quantise so that exact touching (lo_a == hi_b) happens often
+    c = np.round(c)
+    w = np.round(w)
+    lo[:, :3] = c - w
+    hi[:, :3] = c + w
+    t0 = g.integers(0, T, N)
+    t1 = t0 + g.integers(0, 20, N)
+    lo[:, 3] = t0
+    hi[:, 3] = t1
+    obj = g.integers(0, nobj, N).astype(np.uint32)
+    return lo, hi, obj
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sweep_equals_bruteforce_and_python_loop(seed):
+    g = np.random.default_rng(seed)
+    lo, hi, obj = _random_boxes(g, 300, 40)
+    a = O.raw_cells_bruteforce(lo, hi, obj)
+    b = O.raw_cells_sweep(lo, hi, obj)
+    key = lambda c: sorted(map(tuple, c.tolist()))
+    assert key(a) == key(b)
+    # a third, pure-Python definition of the same set
+    ref = []
+    for x in range(len(obj)):
+        for y in range(x + 1, len(obj)):
+            if obj[x] == obj[y]:
+                continue
+            if all(lo[x, k] <= hi[y, k] and lo[y, k] <= hi[x, k] for k in range(4)):
+                i, j = sorted((int(obj[x]), int(obj[y])))
+                ref.append((i, j, int(max(lo[x, 3], lo[y, 3])), int(min(hi[x, 3], hi[y, 3]))))
+    assert key(a) == sorted(ref)
+    assert len(a) > 0
+
+
+def test_selected_is_restriction():
+    g = np.random.default_rng(11)
+    lo, hi, obj = _random_boxes(g, 400, 50)
+    full = O.raw_cells_bruteforce(lo, hi, obj)
+    sel = np.zeros(50, np.uint8)
+    sel[[3, 7, 19, 44]] = 1
+    part = O.raw_cells_selected(lo, hi, obj, sel)
+    keep = [c for c in map(tuple, full.tolist()) if sel[c[0]] or sel[c[1]]]
+    assert sorted(map(tuple, part.tolist())) == sorted(keep)
+
+
+def test_touching_boxes_count_and_same_object_never():
+    lo = np.array([[0, 0, 0, 0], [1, 0, 0, 5], [0, 0, 0, 0]], np.float32)
+    hi = np.array([[1, 1, 1, 5], [2, 1, 1, 9], [1, 1, 1, 5]], np.float32)
+    obj = np.array([0, 1, 0], np.uint32)
+    got = O.raw_cells_bruteforce(lo, hi, obj).tolist()
+    assert sorted(got) == [(0, 1, 5, 5), (0, 1, 5, 5)]
+
+
+def test_identical_elements_collide_over_whole_horizon():
+    # the docked-spacecraft case of Sec. 6.2: identical elements
+    els = P.uniform_leo(6, seed=3)
+    els[4] = els[1]
+    k = np.array([10, 7, 13, 10, 7, 10], np.int64)
+    cells = O.screen(els, 600, 1.0, k)
+    mine = cells[(cells["i"] == 1) & (cells["j"] == 4)]
+    assert mine.tolist() == [(1, 4, 0, 600)]
+
+
+def test_crossing_pair_is_reported_at_its_tick():
+    els, cr = P.catalog_mixture(n=2000, seed=21, crossing_frac=0.004, horizon_s=3000.0,
+                                return_crossings=True)
+    sub = sorted({x for c in cr for x in c[:2]})
+    e2 = els[sub]
+    k = O.step_ticks(e2, O.STEP_PERIOD_FRACTION, 1.0, frac=100.0)
+    cells = O.screen(e2, 3000, 1.0, k)
+    for (b, c, tc) in cr:
+        i, j = sub.index(b), sub.index(c)
+        m = cells[(cells["i"] == i) & (cells["j"] == j)]
+        assert np.any((m["tlo"] <= tc) & (tc <= m["thi"]))
+        # and at t_c the two objects really meet (Alg 1's test)
+        assert np.abs(O.position(e2[i], tc) - O.position(e2[j], tc)).max() < 1e-6
+
+
+def test_geo_and_leo_never_pair():
+    els = np.array([[42164.0, 0.0, 0.0, 0.0, 0.0, 0.0, 2.5],
+                    [6778.0, 0.0, 0.0, 0.0, 0.0, 0.0, 2.5]])
+    k = np.array([100, 50], np.int64)
+    assert len(O.screen(els, 86400, 1.0, k)) == 0
+
+
+@pytest.mark.parametrize("mode", [O.BOX_SPEED, O.BOX_INTERVAL])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_screen_covers_every_alg1_witness(mode, seed):
+    """Soundness: each true collision (i, j, t) of Alg 1 lies inside a
+    reported (i, j, [tlo, thi])."""
+    g = np.random.default_rng(seed)
+    els = P.uniform_leo(24, seed=100 + seed, radius_km=300.0)
+    T = 400
+    wit = O.alg1_witnesses(els, T, 1.0)
+    assert len(wit) > 0
+    k = g.integers(1, 40, len(els)).astype(np.int64)
+    cells = O.screen(els, T, 1.0, k, mode)
+    for w in wit.tolist():
+        m = cells[(cells["i"] == w[0]) & (cells["j"] == w[1])]
+        assert np.any((m["tlo"] <= w[2]) & (w[2] <= m["thi"])), w
+
+
+def test_one_tick_segments_equal_alg1_exactly():
+    """With a step of one tick every box is a single instant (Property 1), so
+    the pair set is Alg 1's witness set up to the epsilon margin and FP32
+    rounding; with well-separated distances it is exactly that set."""
+    els = P.uniform_leo(16, seed=5, radius_km=400.0)
+    T = 120
+    wit = O.alg1_witnesses(els, T, 1.0)
+    k = np.ones(len(els), np.int64)
+    lo, hi, obj = O.boxes(els, T, 1.0, k)
+    raw = O.raw_cells_sweep(lo, hi, obj)
+    got = sorted((c[0], c[1], c[2]) for c in raw.tolist())
+    assert all(c[2] == c[3] for c in raw.tolist())
+    assert got == sorted(map(tuple, wit.tolist()))
