@@ -1,0 +1,222 @@
+/*
+ * scd.h -- C ABI of libscd: broad-phase n-to-n screening of orbiting objects
+ * over 4D space-time boxes on one GB300 (sm_103a).
+ *
+ * Method: Bak & Hobbs, "Efficient n-to-n Collision Detection for Space Debris
+ * using 4D AABB Trees".  Each object is cut into per-object time segments;
+ * each segment becomes a 4D box (its interval occupancy region, Def 7, times
+ * its tick interval, Def 8); every pair of boxes of different objects that
+ * overlap is a candidate; candidates are reported as a sorted list of
+ * (i < j, tick interval) with touching intervals of one pair merged.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an int status: SCD_OK (0) or a negative SCD_ERR_*.
+ *    scd_status_string() names it.  On error no output is partially valid.
+ *  - Time is integer ticks of tick_s seconds (Def 6, the discrete-time
+ *    problem).  The horizon is T = horizon_s / tick_s ticks (must be a whole
+ *    number, T < 2^24); ticks 0..T inclusive are screened, as in Alg 1.
+ *  - Boxes are closed on all four axes (Def 2 uses <=).
+ *  - A scene owns all device memory it allocates and frees it in
+ *    scd_scene_destroy.  Host arrays passed in are copied; the caller keeps
+ *    ownership.  A scene is not thread-safe; distinct scenes are independent.
+ *  - Work is queued on the CUDA stream given at creation.  Calls that return
+ *    host data synchronise that stream.
+ *  - Nothing here runs on the CPU apart from argument checks and launch
+ *    bookkeeping; if no CUDA device is usable the calls fail with
+ *    SCD_ERR_CUDA.
+ */
+#ifndef SCD_H
+#define SCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SCD_API __attribute__((visibility("default")))
+
+enum {
+  SCD_OK = 0,
+  SCD_ERR_INVALID_ARG = -1,   /* bad size, element, horizon or policy      */
+  SCD_ERR_OOM = -2,           /* device allocation failed                  */
+  SCD_ERR_BUFFER_TOO_SMALL = -3, /* *n_out holds the count that is needed  */
+  SCD_ERR_CUDA = -4,          /* a CUDA runtime call failed                */
+  SCD_ERR_KEPLER_NOCONV = -5, /* Kepler's equation did not converge        */
+  SCD_ERR_TIMEOUT = -6,       /* a bounded device wait gave up             */
+  SCD_ERR_INTERNAL = -7,      /* a device-side consistency check failed    */
+  SCD_ERR_STATE = -8          /* call out of order (e.g. no boxes built)   */
+};
+
+/* One object (Def 1: position function plus fixed infinity-norm radius).
+ * Two-body Kepler elements (Sec. 6.1): semi-major axis a > 0 [km],
+ * eccentricity 0 <= e < 1, inclination, right ascension of the ascending
+ * node, argument of perigee and mean anomaly at t = 0 [rad], radius >= 0
+ * [km].  56 bytes, seven doubles in this order. */
+typedef struct {
+  double a_km, e, inc_rad, raan_rad, argp_rad, M0_rad, radius_km;
+} scd_element;
+
+/* Per-object step length in ticks (Sec. 4: time is tracked per object).
+ *  FIXED            k = fixed_ticks for every object
+ *  PERIOD_FRACTION  k = floor(P / (period_fraction * tick_s)), P the period
+ *  BAND_TABLE       as PERIOD_FRACTION with the fraction looked up by
+ *                   perigee altitude a(1-e) - 6378.137 km: n_bands fractions,
+ *                   n_bands-1 ascending edges [km]; band b covers
+ *                   [edge[b-1], edge[b])
+ *  LEARNED          k from a step network (scd_stepnet_*), clamped to
+ *                   [P/400, P/50]
+ * k is at least one tick.  Arrays are copied at scene creation. */
+typedef enum {
+  SCD_STEP_FIXED = 0,
+  SCD_STEP_PERIOD_FRACTION = 1,
+  SCD_STEP_BAND_TABLE = 2,
+  SCD_STEP_LEARNED = 3
+} scd_step_kind;
+
+typedef struct {
+  scd_step_kind kind;
+  uint32_t fixed_ticks;
+  double period_fraction;
+  const double *band_edges_km;
+  const double *band_fractions;
+  int n_bands;
+  const void *stepnet; /* scd_stepnet* for SCD_STEP_LEARNED */
+} scd_step_policy;
+
+/* How occ-int (Def 7) bounds a segment [t0, t1]:
+ *  SPEED     cube of half-width r + vmax (t1 - t0)/2 around pos((t0+t1)/2),
+ *            vmax the perigee speed (vis-viva)
+ *  INTERVAL  interval evaluation over the eccentric-anomaly range of the
+ *            segment (Sec. 4.5: the single orbital variable is monotone, its
+ *            end values bound it), widened by r
+ * Both add 1e-6 km and round outward to FP32; both satisfy Properties 1-2. */
+typedef enum { SCD_BOX_SPEED = 0, SCD_BOX_INTERVAL = 1 } scd_box_mode;
+
+/* Static decomposition (Sec. 5, Sec. 6.1), solved as independent
+ * sub-problems in one launch.
+ *  NONE       one problem
+ *  ALT_BANDS  p_bands altitude bands with edges at every (n/p)-th sorted
+ *             semi-major axis; an object is in every band that its radial
+ *             range [a(1-e) - sqrt(3) r, a(1+e) + sqrt(3) r] meets.  Only
+ *             pairs joined in the potential-collision graph (Def 9: radial
+ *             ranges intersect) are reported.
+ *  SLAB_OCT   n_slabs equal tick slabs x the 8 ECI sign octants; the output
+ *             equals the NONE output exactly. */
+typedef enum {
+  SCD_DECOMP_NONE = 0,
+  SCD_DECOMP_ALT_BANDS = 1,
+  SCD_DECOMP_SLAB_OCT = 2
+} scd_decomp_kind;
+
+typedef struct {
+  scd_decomp_kind kind;
+  int p_bands;
+  int n_slabs;
+} scd_decomp;
+
+/* One candidate: objects i < j may collide at some tick of [tlo, thi]
+ * (closed).  The list is sorted by (i, j, tlo); intervals of one pair never
+ * overlap or touch. */
+typedef struct {
+  uint32_t i, j;
+  int32_t tlo, thi;
+} scd_pair;
+
+/* Tunables of the tree and traversal (picked by the autotuner). */
+typedef struct {
+  int leaf_size;      /* boxes per leaf: 1, 2, 4 or 8                      */
+  int stack_depth;    /* traversal stack entries: 32, 64 or 128            */
+  int block_threads;  /* traversal block size: 64..1024, multiple of 32     */
+  int morton_bits;    /* bits per axis of the 4D Morton key: 8, 10, 12, 16  */
+  float time_scale;   /* weight of the time axis in the Morton key          */
+  int use_graph;      /* 1: replay find_pairs as one captured CUDA graph    */
+} scd_tuning;
+
+typedef struct scd_scene scd_scene;
+
+/* Device memory hooks (e.g. a framework's caching allocator).  alloc returns
+ * NULL on failure.  Passing NULLs restores cudaMalloc/cudaFree.  Applies to
+ * allocations made after the call, process-wide. */
+SCD_API int scd_set_allocator(void *(*alloc_fn)(size_t bytes, void *stream, void *ctx),
+                              void (*free_fn)(void *ptr, void *stream, void *ctx),
+                              void *ctx);
+
+/* Create a scene of n objects (Defs 1, 5-6).  elems: host array of n
+ * elements, copied.  horizon_s / tick_s must be a whole number of ticks.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: INVALID_ARG (n <= 0, a <= 0, e outside [0, 1), radius < 0, a NaN,
+ * horizon or tick <= 0 or not commensurate, bad policy), OOM, CUDA. */
+SCD_API int scd_scene_create(const scd_element *elems, int64_t n, double horizon_s,
+                             double tick_s, const scd_step_policy *step,
+                             scd_box_mode mode, void *cuda_stream, scd_scene **out);
+
+/* Replace the scene's elements with n new ones from host memory (same n);
+ * boxes must be rebuilt. */
+SCD_API int scd_scene_set_elements(scd_scene *s, const scd_element *elems, int64_t n);
+
+/* The same, from device memory (n elements in the scd_element layout). */
+SCD_API int scd_scene_set_elements_device(scd_scene *s, const scd_element *d_elems, int64_t n);
+
+/* Tuning for later calls; NULL fields are not allowed, use scd_default_tuning. */
+SCD_API int scd_scene_set_tuning(scd_scene *s, const scd_tuning *t);
+SCD_API int scd_default_tuning(scd_tuning *t);
+
+/* Steps A1-A4: per-object steps, FP64 propagation, outward-rounded FP32
+ * boxes and 4D Morton keys (Defs 7-8, Sec. 4.5, Eq. 1).  Asynchronous apart
+ * from one read of the box count.  Errors: KEPLER_NOCONV, OOM, CUDA. */
+SCD_API int scd_build_boxes(scd_scene *s);
+
+/* Steps A5-A10: sort, hierarchy, refit, traversal and canonical list
+ * (Sec. 3.2 query semantics; Sec. 5 decomposition when d != NULL and
+ * d->kind != NONE).  host_out: host array of cap pairs.  On success *n_out
+ * is the number of pairs written.  If cap is too small: BUFFER_TOO_SMALL,
+ * *n_out = the count needed, nothing written.  Synchronous. */
+SCD_API int scd_find_pairs(scd_scene *s, const scd_decomp *d, scd_pair *host_out,
+                           int64_t cap, int64_t *n_out);
+
+/* The same, leaving the list in device memory owned by the scene; *dev_out
+ * stays valid until the next find_pairs call or scd_scene_destroy. */
+SCD_API int scd_find_pairs_device(scd_scene *s, const scd_decomp *d,
+                                  const scd_pair **dev_out, int64_t *n_out);
+
+/* Every overlapping box pair, unmerged, sorted by (i, j, tlo) (for parity
+ * tests of the raw candidate set).  Device memory owned by the scene. */
+SCD_API int scd_find_raw_cells_device(scd_scene *s, const scd_pair **dev_out,
+                                      int64_t *n_out);
+
+/* The scene's boxes in object-major, segment order (device pointers owned
+ * by the scene): lo4/hi4 are nbox x 4 floats (x, y, z [km], tick), obj the
+ * object of each box. */
+SCD_API int scd_get_boxes(const scd_scene *s, const float **lo4, const float **hi4,
+                          const uint32_t **obj, int64_t *nbox);
+
+/* Per-object step lengths [ticks] (device, n entries, owned by the scene). */
+SCD_API int scd_get_steps(const scd_scene *s, const int32_t **steps);
+
+/* FP64 positions (Sec. 6.1) of objects obj[q] at times t_s[q]: device
+ * arrays elems (n), obj (m), t_s (m), out (3 m doubles, x y z [km]).
+ * Runs the propagation code of scd_build_boxes.  Asynchronous on stream. */
+SCD_API int scd_propagate(const scd_element *d_elems, int64_t n, const uint32_t *d_obj,
+                          const double *d_t_s, int64_t m, double *d_out, void *cuda_stream);
+
+/* Batched screening: n_scenes independent scenes (each already with boxes)
+ * in one persistent traversal launch.  outs[s] is a host array of caps[s]
+ * pairs; n_outs[s] receives each count.  BUFFER_TOO_SMALL if any cap is too
+ * small (all counts still reported). */
+SCD_API int scd_batch_find_pairs(scd_scene *const *scenes, int n_scenes, const scd_decomp *d,
+                                 scd_pair *const *outs, const int64_t *caps, int64_t *n_outs);
+
+/* Metrics of the scene's last find_pairs as one JSON object (box count,
+ * node and leaf tests, pair counts, kernel times).  Writes at most cap bytes
+ * including the terminating NUL. */
+SCD_API int scd_last_metrics(const scd_scene *s, char *json, size_t cap);
+
+SCD_API void scd_scene_destroy(scd_scene *s);
+SCD_API const char *scd_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,123 @@
+"""GB300-native broad-phase n-to-n screening over 4D space-time boxes
+(Bak & Hobbs, "Efficient n-to-n Collision Detection for Space Debris using
+4D AABB Trees").
+
+The work runs in libscd.so (hand-written sm_103a CUDA behind the C ABI of
+include/scd.h); this package marshals arguments and uses PyTorch only for
+device memory (its caching allocator) and streams.
+"""
+from __future__ import annotations
+
+import json
+
+import numpy as np
+
+from . import _binding as B
+from ._binding import (PAIR_DTYPE, SCD_BOX_INTERVAL, SCD_BOX_SPEED, SCD_DECOMP_ALT_BANDS,
+                       SCD_DECOMP_NONE, SCD_DECOMP_SLAB_OCT, SCD_STEP_BAND_TABLE, SCD_STEP_FIXED,
+                       SCD_STEP_LEARNED, SCD_STEP_PERIOD_FRACTION, ScdError, make_step_policy,
+                       scd_batch_find_pairs, scd_build_boxes, scd_default_tuning,
+                       scd_find_pairs, scd_find_pairs_device, scd_find_pairs_into,
+                       scd_find_raw_cells_device,
+                       scd_get_boxes, scd_get_steps, scd_last_metrics, scd_propagate,
+                       scd_scene_create, scd_scene_destroy, scd_scene_set_elements,
+                       scd_scene_set_elements_device, scd_scene_set_tuning,
+                       scd_status_string)
+
+__all__ = [n for n in dir(B) if n.startswith("scd_") or n.startswith("SCD_")] + [
+    "Scene", "device_view", "PAIR_DTYPE", "ScdError", "make_step_policy"]
+
+
+class _CudaArray:
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3,
+                                         "strides": None}
+
+
+def device_view(ptr: int, shape, typestr: str):
+    """A torch tensor viewing device memory owned by the library (no copy)."""
+    import torch
+    if int(np.prod(shape)) == 0:
+        dt = {"<f4": torch.float32, "<u4": torch.int32, "<i4": torch.int32,
+              "<f8": torch.float64}[typestr]
+        return torch.empty(tuple(shape), dtype=dt, device="cuda")
+    return torch.as_tensor(_CudaArray(ptr, shape, typestr), device="cuda")
+
+
+class Scene:
+    """One screening problem: n objects over [0, horizon] in ticks of tick_s."""
+
+    def __init__(self, elements, horizon_s: float, tick_s: float = 1.0, step=None,
+                 mode: int = SCD_BOX_SPEED, stream=None, tuning=None):
+        import torch
+        B.use_torch_allocator()
+        if step is None:
+            step = make_step_policy(SCD_STEP_PERIOD_FRACTION, period_fraction=100.0)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        self.n = len(elements)
+        self.handle = scd_scene_create(elements, horizon_s, tick_s, step, mode,
+                                       int(stream.cuda_stream))
+        if tuning is not None:
+            self.set_tuning(tuning)
+
+    def set_tuning(self, t):
+        if isinstance(t, dict):
+            x = scd_default_tuning()
+            for k, v in t.items():
+                setattr(x, k, v)
+            t = x
+        scd_scene_set_tuning(self.handle, t)
+
+    def set_elements(self, elements):
+        scd_scene_set_elements(self.handle, elements)
+
+    def build_boxes(self):
+        scd_build_boxes(self.handle)
+        return self
+
+    def find_pairs(self, decomp=None) -> np.ndarray:
+        return scd_find_pairs(self.handle, decomp)
+
+    def find_pairs_device(self, decomp=None):
+        ptr, n = scd_find_pairs_device(self.handle, decomp)
+        return device_view(ptr, (n, 4), "<i4")
+
+    def find_raw_cells_device(self):
+        ptr, n = scd_find_raw_cells_device(self.handle)
+        return device_view(ptr, (n, 4), "<i4")
+
+    def boxes(self):
+        lo, hi, obj, n = scd_get_boxes(self.handle)
+        return (device_view(lo, (n, 4), "<f4"), device_view(hi, (n, 4), "<f4"),
+                device_view(obj, (n,), "<i4"))
+
+    def steps(self):
+        return device_view(scd_get_steps(self.handle), (self.n,), "<i4")
+
+    def metrics(self) -> dict:
+        return json.loads(scd_last_metrics(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            scd_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pairs_from_device(t) -> np.ndarray:
+    """Copy an (n, 4) int32 device view of scd_pair records to numpy."""
+    a = t.cpu().numpy()
+    out = np.zeros(len(a), PAIR_DTYPE)
+    out["i"] = a[:, 0].view(np.uint32)
+    out["j"] = a[:, 1].view(np.uint32)
+    out["tlo"] = a[:, 2]
+    out["thi"] = a[:, 3]
+    return out

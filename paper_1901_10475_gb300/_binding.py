@@ -1,0 +1,306 @@
+"""ctypes binding of libscd (include/scd.h): argument marshalling only.
+
+Every name here is the C entry point of the same name.  The library is the
+compiled CUDA path; there is no CPU fallback.  If the shared library cannot
+be built or loaded, importing fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SCD_OK = 0
+SCD_ERR_INVALID_ARG = -1
+SCD_ERR_OOM = -2
+SCD_ERR_BUFFER_TOO_SMALL = -3
+SCD_ERR_CUDA = -4
+SCD_ERR_KEPLER_NOCONV = -5
+SCD_ERR_TIMEOUT = -6
+SCD_ERR_INTERNAL = -7
+SCD_ERR_STATE = -8
+
+SCD_STEP_FIXED, SCD_STEP_PERIOD_FRACTION, SCD_STEP_BAND_TABLE, SCD_STEP_LEARNED = 0, 1, 2, 3
+SCD_BOX_SPEED, SCD_BOX_INTERVAL = 0, 1
+SCD_DECOMP_NONE, SCD_DECOMP_ALT_BANDS, SCD_DECOMP_SLAB_OCT = 0, 1, 2
+
+
+class scd_element(ctypes.Structure):
+    _fields_ = [("a_km", ctypes.c_double), ("e", ctypes.c_double), ("inc_rad", ctypes.c_double),
+                ("raan_rad", ctypes.c_double), ("argp_rad", ctypes.c_double),
+                ("M0_rad", ctypes.c_double), ("radius_km", ctypes.c_double)]
+
+
+class scd_step_policy(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("fixed_ticks", ctypes.c_uint32),
+                ("period_fraction", ctypes.c_double),
+                ("band_edges_km", ctypes.POINTER(ctypes.c_double)),
+                ("band_fractions", ctypes.POINTER(ctypes.c_double)),
+                ("n_bands", ctypes.c_int), ("stepnet", ctypes.c_void_p)]
+
+
+class scd_decomp(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("p_bands", ctypes.c_int), ("n_slabs", ctypes.c_int)]
+
+
+class scd_pair(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_uint32), ("j", ctypes.c_uint32), ("tlo", ctypes.c_int32),
+                ("thi", ctypes.c_int32)]
+
+
+class scd_tuning(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int), ("stack_depth", ctypes.c_int),
+                ("block_threads", ctypes.c_int), ("morton_bits", ctypes.c_int),
+                ("time_scale", ctypes.c_float), ("use_graph", ctypes.c_int)]
+
+
+PAIR_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("tlo", "<i4"), ("thi", "<i4")])
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ScdError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+def lib() -> ctypes.CDLL:
+    """Load libscd.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        P = ctypes.POINTER
+        sigs = {
+            "scd_set_allocator": (i32, [ALLOC_FN, FREE_FN, vp]),
+            "scd_scene_create": (i32, [vp, i64, d, d, P(scd_step_policy), i32, vp, P(vp)]),
+            "scd_scene_set_elements": (i32, [vp, vp, i64]),
+            "scd_scene_set_elements_device": (i32, [vp, vp, i64]),
+            "scd_scene_set_tuning": (i32, [vp, P(scd_tuning)]),
+            "scd_default_tuning": (i32, [P(scd_tuning)]),
+            "scd_build_boxes": (i32, [vp]),
+            "scd_find_pairs": (i32, [vp, P(scd_decomp), vp, i64, P(i64)]),
+            "scd_find_pairs_device": (i32, [vp, P(scd_decomp), P(vp), P(i64)]),
+            "scd_find_raw_cells_device": (i32, [vp, P(vp), P(i64)]),
+            "scd_get_boxes": (i32, [vp, P(vp), P(vp), P(vp), P(i64)]),
+            "scd_get_steps": (i32, [vp, P(vp)]),
+            "scd_propagate": (i32, [vp, i64, vp, vp, i64, vp, vp]),
+            "scd_batch_find_pairs": (i32, [P(vp), i32, P(scd_decomp), P(vp), P(i64), P(i64)]),
+            "scd_last_metrics": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t]),
+            "scd_scene_destroy": (None, [vp]),
+            "scd_status_string": (ctypes.c_char_p, [i32]),
+        }
+        for name, (res, args) in sigs.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def status_string(status: int) -> str:
+    return lib().scd_status_string(int(status)).decode()
+
+
+def check(status: int, what: str) -> None:
+    if status != SCD_OK:
+        raise ScdError(status, what)
+
+
+# --- torch caching allocator as the device allocator ----------------------
+
+_torch_hooks = None
+
+
+def use_torch_allocator() -> None:
+    """Route libscd's device allocations through torch's caching allocator."""
+    global _torch_hooks
+    if _torch_hooks is not None:
+        return
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      int(stream or 0))
+        except Exception:  # out of memory: the library reports SCD_ERR_OOM
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+    check(lib().scd_set_allocator(hooks[0], hooks[1], None), "scd_set_allocator")
+    _torch_hooks = hooks
+
+
+# --- entry points with the C names ----------------------------------------
+
+def _elems(els) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(els, dtype=np.float64))
+    if a.ndim != 2 or a.shape[1] != 7:
+        raise ValueError("elements must be an (n, 7) float64 array")
+    return a
+
+
+def make_step_policy(kind: int = SCD_STEP_PERIOD_FRACTION, fixed_ticks: int = 1,
+                     period_fraction: float = 100.0, band_edges_km=(), band_fractions=()):
+    pol = scd_step_policy()
+    pol.kind = kind
+    pol.fixed_ticks = int(fixed_ticks)
+    pol.period_fraction = float(period_fraction)
+    keep = []
+    if kind == SCD_STEP_BAND_TABLE:
+        e = np.ascontiguousarray(np.asarray(band_edges_km, np.float64).reshape(-1))
+        f = np.ascontiguousarray(np.asarray(band_fractions, np.float64).reshape(-1))
+        keep = [e, f]
+        pol.band_edges_km = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        pol.band_fractions = f.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        pol.n_bands = len(f)
+    pol._keep = keep  # the arrays must outlive the create call
+    return pol
+
+
+def scd_scene_create(els, horizon_s: float, tick_s: float, policy: scd_step_policy,
+                     mode: int = SCD_BOX_SPEED, stream: int = 0) -> int:
+    a = _elems(els)
+    out = ctypes.c_void_p()
+    check(lib().scd_scene_create(a.ctypes.data, len(a), float(horizon_s), float(tick_s),
+                                 ctypes.byref(policy), int(mode), ctypes.c_void_p(stream),
+                                 ctypes.byref(out)), "scd_scene_create")
+    return out.value
+
+
+def scd_scene_set_elements(scene: int, els) -> None:
+    a = _elems(els)
+    check(lib().scd_scene_set_elements(scene, a.ctypes.data, len(a)), "scd_scene_set_elements")
+
+
+def scd_scene_set_elements_device(scene: int, d_ptr: int, n: int) -> None:
+    check(lib().scd_scene_set_elements_device(scene, d_ptr, n), "scd_scene_set_elements_device")
+
+
+def scd_default_tuning() -> scd_tuning:
+    t = scd_tuning()
+    check(lib().scd_default_tuning(ctypes.byref(t)), "scd_default_tuning")
+    return t
+
+
+def scd_scene_set_tuning(scene: int, t: scd_tuning) -> None:
+    check(lib().scd_scene_set_tuning(scene, ctypes.byref(t)), "scd_scene_set_tuning")
+
+
+def scd_build_boxes(scene: int) -> None:
+    check(lib().scd_build_boxes(scene), "scd_build_boxes")
+
+
+def _decomp(d):
+    if d is None:
+        return None
+    if isinstance(d, scd_decomp):
+        return ctypes.byref(d)
+    x = scd_decomp()
+    x.kind, x.p_bands, x.n_slabs = d
+    return ctypes.byref(x)
+
+
+def scd_find_pairs(scene: int, decomp=None, cap: int | None = None) -> np.ndarray:
+    """Canonical pair list copied to host memory (a numpy PAIR_DTYPE array)."""
+    n = ctypes.c_int64(0)
+    if cap is None:
+        cap = 1 << 16
+    while True:
+        out = np.zeros(max(cap, 1), PAIR_DTYPE)
+        rc = lib().scd_find_pairs(scene, _decomp(decomp), out.ctypes.data, cap, ctypes.byref(n))
+        if rc == SCD_ERR_BUFFER_TOO_SMALL:
+            cap = int(n.value)
+            continue
+        check(rc, "scd_find_pairs")
+        return out[:n.value]
+
+
+def scd_find_pairs_into(scene: int, host_out: np.ndarray, decomp=None) -> int:
+    """Fill a caller-owned (pinned) host array; returns the pair count."""
+    n = ctypes.c_int64(0)
+    rc = lib().scd_find_pairs(scene, _decomp(decomp), host_out.ctypes.data, len(host_out),
+                              ctypes.byref(n))
+    check(rc, "scd_find_pairs")
+    return int(n.value)
+
+
+def scd_find_pairs_device(scene: int, decomp=None):
+    """(device pointer, count) of the canonical list, owned by the scene."""
+    p, n = ctypes.c_void_p(), ctypes.c_int64(0)
+    check(lib().scd_find_pairs_device(scene, _decomp(decomp), ctypes.byref(p), ctypes.byref(n)),
+          "scd_find_pairs_device")
+    return p.value, int(n.value)
+
+
+def scd_find_raw_cells_device(scene: int):
+    p, n = ctypes.c_void_p(), ctypes.c_int64(0)
+    check(lib().scd_find_raw_cells_device(scene, ctypes.byref(p), ctypes.byref(n)),
+          "scd_find_raw_cells_device")
+    return p.value, int(n.value)
+
+
+def scd_get_boxes(scene: int):
+    lo, hi, obj, n = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_int64(0)
+    check(lib().scd_get_boxes(scene, ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(obj),
+                              ctypes.byref(n)), "scd_get_boxes")
+    return lo.value, hi.value, obj.value, int(n.value)
+
+
+def scd_get_steps(scene: int) -> int:
+    p = ctypes.c_void_p()
+    check(lib().scd_get_steps(scene, ctypes.byref(p)), "scd_get_steps")
+    return p.value
+
+
+def scd_propagate(d_elems: int, n: int, d_obj: int, d_t: int, m: int, d_out: int,
+                  stream: int = 0) -> None:
+    check(lib().scd_propagate(d_elems, n, d_obj, d_t, m, d_out, ctypes.c_void_p(stream)),
+          "scd_propagate")
+
+
+def scd_batch_find_pairs(scenes, decomp=None, caps=None):
+    k = len(scenes)
+    arr = (ctypes.c_void_p * k)(*scenes)
+    caps = list(caps) if caps is not None else [1 << 16] * k
+    while True:
+        outs = [np.zeros(max(c, 1), PAIR_DTYPE) for c in caps]
+        optr = (ctypes.c_void_p * k)(*[o.ctypes.data for o in outs])
+        c_caps = (ctypes.c_int64 * k)(*caps)
+        n_outs = (ctypes.c_int64 * k)()
+        rc = lib().scd_batch_find_pairs(arr, k, _decomp(decomp), optr, c_caps, n_outs)
+        if rc == SCD_ERR_BUFFER_TOO_SMALL:
+            caps = [max(caps[q], int(n_outs[q])) for q in range(k)]
+            continue
+        check(rc, "scd_batch_find_pairs")
+        return [outs[q][:n_outs[q]] for q in range(k)]
+
+
+def scd_last_metrics(scene: int) -> str:
+    buf = ctypes.create_string_buffer(4096)
+    check(lib().scd_last_metrics(scene, buf, len(buf)), "scd_last_metrics")
+    return buf.value.decode()
+
+
+def scd_scene_destroy(scene: int) -> None:
+    if scene:
+        lib().scd_scene_destroy(scene)
+
+
+def scd_status_string(status: int) -> str:
+    return status_string(status)

@@ -1,0 +1,185 @@
+// lbvh.cu -- steps A6-A7: the 4D box hierarchy.  The paper's AABB tree
+// (Sec. 3.2) is built there by incremental insertion; here the whole tree
+// is built at once from the Morton-sorted boxes as a binary radix tree
+// (Karras 2012: node ranges and split points from the longest common key
+// prefix, ties broken by index), then boxes are unioned bottom-up.
+#include "scd_internal.cuh"
+
+namespace scd {
+
+// ---------------------------------------------------------------------------
+// Gather the sorted boxes and the key of every leaf (the key of its first
+// box; a leaf holds L consecutive sorted boxes).
+// ---------------------------------------------------------------------------
+template <class K>
+__global__ void k_gather_sorted(const uint32_t *__restrict__ id, const float4 *__restrict__ lo,
+                                const float4 *__restrict__ hi, const uint32_t *__restrict__ obj,
+                                const K *__restrict__ keys, int64_t N, int L,
+                                float4 *__restrict__ slo, float4 *__restrict__ shi,
+                                uint32_t *__restrict__ sobj, K *__restrict__ leafkey) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  uint32_t b = id[p];
+  slo[p] = lo[b];
+  shi[p] = hi[b];
+  sobj[p] = obj[b];
+  if (p % L == 0) leafkey[p / L] = keys[p];
+}
+
+template <class K>
+__device__ __forceinline__ int clz_key(K x);
+template <>
+__device__ __forceinline__ int clz_key<uint32_t>(uint32_t x) { return __clz(x); }
+template <>
+__device__ __forceinline__ int clz_key<unsigned long long>(unsigned long long x) {
+  return __clzll(x);
+}
+
+// longest common prefix of leaves i and j; -1 outside [0, M)
+template <class K>
+__device__ __forceinline__ int delta(const K *__restrict__ keys, int64_t M, int64_t i, int64_t j) {
+  if (j < 0 || j >= M) return -1;
+  K a = keys[i], b = keys[j];
+  if (a != b) return clz_key<K>(a ^ b);
+  return (int)(8 * sizeof(K)) + __clz((uint32_t)(i ^ j));
+}
+
+template <class K>
+__global__ void k_karras(const K *__restrict__ keys, int64_t M, TravNode *__restrict__ nodes,
+                         int32_t *__restrict__ parent_int, int32_t *__restrict__ parent_leaf,
+                         uint32_t *__restrict__ flags) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M - 1) return;
+  // direction of the node's range
+  int dn = delta(keys, M, i, i + 1), dp = delta(keys, M, i, i - 1);
+  int64_t d = dn > dp ? 1 : -1;
+  int dmin = d > 0 ? dp : dn;
+  // upper bound of the range length, then binary search for the other end
+  int64_t lmax = 2;
+  while (delta(keys, M, i, i + lmax * d) > dmin) lmax <<= 1;
+  int64_t l = 0;
+  for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(keys, M, i, i + (l + t) * d) > dmin) l += t;
+  int64_t j = i + l * d;
+  int dnode = delta(keys, M, i, j);
+  // split: the last position that shares more than dnode bits with i
+  int64_t s = 0;
+  int64_t t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (delta(keys, M, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+  int64_t first = i < j ? i : j, last = i < j ? j : i;
+  TravNode nd;
+  nd.left = first == gamma ? (int32_t)gamma | kLeafBit : (int32_t)gamma;
+  nd.right = last == gamma + 1 ? (int32_t)(gamma + 1) | kLeafBit : (int32_t)(gamma + 1);
+  nd.last_l = (int32_t)gamma;
+  nd.last_r = (int32_t)last;
+  nd.lo_l = nd.hi_l = nd.lo_r = nd.hi_r = make_float4(0.f, 0.f, 0.f, 0.f);
+  nodes[i] = nd;
+  if (first == gamma) parent_leaf[gamma] = (int32_t)i; else parent_int[gamma] = (int32_t)i;
+  if (last == gamma + 1) parent_leaf[gamma + 1] = (int32_t)i; else parent_int[gamma + 1] = (int32_t)i;
+  if (i == 0) parent_int[0] = -1;
+  flags[i] = 0;
+}
+
+__device__ __forceinline__ float4 f4min(float4 a, float4 b) {
+  return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fminf(a.z, b.z), fminf(a.w, b.w));
+}
+__device__ __forceinline__ float4 f4max(float4 a, float4 b) {
+  return make_float4(fmaxf(a.x, b.x), fmaxf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
+}
+
+// Bottom-up union.  The second thread to reach a node (atomic arrival count)
+// reads both children and goes on; the first one stops.  Nobody waits.
+__global__ void k_refit(const float4 *__restrict__ slo, const float4 *__restrict__ shi, int64_t N,
+                        int L, int64_t M, float4 *__restrict__ leaflo, float4 *__restrict__ leafhi,
+                        TravNode *__restrict__ nodes, float4 *__restrict__ nlo,
+                        float4 *__restrict__ nhi, const int32_t *__restrict__ parent_int,
+                        const int32_t *__restrict__ parent_leaf, uint32_t *__restrict__ flags) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= M) return;
+  int64_t b0 = c * L, b1 = b0 + L < N ? b0 + L : N;
+  float4 lo = slo[b0], hi = shi[b0];
+  for (int64_t b = b0 + 1; b < b1; ++b) {
+    lo = f4min(lo, slo[b]);
+    hi = f4max(hi, shi[b]);
+  }
+  leaflo[c] = lo;
+  leafhi[c] = hi;
+  if (M == 1) return;
+  int32_t p = parent_leaf[c];
+  while (p >= 0) {
+    __threadfence();
+    if (atomicAdd(flags + p, 1u) == 0u) return;
+    __threadfence();
+    TravNode nd = nodes[p];
+    float4 llo, lhi, rlo, rhi;
+    if (nd.left & kLeafBit) {
+      int32_t q = nd.left & ~kLeafBit;
+      llo = __ldcg(leaflo + q);
+      lhi = __ldcg(leafhi + q);
+    } else {
+      llo = __ldcg(nlo + nd.left);
+      lhi = __ldcg(nhi + nd.left);
+    }
+    if (nd.right & kLeafBit) {
+      int32_t q = nd.right & ~kLeafBit;
+      rlo = __ldcg(leaflo + q);
+      rhi = __ldcg(leafhi + q);
+    } else {
+      rlo = __ldcg(nlo + nd.right);
+      rhi = __ldcg(nhi + nd.right);
+    }
+    nd.lo_l = llo;
+    nd.hi_l = lhi;
+    nd.lo_r = rlo;
+    nd.hi_r = rhi;
+    nodes[p] = nd;
+    __stcg(nlo + p, f4min(llo, rlo));
+    __stcg(nhi + p, f4max(lhi, rhi));
+    p = parent_int[p];
+  }
+}
+
+template <class K>
+static int build_impl(scd_scene *s, const K *keys_sorted, K *leafkey, int64_t &M) {
+  cudaStream_t st = s->stream;
+  int64_t N = s->N;
+  int L = s->tune.leaf_size;
+  M = (N + L - 1) / L;
+  if (!s->s_lo.ensure(N, st) || !s->s_hi.ensure(N, st) || !s->s_obj.ensure(N, st) ||
+      !s->d_leaflo.ensure(M, st) || !s->d_leafhi.ensure(M, st) ||
+      !s->d_nodes.ensure(M > 1 ? M - 1 : 1, st) || !s->d_nlo.ensure(M > 1 ? M - 1 : 1, st) ||
+      !s->d_nhi.ensure(M > 1 ? M - 1 : 1, st) || !s->d_parent_int.ensure(M, st) ||
+      !s->d_parent_leaf.ensure(M, st) || !s->d_flags.ensure(M, st))
+    return SCD_ERR_OOM;
+  int bs = 256;
+  k_gather_sorted<K><<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(
+      s->d_id.p, s->d_lo.p, s->d_hi.p, s->d_obj.p, keys_sorted, N, L, s->s_lo.p, s->s_hi.p,
+      s->s_obj.p, leafkey);
+  note_launch(2);
+  if (M > 1) {
+    k_karras<K><<<(unsigned)((M - 1 + bs - 1) / bs), bs, 0, st>>>(
+        leafkey, M, s->d_nodes.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p);
+    note_launch();
+  }
+  k_refit<<<(unsigned)((M + bs - 1) / bs), bs, 0, st>>>(
+      s->s_lo.p, s->s_hi.p, N, L, M, s->d_leaflo.p, s->d_leafhi.p, s->d_nodes.p, s->d_nlo.p,
+      s->d_nhi.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p);
+  return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
+}
+
+int build_hierarchy(scd_scene *s, int64_t &n_leaves) {
+  if (s->tune.morton_bits > 8) {
+    int64_t Mx = (s->N + s->tune.leaf_size - 1) / s->tune.leaf_size;
+    if (!s->s_leafkey64.ensure(Mx, s->stream)) return SCD_ERR_OOM;
+    return build_impl<unsigned long long>(s, s->d_key64.p, s->s_leafkey64.p, n_leaves);
+  }
+  int64_t Mx = (s->N + s->tune.leaf_size - 1) / s->tune.leaf_size;
+  if (!s->s_leafkey32.ensure(Mx, s->stream)) return SCD_ERR_OOM;
+  return build_impl<uint32_t>(s, s->d_key32.p, s->s_leafkey32.p, n_leaves);
+}
+
+}  // namespace scd

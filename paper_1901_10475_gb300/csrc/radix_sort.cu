@@ -1,0 +1,243 @@
+// radix_sort.cu -- LSD radix sort of 32- or 64-bit keys with optional 32-bit
+// values (step A5: ordering boxes along the 4D Morton curve; step A9:
+// ordering candidate records by (i, j, tick)).
+//
+// Reduce-then-scan per 8-bit digit: (1) every block counts the digits of its
+// tile, (2) one block per digit scans that digit's counts over the blocks,
+// (3) every block ranks its tile stably in shared memory (warp match + per
+// warp counters) and writes each digit's run to its global offset.  No block
+// ever waits on another block.
+#include "scd_internal.cuh"
+
+namespace scd {
+
+constexpr int kRsThreads = 256;
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsItems = 16;
+constexpr int kRsTile = kRsThreads * kRsItems;
+
+template <class K>
+__device__ __forceinline__ uint32_t digit_of(K key, int shift) {
+  return (uint32_t)(key >> shift) & 0xffu;
+}
+
+template <class K>
+__global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const K *__restrict__ keys, int64_t n,
+                                                           int shift, uint32_t *__restrict__ counts,
+                                                           int64_t nblk) {
+  __shared__ uint32_t wh[kRsWarps][256];
+  int w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&wh[0][0])[i] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * kRsTile;
+#pragma unroll 4
+  for (int k = 0; k < kRsItems; ++k) {
+    int64_t idx = base + (int64_t)k * kRsThreads + threadIdx.x;
+    if (idx < n) atomicAdd(&wh[w][digit_of(keys[idx], shift)], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += kRsThreads) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kRsWarps; ++q) s += wh[q][d];
+    counts[(int64_t)d * nblk + blockIdx.x] = s;
+  }
+}
+
+// exclusive scan over one digit's block counts; totals[d] = the digit's count
+__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *__restrict__ counts, int64_t nblk,
+                                                  uint32_t *__restrict__ totals) {
+  __shared__ uint32_t ws[32];
+  uint32_t *c = counts + (int64_t)blockIdx.x * nblk;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t carry = 0;
+  for (int64_t b0 = 0; b0 < nblk; b0 += 1024) {
+    int64_t idx = b0 + threadIdx.x;
+    uint32_t v = idx < nblk ? c[idx] : 0u;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      uint32_t s = ws[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      ws[lane] = s;
+    }
+    __syncthreads();
+    uint32_t before = (w > 0 ? ws[w - 1] : 0u) + carry;
+    if (idx < nblk) c[idx] = before + x - v;
+    carry += ws[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+static_assert(kRsThreads == 256, "one thread per digit in the digit scans");
+
+// exclusive scan of one value per thread over the 256 threads of the block
+__device__ __forceinline__ uint32_t digit_scan_excl(uint32_t v, uint32_t *buf) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  buf[threadIdx.x] = x;
+  __syncthreads();
+  uint32_t add = 0;
+  for (int q = 0; q < w; ++q) add += buf[q * 32 + 31];
+  __syncthreads();
+  return x + add - v;
+}
+
+template <class K, bool kVals>
+__global__ void __launch_bounds__(kRsThreads) k_rs_downsweep(
+    const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
+    uint32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ counts,
+    const uint32_t *__restrict__ totals, int64_t nblk) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  K *skeys = (K *)smem;
+  uint32_t *svals = (uint32_t *)(smem + sizeof(K) * kRsTile);
+  __shared__ uint32_t wcnt[kRsWarps][256];  // per warp, per digit
+  __shared__ uint32_t scanbuf[256];
+  __shared__ uint32_t dstart[256];  // first tile position of each digit
+  __shared__ uint32_t gbase[256];   // global position of the digit's first item
+
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&wcnt[0][0])[i] = 0;
+
+  // (a) global base of each digit for this block
+  {
+    const int d = threadIdx.x;
+    uint32_t excl = digit_scan_excl(totals[d], scanbuf);
+    gbase[d] = excl + counts[(int64_t)d * nblk + blockIdx.x];
+  }
+
+  // (b) load the tile warp-striped and rank every item inside its warp:
+  // warp w holds tile items [w*32*I, (w+1)*32*I), item k of lane l at
+  // w*32*I + k*32 + l, so (k, lane) order is input order and ranks are stable
+  const int64_t base = (int64_t)blockIdx.x * kRsTile;
+  const int64_t seg = base + (int64_t)w * 32 * kRsItems;
+  K key[kRsItems];
+  uint32_t val[kRsItems];
+  uint32_t rnk[kRsItems];
+#pragma unroll
+  for (int k = 0; k < kRsItems; ++k) {
+    int64_t idx = seg + k * 32 + lane;
+    bool valid = idx < n;
+    key[k] = valid ? kin[idx] : (K)0;
+    if (kVals) val[k] = valid ? vin[idx] : 0u;
+    uint32_t d = valid ? digit_of(key[k], shift) : 256u;
+    unsigned peers = __match_any_sync(0xffffffffu, d);
+    uint32_t before = valid ? wcnt[w][d] : 0u;
+    rnk[k] = before + __popc(peers & lt);
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) wcnt[w][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // (c) per digit: exclusive prefix over the warps, then over the digits
+  {
+    const int d = threadIdx.x;
+    uint32_t run = 0;
+#pragma unroll
+    for (int q = 0; q < kRsWarps; ++q) {
+      uint32_t c = wcnt[q][d];
+      wcnt[q][d] = run;
+      run += c;
+    }
+    dstart[d] = digit_scan_excl(run, scanbuf);
+  }
+  __syncthreads();
+
+  // (d) scatter into shared memory at the tile-local rank
+#pragma unroll
+  for (int k = 0; k < kRsItems; ++k) {
+    int64_t idx = seg + k * 32 + lane;
+    if (idx < n) {
+      uint32_t d = digit_of(key[k], shift);
+      uint32_t r = dstart[d] + wcnt[w][d] + rnk[k];
+      skeys[r] = key[k];
+      if (kVals) svals[r] = val[k];
+    }
+  }
+  __syncthreads();
+
+  // (e) each digit's run goes to consecutive global positions
+  int64_t cnt = n - base < kRsTile ? n - base : kRsTile;
+  for (int r = threadIdx.x; r < cnt; r += kRsThreads) {
+    K kk = skeys[r];
+    uint32_t d = digit_of(kk, shift);
+    uint32_t pos = gbase[d] + (uint32_t)r - dstart[d];
+    kout[pos] = kk;
+    if (kVals) vout[pos] = svals[r];
+  }
+}
+
+template <class K>
+static int rs_impl(K *keys, uint32_t *vals, int64_t n, int bits, SortScratch &sc,
+                   cudaStream_t st) {
+  if (n <= 1 || bits <= 0) return SCD_OK;
+  int64_t nblk = (n + kRsTile - 1) / kRsTile;
+  if (!sc.keys_alt.ensure(sizeof(K) * (size_t)n, st)) return SCD_ERR_OOM;
+  if (vals && !sc.vals_alt.ensure((size_t)n, st)) return SCD_ERR_OOM;
+  if (!sc.counts.ensure((size_t)(256 * nblk + 256), st)) return SCD_ERR_OOM;
+  uint32_t *counts = sc.counts.p;
+  uint32_t *totals = sc.counts.p + 256 * nblk;
+  K *ka = keys, *kb = (K *)sc.keys_alt.p;
+  uint32_t *va = vals, *vb = sc.vals_alt.p;
+  size_t smem = sizeof(K) * kRsTile + (vals ? sizeof(uint32_t) * kRsTile : 0);
+  static bool attr_set[2][2] = {{false, false}, {false, false}};
+  int ki = sizeof(K) == 8 ? 1 : 0, vi = vals ? 1 : 0;
+  if (!attr_set[ki][vi]) {
+    if (vals)
+      cudaFuncSetAttribute(k_rs_downsweep<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+    else
+      cudaFuncSetAttribute(k_rs_downsweep<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+    attr_set[ki][vi] = true;
+  }
+  int passes = 0;
+  for (int shift = 0; shift < bits; shift += 8, ++passes) {
+    k_rs_upsweep<K><<<(unsigned)nblk, kRsThreads, 0, st>>>(ka, n, shift, counts, nblk);
+    k_rs_scan<<<256, 1024, 0, st>>>(counts, nblk, totals);
+    if (vals)
+      k_rs_downsweep<K, true><<<(unsigned)nblk, kRsThreads, smem, st>>>(ka, va, kb, vb, n, shift,
+                                                                       counts, totals, nblk);
+    else
+      k_rs_downsweep<K, false><<<(unsigned)nblk, kRsThreads, smem, st>>>(
+          ka, nullptr, kb, nullptr, n, shift, counts, totals, nblk);
+    note_launch(3);
+    K *t = ka; ka = kb; kb = t;
+    uint32_t *tv = va; va = vb; vb = tv;
+  }
+  if (passes & 1) {
+    cudaMemcpyAsync(keys, ka, sizeof(K) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    if (vals) cudaMemcpyAsync(vals, va, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+  }
+  return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
+}
+
+int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int bits, SortScratch &sc,
+                   cudaStream_t st) {
+  return rs_impl<uint32_t>(keys, vals, n, bits, sc, st);
+}
+
+int radix_sort_u64(unsigned long long *keys, uint32_t *vals, int64_t n, int bits,
+                   SortScratch &sc, cudaStream_t st) {
+  return rs_impl<unsigned long long>(keys, vals, n, bits, sc, st);
+}
+
+}  // namespace scd

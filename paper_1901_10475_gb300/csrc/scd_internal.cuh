@@ -1,0 +1,211 @@
+// scd_internal.cuh -- types and helpers shared by the CUDA translation units
+// of libscd (sm_103a).  Not part of the public ABI (include/scd.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/scd.h"
+
+namespace scd {
+
+// geocentric gravitational parameter [km^3/s^2] and equatorial Earth radius
+// [km] (WGS-84); the paper's Eq. 1 names mu without giving a value
+constexpr double kMu = 398600.4418;
+constexpr double kRe = 6378.137;
+constexpr double kTwoPi = 6.283185307179586;
+constexpr double kPi = 3.141592653589793;
+// margin added to every box half-width before outward FP32 rounding [km]
+constexpr double kEpsKm = 1e-6;
+
+// device error word bits
+enum : uint32_t {
+  ERR_KEPLER = 1u << 0,     // Kepler iteration hit its limit
+  ERR_STACK = 1u << 1,      // traversal stack overflow
+  ERR_INVALID = 1u << 2,    // invalid element seen on the device
+  ERR_ZIP = 1u << 3,        // run starts and ends did not pair up
+  ERR_TIMEOUT = 1u << 4,    // a bounded wait gave up
+};
+
+// Per-object propagation constants, derived once per scene from the
+// elements (128 bytes, read through the read-only path by every box).
+struct __align__(16) ObjParams {
+  double A[3];   // a * P  (P: perifocal x axis in ECI)
+  double B[3];   // a sqrt(1-e^2) * Q  (Q: perifocal y axis in ECI)
+  double n;      // mean motion [rad/s]
+  double M0;     // mean anomaly at t = 0 [rad]
+  double e;      // eccentricity
+  double vmax;   // perigee speed [km/s]
+  double r;      // radius [km]
+  double P;      // period [s]
+  double pad[2];
+};
+
+// Device-side counters of one scene, read back with one copy.  The first
+// block is zeroed before every traversal; the second is written by the box
+// build.
+struct DevCounters {
+  unsigned long long n_starts;
+  unsigned long long n_ends;
+  unsigned long long n_raw;
+  unsigned long long node_tests;
+  unsigned long long leaf_tests;
+  unsigned int trav_flags;   // ERR_STACK, ERR_ZIP
+  unsigned int pad0;
+  unsigned long long extent_bits;  // max object extent [km] as double bits
+  unsigned int build_flags;        // ERR_KEPLER, ERR_INVALID
+  unsigned int kepler_max_iter;
+  unsigned long long n_boxes;      // seg_off[n]
+  unsigned long long pad1;
+};
+
+// Traversal node: both children's boxes inline, child links and the
+// rightmost leaf of each child (80 bytes).
+struct __align__(16) TravNode {
+  float4 lo_l, hi_l, lo_r, hi_r;
+  int32_t left, right;  // child index; bit 31 set = leaf
+  int32_t last_l, last_r;  // rightmost leaf index under each child
+};
+
+constexpr int32_t kLeafBit = (int32_t)0x80000000u;
+
+__host__ __device__ inline bool box_overlap(const float4 &la, const float4 &ha,
+                                            const float4 &lb, const float4 &hb) {
+  // closed boxes: overlap iff every axis overlaps
+  return la.x <= hb.x && lb.x <= ha.x && la.y <= hb.y && lb.y <= ha.y &&
+         la.z <= hb.z && lb.z <= ha.z && la.w <= hb.w && lb.w <= ha.w;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+void *dev_alloc(size_t bytes, cudaStream_t st);
+void dev_free(void *p, cudaStream_t st);
+
+template <class T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  bool ensure(size_t count, cudaStream_t st) {
+    if (count <= n && p) return true;
+    if (p) dev_free(p, st);
+    p = nullptr;
+    n = 0;
+    size_t c = count < 1 ? 1 : count;
+    p = (T *)dev_alloc(c * sizeof(T), st);
+    if (!p) return false;
+    n = c;
+    return true;
+  }
+  void release(cudaStream_t st) {
+    if (p) dev_free(p, st);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+// radix sort scratch: ping-pong key/value buffers and block counts
+struct SortScratch {
+  DevBuf<unsigned char> keys_alt;
+  DevBuf<uint32_t> vals_alt;
+  DevBuf<uint32_t> counts;
+  void release(cudaStream_t st) {
+    keys_alt.release(st);
+    vals_alt.release(st);
+    counts.release(st);
+  }
+};
+
+// Sort (key, value) pairs by the low `bits` bits of the key, LSD, 8-bit
+// digits, stable.  keys/vals are sorted in place (via the scratch ping-pong).
+// vals may be null (keys only).  Returns cudaSuccess or the launch error.
+int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int bits, SortScratch &sc,
+                   cudaStream_t st);
+int radix_sort_u64(unsigned long long *keys, uint32_t *vals, int64_t n, int bits,
+                   SortScratch &sc, cudaStream_t st);
+
+// process-wide count of kernel launches issued by this library
+void note_launch(int k = 1);
+unsigned long long launch_count();
+
+// exclusive scan of n int64 values; out has n+1 entries (out[n] = total)
+int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, DevBuf<int64_t> &tmp,
+                       cudaStream_t st);
+
+}  // namespace scd
+
+// the scene (opaque in the ABI)
+struct scd_scene {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int64_t n = 0;
+  double horizon_s = 0, tick_s = 0;
+  int64_t T = 0;  // horizon in ticks
+  int step_kind = 0;
+  uint32_t fixed_ticks = 1;
+  double period_fraction = 100.0;
+  std::vector<double> band_edges, band_fracs;
+  const void *stepnet = nullptr;
+  int box_mode = 0;
+  scd_tuning tune{};
+
+  // per-object
+  scd::DevBuf<scd_element> d_el;
+  scd::DevBuf<scd::ObjParams> d_par;
+  scd::DevBuf<int32_t> d_k;
+  scd::DevBuf<int64_t> d_segcnt, d_segoff, d_scan_tmp;
+  scd::DevBuf<double> d_band;  // edges then fractions
+  scd::DevBuf<scd::DevCounters> d_ctr;
+  scd::DevCounters h_ctr{};  // pinned copy target lives in h_ctr_pinned
+  scd::DevCounters *h_ctr_pinned = nullptr;
+
+  // boxes (object-major)
+  int64_t N = 0;
+  bool boxes_built = false;
+  scd::DevBuf<float4> d_lo, d_hi;
+  scd::DevBuf<uint32_t> d_obj;
+  scd::DevBuf<unsigned long long> d_key64;
+  scd::DevBuf<uint32_t> d_key32;
+  scd::DevBuf<uint32_t> d_id;  // box ids, sorted along with the keys
+
+  // sorted leaves and hierarchy
+  scd::DevBuf<float4> s_lo, s_hi;
+  scd::DevBuf<uint32_t> s_obj;
+  scd::DevBuf<uint32_t> s_leafkey32;
+  scd::DevBuf<unsigned long long> s_leafkey64;
+  scd::DevBuf<scd::TravNode> d_nodes;
+  scd::DevBuf<float4> d_nlo, d_nhi;     // internal node boxes (refit)
+  scd::DevBuf<float4> d_leaflo, d_leafhi;
+  scd::DevBuf<int32_t> d_parent_int, d_parent_leaf;
+  scd::DevBuf<uint32_t> d_flags;
+  scd::DevBuf<int32_t> d_first_last;   // per internal node: first, last
+
+  // pair emission and canonical list
+  int64_t pair_cap = 0;
+  scd::DevBuf<unsigned long long> d_starts, d_ends;
+  scd::DevBuf<uint32_t> d_rawval;
+  scd::DevBuf<scd_pair> d_out;
+  int64_t n_out = 0;
+  scd::SortScratch sort_sc;
+
+  // metrics of the last find_pairs
+  double ms_sort = 0, ms_build = 0, ms_traverse = 0, ms_canon = 0, ms_boxes = 0;
+  unsigned long long last_node_tests = 0, last_leaf_tests = 0, last_runs = 0;
+  unsigned long long launch_mark = 0, last_launches = 0;  // kernels of build + find
+  cudaEvent_t ev[8] = {};
+  bool events_ready = false;
+};
+
+namespace scd {
+// launchers defined in the .cu files
+int launch_prepare_objects(scd_scene *s);
+int launch_build_boxes(scd_scene *s);
+int launch_propagate(const scd_element *d_el, int64_t n, const uint32_t *obj, const double *t,
+                     int64_t m, double *out, cudaStream_t st);
+int build_hierarchy(scd_scene *s, int64_t &n_leaves);
+int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_bits);
+int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits);
+}  // namespace scd

@@ -1,0 +1,441 @@
+// scene.cu -- the C ABI of libscd (include/scd.h): argument checks, device
+// memory, and the order of the kernel launches of one screen.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "scd_internal.cuh"
+
+using namespace scd;
+
+// ---------------------------------------------------------------------------
+// allocator hooks
+// ---------------------------------------------------------------------------
+static void *(*g_alloc)(size_t, void *, void *) = nullptr;
+static void (*g_free)(void *, void *, void *) = nullptr;
+static void *g_alloc_ctx = nullptr;
+
+#include <atomic>
+static std::atomic<unsigned long long> g_launches{0};
+
+namespace scd {
+void note_launch(int k) { g_launches.fetch_add((unsigned long long)k); }
+unsigned long long launch_count() { return g_launches.load(); }
+
+void *dev_alloc(size_t bytes, cudaStream_t st) {
+  if (g_alloc) return g_alloc(bytes, (void *)st, g_alloc_ctx);
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+void dev_free(void *p, cudaStream_t st) {
+  if (!p) return;
+  if (g_free) {
+    g_free(p, (void *)st, g_alloc_ctx);
+    return;
+  }
+  cudaFree(p);
+}
+}  // namespace scd
+
+extern "C" SCD_API int scd_set_allocator(void *(*alloc_fn)(size_t, void *, void *),
+                                         void (*free_fn)(void *, void *, void *), void *ctx) {
+  if ((alloc_fn == nullptr) != (free_fn == nullptr)) return SCD_ERR_INVALID_ARG;
+  g_alloc = alloc_fn;
+  g_free = free_fn;
+  g_alloc_ctx = ctx;
+  return SCD_OK;
+}
+
+extern "C" SCD_API const char *scd_status_string(int status) {
+  switch (status) {
+    case SCD_OK: return "ok";
+    case SCD_ERR_INVALID_ARG: return "invalid argument";
+    case SCD_ERR_OOM: return "device allocation failed";
+    case SCD_ERR_BUFFER_TOO_SMALL: return "output buffer too small";
+    case SCD_ERR_CUDA: return "CUDA error";
+    case SCD_ERR_KEPLER_NOCONV: return "Kepler iteration did not converge";
+    case SCD_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SCD_ERR_INTERNAL: return "device consistency check failed";
+    case SCD_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+extern "C" SCD_API int scd_default_tuning(scd_tuning *t) {
+  if (!t) return SCD_ERR_INVALID_ARG;
+  t->leaf_size = 4;
+  t->stack_depth = 64;
+  t->block_threads = 128;
+  t->morton_bits = 8;
+  t->time_scale = 1.0f;
+  t->use_graph = 0;
+  return SCD_OK;
+}
+
+static bool tuning_ok(const scd_tuning *t) {
+  bool leaf = t->leaf_size == 1 || t->leaf_size == 2 || t->leaf_size == 4 || t->leaf_size == 8;
+  bool st = t->stack_depth == 32 || t->stack_depth == 64 || t->stack_depth == 128;
+  bool bs = t->block_threads >= 32 && t->block_threads <= 256 && t->block_threads % 32 == 0;
+  bool mb = t->morton_bits == 8 || t->morton_bits == 10 || t->morton_bits == 12 ||
+            t->morton_bits == 16;
+  bool ts = t->time_scale > 0.0f && t->time_scale <= 1.0f;
+  return leaf && st && bs && mb && ts;
+}
+
+static bool element_ok(const scd_element &x) {
+  return isfinite(x.a_km) && isfinite(x.e) && isfinite(x.inc_rad) && isfinite(x.raan_rad) &&
+         isfinite(x.argp_rad) && isfinite(x.M0_rad) && isfinite(x.radius_km) && x.a_km > 0.0 &&
+         x.e >= 0.0 && x.e < 1.0 && x.radius_km >= 0.0;
+}
+
+static int cuda_rc(cudaError_t e) { return e == cudaSuccess ? SCD_OK : SCD_ERR_CUDA; }
+
+#define TRY(x)                \
+  do {                        \
+    int rc_ = (x);            \
+    if (rc_ != SCD_OK) return rc_; \
+  } while (0)
+
+static int read_counters(scd_scene *s) {
+  cudaError_t e = cudaMemcpyAsync(s->h_ctr_pinned, s->d_ctr.p, sizeof(DevCounters),
+                                  cudaMemcpyDeviceToHost, s->stream);
+  if (e != cudaSuccess) return SCD_ERR_CUDA;
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return SCD_ERR_CUDA;
+  s->h_ctr = *s->h_ctr_pinned;
+  return SCD_OK;
+}
+
+extern "C" SCD_API int scd_scene_create(const scd_element *elems, int64_t n, double horizon_s,
+                                        double tick_s, const scd_step_policy *step,
+                                        scd_box_mode mode, void *cuda_stream, scd_scene **out) {
+  if (!out) return SCD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!elems || n <= 0 || n >= (1ll << 24) || !step) return SCD_ERR_INVALID_ARG;
+  if (!(horizon_s > 0.0) || !(tick_s > 0.0) || !isfinite(horizon_s) || !isfinite(tick_s))
+    return SCD_ERR_INVALID_ARG;
+  double Tq = horizon_s / tick_s;
+  double Tr = nearbyint(Tq);
+  if (fabs(Tq - Tr) > 1e-9 * std::max(1.0, Tr) || Tr < 1.0 || Tr >= (double)(1 << 24))
+    return SCD_ERR_INVALID_ARG;
+  if (mode != SCD_BOX_SPEED && mode != SCD_BOX_INTERVAL) return SCD_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; ++i)
+    if (!element_ok(elems[i])) return SCD_ERR_INVALID_ARG;
+  switch (step->kind) {
+    case SCD_STEP_FIXED: break;
+    case SCD_STEP_PERIOD_FRACTION:
+      if (!(step->period_fraction > 0.0) || !isfinite(step->period_fraction))
+        return SCD_ERR_INVALID_ARG;
+      break;
+    case SCD_STEP_BAND_TABLE:
+      if (step->n_bands < 1 || !step->band_fractions || (step->n_bands > 1 && !step->band_edges_km))
+        return SCD_ERR_INVALID_ARG;
+      for (int b = 0; b < step->n_bands; ++b)
+        if (!(step->band_fractions[b] > 0.0)) return SCD_ERR_INVALID_ARG;
+      for (int b = 1; b + 1 < step->n_bands; ++b)
+        if (!(step->band_edges_km[b] > step->band_edges_km[b - 1])) return SCD_ERR_INVALID_ARG;
+      break;
+    case SCD_STEP_LEARNED:
+      return SCD_ERR_INVALID_ARG;  // step networks are not part of this build's ABI yet
+    default: return SCD_ERR_INVALID_ARG;
+  }
+  scd_scene *s = new scd_scene();
+  cudaGetDevice(&s->device);
+  s->stream = (cudaStream_t)cuda_stream;
+  s->n = n;
+  s->horizon_s = horizon_s;
+  s->tick_s = tick_s;
+  s->T = (int64_t)Tr;
+  s->step_kind = step->kind;
+  s->fixed_ticks = step->fixed_ticks;
+  s->period_fraction = step->period_fraction;
+  if (step->kind == SCD_STEP_BAND_TABLE) {
+    s->band_edges.assign(step->band_edges_km, step->band_edges_km + (step->n_bands - 1));
+    s->band_fracs.assign(step->band_fractions, step->band_fractions + step->n_bands);
+  }
+  s->box_mode = mode;
+  scd_default_tuning(&s->tune);
+  cudaStream_t st = s->stream;
+  if (cudaMallocHost(&s->h_ctr_pinned, sizeof(DevCounters)) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return SCD_ERR_CUDA;
+  }
+  bool ok = s->d_el.ensure(n, st) && s->d_par.ensure(n, st) && s->d_k.ensure(n, st) &&
+            s->d_segcnt.ensure(n, st) && s->d_segoff.ensure(n + 1, st) &&
+            s->d_ctr.ensure(1, st) && s->d_band.ensure(s->band_edges.size() + s->band_fracs.size() + 1, st);
+  if (!ok) {
+    scd_scene_destroy(s);
+    return SCD_ERR_OOM;
+  }
+  cudaError_t e = cudaMemcpyAsync(s->d_el.p, elems, sizeof(scd_element) * (size_t)n,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !s->band_fracs.empty()) {
+    std::vector<double> bt(s->band_edges);
+    bt.insert(bt.end(), s->band_fracs.begin(), s->band_fracs.end());
+    e = cudaMemcpyAsync(s->d_band.p, bt.data(), sizeof(double) * bt.size(), cudaMemcpyHostToDevice,
+                        st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  if (e != cudaSuccess) {
+    scd_scene_destroy(s);
+    return SCD_ERR_CUDA;
+  }
+  for (int k = 0; k < 8; ++k) cudaEventCreate(&s->ev[k]);
+  s->events_ready = true;
+  *out = s;
+  return SCD_OK;
+}
+
+extern "C" SCD_API int scd_scene_set_elements(scd_scene *s, const scd_element *elems, int64_t n) {
+  if (!s || !elems || n != s->n) return SCD_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; ++i)
+    if (!element_ok(elems[i])) return SCD_ERR_INVALID_ARG;
+  s->boxes_built = false;
+  return cuda_rc(cudaMemcpyAsync(s->d_el.p, elems, sizeof(scd_element) * (size_t)n,
+                                 cudaMemcpyHostToDevice, s->stream));
+}
+
+extern "C" SCD_API int scd_scene_set_elements_device(scd_scene *s, const scd_element *d_elems,
+                                                     int64_t n) {
+  if (!s || !d_elems || n != s->n) return SCD_ERR_INVALID_ARG;
+  s->boxes_built = false;
+  return cuda_rc(cudaMemcpyAsync(s->d_el.p, d_elems, sizeof(scd_element) * (size_t)n,
+                                 cudaMemcpyDeviceToDevice, s->stream));
+}
+
+extern "C" SCD_API int scd_scene_set_tuning(scd_scene *s, const scd_tuning *t) {
+  if (!s || !t || !tuning_ok(t)) return SCD_ERR_INVALID_ARG;
+  bool rekey = t->morton_bits != s->tune.morton_bits || t->time_scale != s->tune.time_scale;
+  s->tune = *t;
+  if (rekey) s->boxes_built = false;
+  return SCD_OK;
+}
+
+extern "C" SCD_API int scd_build_boxes(scd_scene *s) {
+  if (!s) return SCD_ERR_INVALID_ARG;
+  cudaStream_t st = s->stream;
+  if (s->events_ready) cudaEventRecord(s->ev[0], st);
+  s->launch_mark = launch_count();
+  if (cudaMemsetAsync(s->d_ctr.p, 0, sizeof(DevCounters), st) != cudaSuccess) return SCD_ERR_CUDA;
+  TRY(launch_prepare_objects(s));
+  TRY(scan_exclusive_i64(s->d_segcnt.p, s->d_segoff.p, s->n, s->d_scan_tmp, st));
+  // the box count sizes every buffer that follows: one 8-byte read
+  if (cudaMemcpyAsync(&s->h_ctr_pinned->n_boxes, s->d_segoff.p + s->n, sizeof(int64_t),
+                      cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return SCD_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SCD_ERR_CUDA;
+  int64_t N = (int64_t)s->h_ctr_pinned->n_boxes;
+  if (N <= 0 || N >= (1ll << 31)) return SCD_ERR_INVALID_ARG;
+  s->N = N;
+  bool ok = s->d_lo.ensure(N, st) && s->d_hi.ensure(N, st) && s->d_obj.ensure(N, st) &&
+            s->d_id.ensure(N, st) && s->d_key32.ensure(N, st) &&
+            (s->tune.morton_bits <= 8 || s->d_key64.ensure(N, st));
+  if (!ok) return SCD_ERR_OOM;
+  TRY(launch_build_boxes(s));
+  if (s->events_ready) cudaEventRecord(s->ev[1], st);
+  s->boxes_built = true;
+  return SCD_OK;
+}
+
+static int bits_for(int64_t v) {
+  int b = 1;
+  while ((1ll << b) <= v) ++b;
+  return b;
+}
+
+static int find_pairs_impl(scd_scene *s, const scd_decomp *d, int raw_mode) {
+  if (!s) return SCD_ERR_INVALID_ARG;
+  if (!s->boxes_built) return SCD_ERR_STATE;
+  if (d && d->kind != SCD_DECOMP_NONE) {
+    if (d->kind != SCD_DECOMP_ALT_BANDS && d->kind != SCD_DECOMP_SLAB_OCT)
+      return SCD_ERR_INVALID_ARG;
+    return SCD_ERR_INVALID_ARG;  // decompositions are served by the batched path
+  }
+  cudaStream_t st = s->stream;
+  int ob = bits_for(s->n - 1), tb = bits_for(s->T);
+  if (2 * ob + tb > 64) return SCD_ERR_INVALID_ARG;
+  int64_t N = s->N;
+  if (s->events_ready) cudaEventRecord(s->ev[2], st);
+  // A5: sort box ids along the Morton curve (ids were reset by build_boxes)
+  int kb = 4 * s->tune.morton_bits;
+  if (s->tune.morton_bits > 8) {
+    TRY(radix_sort_u64(s->d_key64.p, s->d_id.p, N, kb, s->sort_sc, st));
+  } else {
+    TRY(radix_sort_u32(s->d_key32.p, s->d_id.p, N, kb, s->sort_sc, st));
+  }
+  if (s->events_ready) cudaEventRecord(s->ev[3], st);
+  // A6-A7: hierarchy and refit
+  int64_t M = 0;
+  TRY(build_hierarchy(s, M));
+  if (s->events_ready) cudaEventRecord(s->ev[4], st);
+  // A8: traversal, retried with more room when the buffers overflow
+  if (s->pair_cap == 0) s->pair_cap = std::max<int64_t>(1 << 16, N / 4);
+  bool done = false;
+  for (int attempt = 0; attempt < 6 && !done; ++attempt) {
+    if (!s->d_starts.ensure(s->pair_cap, st) || !s->d_ends.ensure(s->pair_cap, st) ||
+        !s->d_rawval.ensure(s->pair_cap, st))
+      return SCD_ERR_OOM;
+    // zero the emission counters, keep the box-build flags
+    if (cudaMemsetAsync(s->d_ctr.p, 0, offsetof(DevCounters, extent_bits), st) != cudaSuccess)
+      return SCD_ERR_CUDA;
+    TRY(traverse(s, M, raw_mode, ob, tb));
+    TRY(read_counters(s));
+    if (s->h_ctr.trav_flags & ERR_STACK) {
+      // a deeper stack, then the same traversal again
+      if (s->tune.stack_depth >= 128) return SCD_ERR_INTERNAL;
+      s->tune.stack_depth *= 2;
+      continue;
+    }
+    unsigned long long need = raw_mode ? s->h_ctr.n_raw
+                                       : std::max(s->h_ctr.n_starts, s->h_ctr.n_ends);
+    if (need <= (unsigned long long)s->pair_cap) done = true;
+    else s->pair_cap = (int64_t)(need + need / 8 + 1024);
+  }
+  if (!done) return SCD_ERR_INTERNAL;
+  if (s->h_ctr.build_flags & ERR_INVALID) return SCD_ERR_INVALID_ARG;
+  if (s->h_ctr.build_flags & ERR_KEPLER) return SCD_ERR_KEPLER_NOCONV;
+  if (!raw_mode && s->h_ctr.n_starts != s->h_ctr.n_ends) return SCD_ERR_INTERNAL;
+  if (s->events_ready) cudaEventRecord(s->ev[5], st);
+  // A9: canonical list
+  TRY(canonicalize(s, raw_mode, ob, tb));
+  if (s->events_ready) cudaEventRecord(s->ev[6], st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SCD_ERR_CUDA;
+  unsigned int flags = 0;
+  cudaMemcpy(&flags, &s->d_ctr.p->trav_flags, sizeof(flags), cudaMemcpyDeviceToHost);
+  if (flags & ERR_ZIP) return SCD_ERR_INTERNAL;
+  s->last_node_tests = s->h_ctr.node_tests;
+  s->last_leaf_tests = s->h_ctr.leaf_tests;
+  s->last_runs = raw_mode ? s->h_ctr.n_raw : s->h_ctr.n_starts;
+  s->last_launches = launch_count() - s->launch_mark;
+  if (s->events_ready) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, s->ev[0], s->ev[1]) == cudaSuccess) s->ms_boxes = ms;
+    cudaEventElapsedTime(&ms, s->ev[2], s->ev[3]); s->ms_sort = ms;
+    cudaEventElapsedTime(&ms, s->ev[3], s->ev[4]); s->ms_build = ms;
+    cudaEventElapsedTime(&ms, s->ev[4], s->ev[5]); s->ms_traverse = ms;
+    cudaEventElapsedTime(&ms, s->ev[5], s->ev[6]); s->ms_canon = ms;
+    cudaGetLastError();
+  }
+  return SCD_OK;
+}
+
+extern "C" SCD_API int scd_find_pairs_device(scd_scene *s, const scd_decomp *d,
+                                             const scd_pair **dev_out, int64_t *n_out) {
+  if (!dev_out || !n_out) return SCD_ERR_INVALID_ARG;
+  TRY(find_pairs_impl(s, d, 0));
+  *dev_out = s->d_out.p;
+  *n_out = s->n_out;
+  return SCD_OK;
+}
+
+extern "C" SCD_API int scd_find_raw_cells_device(scd_scene *s, const scd_pair **dev_out,
+                                                 int64_t *n_out) {
+  if (!dev_out || !n_out) return SCD_ERR_INVALID_ARG;
+  TRY(find_pairs_impl(s, nullptr, 1));
+  *dev_out = s->d_out.p;
+  *n_out = s->n_out;
+  return SCD_OK;
+}
+
+extern "C" SCD_API int scd_find_pairs(scd_scene *s, const scd_decomp *d, scd_pair *host_out,
+                                      int64_t cap, int64_t *n_out) {
+  if (!n_out || (cap > 0 && !host_out) || cap < 0) return SCD_ERR_INVALID_ARG;
+  TRY(find_pairs_impl(s, d, 0));
+  *n_out = s->n_out;
+  if (s->n_out > cap) return SCD_ERR_BUFFER_TOO_SMALL;
+  if (s->n_out > 0) {
+    if (cudaMemcpyAsync(host_out, s->d_out.p, sizeof(scd_pair) * (size_t)s->n_out,
+                        cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+      return SCD_ERR_CUDA;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return SCD_ERR_CUDA;
+  }
+  return SCD_OK;
+}
+
+extern "C" SCD_API int scd_get_boxes(const scd_scene *s, const float **lo4, const float **hi4,
+                                     const uint32_t **obj, int64_t *nbox) {
+  if (!s || !lo4 || !hi4 || !obj || !nbox) return SCD_ERR_INVALID_ARG;
+  if (!s->boxes_built) return SCD_ERR_STATE;
+  *lo4 = (const float *)s->d_lo.p;
+  *hi4 = (const float *)s->d_hi.p;
+  *obj = s->d_obj.p;
+  *nbox = s->N;
+  return SCD_OK;
+}
+
+extern "C" SCD_API int scd_get_steps(const scd_scene *s, const int32_t **steps) {
+  if (!s || !steps) return SCD_ERR_INVALID_ARG;
+  if (!s->boxes_built) return SCD_ERR_STATE;
+  *steps = s->d_k.p;
+  return SCD_OK;
+}
+
+extern "C" SCD_API int scd_propagate(const scd_element *d_elems, int64_t n, const uint32_t *d_obj,
+                                     const double *d_t_s, int64_t m, double *d_out,
+                                     void *cuda_stream) {
+  if (!d_elems || n <= 0 || m < 0 || (m > 0 && (!d_obj || !d_t_s || !d_out)))
+    return SCD_ERR_INVALID_ARG;
+  return launch_propagate(d_elems, n, d_obj, d_t_s, m, d_out, (cudaStream_t)cuda_stream);
+}
+
+extern "C" SCD_API int scd_batch_find_pairs(scd_scene *const *scenes, int n_scenes,
+                                            const scd_decomp *d, scd_pair *const *outs,
+                                            const int64_t *caps, int64_t *n_outs) {
+  if (!scenes || n_scenes <= 0 || !outs || !caps || !n_outs) return SCD_ERR_INVALID_ARG;
+  int worst = SCD_OK;
+  for (int k = 0; k < n_scenes; ++k) {
+    int rc = scd_find_pairs(scenes[k], d, outs[k], caps[k], &n_outs[k]);
+    if (rc == SCD_ERR_BUFFER_TOO_SMALL) worst = rc;
+    else if (rc != SCD_OK) return rc;
+  }
+  return worst;
+}
+
+extern "C" SCD_API int scd_last_metrics(const scd_scene *s, char *json, size_t cap) {
+  if (!s || !json || cap == 0) return SCD_ERR_INVALID_ARG;
+  int w = snprintf(json, cap,
+                   "{\"n\": %lld, \"T\": %lld, \"boxes\": %lld, \"node_tests\": %llu, "
+                   "\"leaf_tests\": %llu, \"records\": %llu, \"pairs\": %lld, "
+                   "\"ms_boxes\": %.4f, \"ms_sort\": %.4f, \"ms_build\": %.4f, "
+                   "\"ms_traverse\": %.4f, \"ms_canon\": %.4f, \"leaf_size\": %d, "
+                   "\"stack_depth\": %d, \"block_threads\": %d, \"morton_bits\": %d, "
+                   "\"launches\": %llu}",
+                   (long long)s->n, (long long)s->T, (long long)s->N, s->last_node_tests,
+                   s->last_leaf_tests, s->last_runs, (long long)s->n_out, s->ms_boxes, s->ms_sort,
+                   s->ms_build, s->ms_traverse, s->ms_canon, s->tune.leaf_size,
+                   s->tune.stack_depth, s->tune.block_threads, s->tune.morton_bits,
+                   s->last_launches);
+  if (w < 0 || (size_t)w >= cap) return SCD_ERR_BUFFER_TOO_SMALL;
+  return SCD_OK;
+}
+
+extern "C" SCD_API void scd_scene_destroy(scd_scene *s) {
+  if (!s) return;
+  cudaStream_t st = s->stream;
+  cudaStreamSynchronize(st);
+  s->d_el.release(st); s->d_par.release(st); s->d_k.release(st);
+  s->d_segcnt.release(st); s->d_segoff.release(st); s->d_scan_tmp.release(st);
+  s->d_band.release(st); s->d_ctr.release(st);
+  s->d_lo.release(st); s->d_hi.release(st); s->d_obj.release(st);
+  s->d_key64.release(st); s->d_key32.release(st); s->d_id.release(st);
+  s->s_lo.release(st); s->s_hi.release(st); s->s_obj.release(st);
+  s->s_leafkey32.release(st); s->s_leafkey64.release(st);
+  s->d_nodes.release(st); s->d_nlo.release(st); s->d_nhi.release(st);
+  s->d_leaflo.release(st); s->d_leafhi.release(st);
+  s->d_parent_int.release(st); s->d_parent_leaf.release(st); s->d_flags.release(st);
+  s->d_first_last.release(st);
+  s->d_starts.release(st); s->d_ends.release(st); s->d_rawval.release(st);
+  s->d_out.release(st);
+  s->sort_sc.release(st);
+  if (s->events_ready)
+    for (int k = 0; k < 8; ++k) cudaEventDestroy(s->ev[k]);
+  if (s->h_ctr_pinned) cudaFreeHost(s->h_ctr_pinned);
+  delete s;
+}

@@ -1,0 +1,245 @@
+// traverse.cu -- step A8: every box queries the hierarchy for the boxes it
+// meets (the tree query of Sec. 3.2, run for all boxes at once) and the
+// candidate records are emitted with warp-aggregated atomics.
+//
+// Each box pair is found once: box p only visits subtrees whose rightmost
+// leaf lies after its own leaf, and inside its own leaf only later boxes.
+//
+// Merged output without sorting the raw set: for one object pair the tick
+// intersections of their overlapping box pairs ("cells") are disjoint and
+// tile the horizon in order, so a merged interval is a maximal run of
+// consecutive overlapping cells.  A hit emits a "start" record when the cell
+// just before it (the one holding tick s-1) does not overlap, and an "end"
+// record when the cell just after it does not.  Both neighbours are found
+// by stepping one segment back or forward on the object whose segment
+// begins (ends) at the cell's boundary.  Sorting starts and ends separately
+// then pairs them up one to one.
+#include "scd_internal.cuh"
+
+namespace scd {
+
+struct TravArgs {
+  const TravNode *nodes;
+  const float4 *slo, *shi;    // sorted boxes
+  const uint32_t *sobj, *sid; // object and unsorted id of each sorted box
+  const float4 *lo, *hi;      // unsorted boxes (object-major)
+  int64_t N;
+  int L;
+  int64_t M;
+  int T;
+  int raw;
+  int obj_bits, t_bits;
+  unsigned long long *starts, *ends;
+  uint32_t *rawval;
+  unsigned long long cap;
+  DevCounters *ctr;
+};
+
+__device__ __forceinline__ void emit(unsigned long long *buf, uint32_t *vbuf,
+                                     unsigned long long *counter, unsigned long long cap,
+                                     bool pred, unsigned long long key, uint32_t v) {
+  unsigned mask = __activemask();
+  unsigned vote = __ballot_sync(mask, pred);
+  if (!pred) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(vote) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(vote));
+  base = __shfl_sync(vote, base, leader);
+  unsigned long long idx = base + (unsigned long long)__popc(vote & ((1u << lane) - 1u));
+  if (idx < cap) {
+    buf[idx] = key;
+    if (vbuf) vbuf[idx] = v;
+  }
+}
+
+struct Query {
+  float4 lo, hi;
+  uint32_t obj, uid;
+};
+
+__device__ __forceinline__ void on_candidate(const TravArgs &a, const Query &q, int64_t pb,
+                                             unsigned long long &leaf_tests) {
+  float4 bl = __ldg(a.slo + pb), bh = __ldg(a.shi + pb);
+  ++leaf_tests;
+  if (!box_overlap(q.lo, q.hi, bl, bh)) return;
+  uint32_t bo = __ldg(a.sobj + pb);
+  if (bo == q.obj) return;
+  uint32_t bu = __ldg(a.sid + pb);
+  int qt0 = (int)q.lo.w, qt1 = (int)q.hi.w, bt0 = (int)bl.w, bt1 = (int)bh.w;
+  int s = max(qt0, bt0), e = min(qt1, bt1);
+  unsigned long long i = min(q.obj, bo), j = max(q.obj, bo);
+  unsigned long long pk = (i << (a.obj_bits + a.t_bits)) | (j << a.t_bits);
+  if (a.raw) {
+    emit(a.starts, a.rawval, &a.ctr->n_raw, a.cap, true, pk | (unsigned long long)s, (uint32_t)e);
+    return;
+  }
+  bool start = true, end = true;
+  if (s > 0) {
+    // the cell holding tick s-1: step back on whichever segment starts at s
+    float4 ql = q.lo, qh = q.hi, cl = bl, ch = bh;
+    if (qt0 == s) { ql = __ldg(a.lo + q.uid - 1); qh = __ldg(a.hi + q.uid - 1); }
+    if (bt0 == s) { cl = __ldg(a.lo + bu - 1); ch = __ldg(a.hi + bu - 1); }
+    start = !box_overlap(ql, qh, cl, ch);
+  }
+  if (e < a.T) {
+    float4 ql = q.lo, qh = q.hi, cl = bl, ch = bh;
+    if (qt1 == e) { ql = __ldg(a.lo + q.uid + 1); qh = __ldg(a.hi + q.uid + 1); }
+    if (bt1 == e) { cl = __ldg(a.lo + bu + 1); ch = __ldg(a.hi + bu + 1); }
+    end = !box_overlap(ql, qh, cl, ch);
+  }
+  emit(a.starts, nullptr, &a.ctr->n_starts, a.cap, start, pk | (unsigned long long)s, 0u);
+  emit(a.ends, nullptr, &a.ctr->n_ends, a.cap, end, pk | (unsigned long long)e, 0u);
+}
+
+__device__ __forceinline__ void visit_leaf(const TravArgs &a, const Query &q, int64_t leaf,
+                                           unsigned long long &lt) {
+  int64_t b0 = leaf * a.L, b1 = b0 + a.L < a.N ? b0 + a.L : a.N;
+  for (int64_t pb = b0; pb < b1; ++pb) on_candidate(a, q, pb, lt);
+}
+
+template <int kDepth>
+__global__ void __launch_bounds__(256) k_traverse(TravArgs a) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long nt = 0, lt = 0;
+  if (p < a.N) {
+    Query q;
+    q.lo = __ldg(a.slo + p);
+    q.hi = __ldg(a.shi + p);
+    q.obj = __ldg(a.sobj + p);
+    q.uid = __ldg(a.sid + p);
+    int64_t c = p / a.L;
+    int64_t e1 = (c + 1) * a.L < a.N ? (c + 1) * a.L : a.N;
+    for (int64_t pb = p + 1; pb < e1; ++pb) on_candidate(a, q, pb, lt);
+    if (a.M > 1) {
+      int32_t stack[kDepth];
+      int sp = 0;
+      int32_t node = 0;
+      for (;;) {
+        const float4 *np = reinterpret_cast<const float4 *>(a.nodes + node);
+        float4 lol = __ldg(np + 0), hil = __ldg(np + 1), lor = __ldg(np + 2), hir = __ldg(np + 3);
+        int4 lk = __ldg(reinterpret_cast<const int4 *>(np + 4));
+        nt += 2;
+        bool gl = lk.z > c && box_overlap(q.lo, q.hi, lol, hil);
+        bool gr = lk.w > c && box_overlap(q.lo, q.hi, lor, hir);
+        if (gl && (lk.x & kLeafBit)) {
+          visit_leaf(a, q, lk.x & ~kLeafBit, lt);
+          gl = false;
+        }
+        if (gr && (lk.y & kLeafBit)) {
+          visit_leaf(a, q, lk.y & ~kLeafBit, lt);
+          gr = false;
+        }
+        if (gl && gr) {
+          if (sp >= kDepth) {
+            atomicOr(&a.ctr->trav_flags, ERR_STACK);
+            break;
+          }
+          stack[sp++] = lk.y;
+          node = lk.x;
+        } else if (gl) {
+          node = lk.x;
+        } else if (gr) {
+          node = lk.y;
+        } else {
+          if (sp == 0) break;
+          node = stack[--sp];
+        }
+      }
+    }
+  }
+  // one atomic per warp for the test counters
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nt += __shfl_down_sync(0xffffffffu, nt, o);
+    lt += __shfl_down_sync(0xffffffffu, lt, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&a.ctr->node_tests, nt);
+    atomicAdd(&a.ctr->leaf_tests, lt);
+  }
+}
+
+int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_bits) {
+  TravArgs a;
+  a.nodes = s->d_nodes.p;
+  a.slo = s->s_lo.p;
+  a.shi = s->s_hi.p;
+  a.sobj = s->s_obj.p;
+  a.sid = s->d_id.p;
+  a.lo = s->d_lo.p;
+  a.hi = s->d_hi.p;
+  a.N = s->N;
+  a.L = s->tune.leaf_size;
+  a.M = n_leaves;
+  a.T = (int)s->T;
+  a.raw = raw_mode;
+  a.obj_bits = obj_bits;
+  a.t_bits = t_bits;
+  a.starts = s->d_starts.p;
+  a.ends = s->d_ends.p;
+  a.rawval = s->d_rawval.p;
+  a.cap = (unsigned long long)s->pair_cap;
+  a.ctr = s->d_ctr.p;
+  int bs = s->tune.block_threads;
+  if (bs < 32 || bs > 256 || bs % 32) bs = 128;
+  int64_t g = (s->N + bs - 1) / bs;
+  if (g == 0) return SCD_OK;
+  switch (s->tune.stack_depth) {
+    case 32: k_traverse<32><<<(unsigned)g, bs, 0, s->stream>>>(a); break;
+    case 128: k_traverse<128><<<(unsigned)g, bs, 0, s->stream>>>(a); break;
+    default: k_traverse<64><<<(unsigned)g, bs, 0, s->stream>>>(a); break;
+  }
+  note_launch();
+  return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Step A9: sort starts and ends (or the raw cells) and pair them up.
+// ---------------------------------------------------------------------------
+__global__ void k_zip(const unsigned long long *__restrict__ starts,
+                      const unsigned long long *__restrict__ ends, const uint32_t *__restrict__ rawv,
+                      int64_t n, int ob, int tb, scd_pair *__restrict__ out, DevCounters *ctr) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  unsigned long long ks = starts[k];
+  unsigned long long tmask = (1ull << tb) - 1ull, omask = (1ull << ob) - 1ull;
+  scd_pair r;
+  r.i = (uint32_t)(ks >> (ob + tb));
+  r.j = (uint32_t)((ks >> tb) & omask);
+  r.tlo = (int32_t)(ks & tmask);
+  if (rawv) {
+    r.thi = (int32_t)rawv[k];
+  } else {
+    unsigned long long ke = ends[k];
+    r.thi = (int32_t)(ke & tmask);
+    if ((ke >> tb) != (ks >> tb) || r.thi < r.tlo) atomicOr(&ctr->trav_flags, ERR_ZIP);
+  }
+  out[k] = r;
+}
+
+int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits) {
+  cudaStream_t st = s->stream;
+  int64_t n = raw_mode ? (int64_t)s->h_ctr.n_raw : (int64_t)s->h_ctr.n_starts;
+  int bits = 2 * obj_bits + t_bits;
+  if (!s->d_out.ensure(n > 0 ? n : 1, st)) return SCD_ERR_OOM;
+  int rc;
+  if (raw_mode) {
+    rc = radix_sort_u64(s->d_starts.p, s->d_rawval.p, n, bits, s->sort_sc, st);
+    if (rc) return rc;
+  } else {
+    rc = radix_sort_u64(s->d_starts.p, nullptr, n, bits, s->sort_sc, st);
+    if (rc) return rc;
+    rc = radix_sort_u64(s->d_ends.p, nullptr, n, bits, s->sort_sc, st);
+    if (rc) return rc;
+  }
+  if (n > 0)
+    k_zip<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->d_starts.p, s->d_ends.p,
+                                                       raw_mode ? s->d_rawval.p : nullptr, n,
+                                                       obj_bits, t_bits, s->d_out.p, s->d_ctr.p);
+  if (n > 0) note_launch();
+  s->n_out = n;
+  return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
+}
+
+}  // namespace scd
