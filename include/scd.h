@@ -46,7 +46,8 @@ enum {
   SCD_ERR_KEPLER_NOCONV = -5, /* Kepler's equation did not converge        */
   SCD_ERR_TIMEOUT = -6,       /* a bounded device wait gave up             */
   SCD_ERR_INTERNAL = -7,      /* a device-side consistency check failed    */
-  SCD_ERR_STATE = -8          /* call out of order (e.g. no boxes built)   */
+  SCD_ERR_STATE = -8,         /* call out of order (e.g. no boxes built)   */
+  SCD_ERR_CAPACITY = -9       /* size beyond a fixed built-in capacity     */
 };
 
 /* One object (Def 1: position function plus fixed infinity-norm radius).
@@ -200,6 +201,31 @@ SCD_API int scd_get_steps(const scd_scene *s, const int32_t **steps);
  * Runs the propagation code of scd_build_boxes.  Asynchronous on stream. */
 SCD_API int scd_propagate(const scd_element *d_elems, int64_t n, const uint32_t *d_obj,
                           const double *d_t_s, int64_t m, double *d_out, void *cuda_stream);
+
+/* scd_propagate without any device allocation.  The paper has no
+ * counterpart; this exists for callers that cannot allocate device memory
+ * when they call: software that must not allocate after start-up (for
+ * example on-board or embedded code with a fixed memory budget), hosts whose
+ * own allocator this library cannot reach, and latency-bound loops that
+ * cannot pay for the device-wide synchronisation of cudaMalloc/cudaFree.
+ *
+ * Same arguments, layout and result as scd_propagate (obj[q] < n is the
+ * caller's duty).  The per-object scratch (128 bytes per object) lives in a
+ * fixed array in device memory of SCD_NOALLOC_MAX_OBJECTS entries (4 MiB);
+ * every GPU that loads the library holds it until the process exits.
+ * n > SCD_NOALLOC_MAX_OBJECTS fails with SCD_ERR_CAPACITY before any work.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  The call
+ * is asynchronous on cuda_stream and allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  All calls share the one array
+ * and it keeps the last call's contents: calls whose work overlaps on the
+ * GPU (different streams or threads) race and must be serialised by the
+ * caller.  Every scratch entry a call reads is written earlier in the same
+ * call, so nothing needs clearing between calls. */
+#define SCD_NOALLOC_MAX_OBJECTS 32768
+SCD_API int scd_propagate_noalloc(const scd_element *d_elems, int64_t n, const uint32_t *d_obj,
+                                  const double *d_t_s, int64_t m, double *d_out,
+                                  void *cuda_stream);
 
 /* Batched screening: n_scenes independent scenes (each already with boxes)
  * in one persistent traversal launch.  outs[s] is a host array of caps[s]

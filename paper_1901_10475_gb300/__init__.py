@@ -20,6 +20,7 @@ from ._binding import (PAIR_DTYPE, SCD_BOX_INTERVAL, SCD_BOX_SPEED, SCD_DECOMP_A
                        scd_find_pairs, scd_find_pairs_device, scd_find_pairs_into,
                        scd_find_raw_cells_device,
                        scd_get_boxes, scd_get_steps, scd_last_metrics, scd_propagate,
+                       scd_propagate_noalloc,
                        scd_scene_create, scd_scene_destroy, scd_scene_set_elements,
                        scd_scene_set_elements_device, scd_scene_set_tuning,
                        scd_status_string)

@@ -23,6 +23,8 @@ SCD_ERR_KEPLER_NOCONV = -5
 SCD_ERR_TIMEOUT = -6
 SCD_ERR_INTERNAL = -7
 SCD_ERR_STATE = -8
+SCD_ERR_CAPACITY = -9
+SCD_NOALLOC_MAX_OBJECTS = 32768
 
 SCD_STEP_FIXED, SCD_STEP_PERIOD_FRACTION, SCD_STEP_BAND_TABLE, SCD_STEP_LEARNED = 0, 1, 2, 3
 SCD_BOX_SPEED, SCD_BOX_INTERVAL = 0, 1
@@ -97,6 +99,7 @@ def lib() -> ctypes.CDLL:
             "scd_get_boxes": (i32, [vp, P(vp), P(vp), P(vp), P(i64)]),
             "scd_get_steps": (i32, [vp, P(vp)]),
             "scd_propagate": (i32, [vp, i64, vp, vp, i64, vp, vp]),
+            "scd_propagate_noalloc": (i32, [vp, i64, vp, vp, i64, vp, vp]),
             "scd_batch_find_pairs": (i32, [P(vp), i32, P(scd_decomp), P(vp), P(i64), P(i64)]),
             "scd_last_metrics": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t]),
             "scd_scene_destroy": (None, [vp]),
@@ -272,6 +275,15 @@ def scd_propagate(d_elems: int, n: int, d_obj: int, d_t: int, m: int, d_out: int
                   stream: int = 0) -> None:
     check(lib().scd_propagate(d_elems, n, d_obj, d_t, m, d_out, ctypes.c_void_p(stream)),
           "scd_propagate")
+
+
+def scd_propagate_noalloc(d_elems: int, n: int, d_obj: int, d_t: int, m: int, d_out: int,
+                          stream: int = 0) -> None:
+    """scd_propagate for callers that cannot allocate device memory: the
+    scratch lives in a fixed device array of SCD_NOALLOC_MAX_OBJECTS entries,
+    shared by all calls (serialise calls that could overlap on the GPU)."""
+    check(lib().scd_propagate_noalloc(d_elems, n, d_obj, d_t, m, d_out, ctypes.c_void_p(stream)),
+          "scd_propagate_noalloc")
 
 
 def scd_batch_find_pairs(scenes, decomp=None, caps=None):

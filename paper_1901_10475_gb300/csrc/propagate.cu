@@ -473,3 +473,60 @@ int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, DevBuf<int64_
 }
 
 }  // namespace scd
+
+// ---------------------------------------------------------------------------
+// scd_propagate_noalloc: scd_propagate without any device allocation.
+//
+// scd_propagate needs one ObjParams per object as scratch and gets it from
+// the allocator.  Some callers cannot allocate device memory at call time:
+// flight or embedded software that must not allocate after start-up, hosts
+// whose allocator is not reachable from this library, and latency-bound
+// loops that cannot afford the device-wide synchronisation of cudaMalloc and
+// cudaFree.  This variant keeps the scratch in a fixed array in device
+// memory instead; every GPU that loads the library holds that array
+// (kNoAllocMaxObjects * 128 bytes = 4 MiB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace scd {
+constexpr int64_t kNoAllocMaxObjects = SCD_NOALLOC_MAX_OBJECTS;
+static __device__ __align__(256) ObjParams g_noalloc_params[kNoAllocMaxObjects];
+
+constexpr int kNoAllocMaxDevices = 64;
+static ObjParams *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  Host code
+// only holds a stand-in for the symbol, so the address is looked up once per
+// device, with that device current.
+static int noalloc_scratch(ObjParams **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SCD_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return SCD_ERR_CUDA;
+  if (!g_noalloc_ptr[dev]) {
+    ObjParams *p = nullptr;
+    if (cudaGetSymbolAddress((void **)&p, g_noalloc_params) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return SCD_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return SCD_OK;
+}
+}  // namespace scd
+
+extern "C" SCD_API int scd_propagate_noalloc(const scd_element *d_elems, int64_t n,
+                                             const uint32_t *d_obj, const double *d_t_s,
+                                             int64_t m, double *d_out, void *cuda_stream) {
+  if (!d_elems || n <= 0 || m < 0 || (m > 0 && (!d_obj || !d_t_s || !d_out)))
+    return SCD_ERR_INVALID_ARG;
+  if (n > scd::kNoAllocMaxObjects) return SCD_ERR_CAPACITY;
+  scd::ObjParams *par = nullptr;
+  int rc = scd::noalloc_scratch(&par);
+  if (rc != SCD_OK) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int bs = 256;
+  // every entry the second kernel reads is written by the first, so the
+  // array needs no clearing between calls
+  scd::k_prepare_params_only<<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(d_elems, n, par);
+  if (m > 0) scd::k_propagate<<<(unsigned)((m + bs - 1) / bs), bs, 0, st>>>(par, d_obj, d_t_s, m, d_out);
+  return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
+}

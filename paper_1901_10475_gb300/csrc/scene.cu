@@ -63,6 +63,7 @@ extern "C" SCD_API const char *scd_status_string(int status) {
     case SCD_ERR_TIMEOUT: return "bounded device wait timed out";
     case SCD_ERR_INTERNAL: return "device consistency check failed";
     case SCD_ERR_STATE: return "call out of order";
+    case SCD_ERR_CAPACITY: return "size exceeds the fixed built-in capacity";
     default: return "unknown status";
   }
 }
