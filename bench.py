@@ -139,7 +139,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream()
     els = P.catalog_mixture(n=N_OBJ, seed=P.SEED_BASE + 2)
     pol = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=FRACTION)
-    sc = scd.Scene(els, HORIZON_S, TICK_S, pol, stream=stream)
+    sc = scd.Scene(els, args.horizon_s, TICK_S, pol, stream=stream)
     if args.tuning:
         sc.set_tuning(json.loads(args.tuning))
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -237,6 +237,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tuning", default="")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--horizon-s", type=float, default=HORIZON_S,
+                    help="shorter horizons give the small profiling case")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -296,7 +298,9 @@ def main():
         "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "boxes": m["boxes"], "pairs": r["n_pairs"],
+        "config": {"workload": WORKLOAD if args.horizon_s == HORIZON_S else
+                   WORKLOAD.replace("24 h horizon", f"{args.horizon_s:.0f} s horizon"),
+                   "boxes": m["boxes"], "pairs": r["n_pairs"],
                    "records": m["records"], "leaf_size": m["leaf_size"],
                    "morton_bits": m["morton_bits"], "stack_depth": m["stack_depth"],
                    "block_threads": m["block_threads"],
