@@ -133,6 +133,8 @@ typedef struct {
   int morton_bits;    /* bits per axis of the 4D Morton key: 8, 10, 12, 16  */
   float time_scale;   /* weight of the time axis in the Morton key          */
   int use_graph;      /* 1: replay find_pairs as one captured CUDA graph    */
+  int space_warp;     /* 1: log-compress |x| before quantising (finer keys
+                         near Earth, where most boxes are); 0: linear      */
 } scd_tuning;
 
 typedef struct scd_scene scd_scene;

@@ -168,6 +168,7 @@ struct BoxArgs {
   int mode;
   int bits;          // Morton bits per axis
   float time_scale;  // weight of the time axis in the key
+  int space_warp;    // log-compress space coordinates before quantising
   DevCounters *ctr;
   float4 *lo, *hi;
   uint32_t *obj;
@@ -282,10 +283,22 @@ __global__ void __launch_bounds__(256) k_build_boxes(BoxArgs a) {
 
   // 4D Morton key of the box centre in the scene's bounding cube
   double R = __longlong_as_double((long long)a.ctr->extent_bits);
-  float inv = (float)(0.5 / R);
-  float ux = (0.5f * (L.x + H.x)) * inv + 0.5f;
-  float uy = (0.5f * (L.y + H.y)) * inv + 0.5f;
-  float uz = (0.5f * (L.z + H.z)) * inv + 0.5f;
+  float ux, uy, uz;
+  if (a.space_warp) {
+    // sign(x) log(1 + |x|/s) / log(1 + R/s): monotone, so any key order is a
+    // valid tree order; it spends more key bits where most boxes are
+    const float s_km = 1000.0f;
+    float inv = 0.5f / log1pf((float)R / s_km);
+    float cx = 0.5f * (L.x + H.x), cy = 0.5f * (L.y + H.y), cz = 0.5f * (L.z + H.z);
+    ux = copysignf(log1pf(fabsf(cx) / s_km), cx) * inv + 0.5f;
+    uy = copysignf(log1pf(fabsf(cy) / s_km), cy) * inv + 0.5f;
+    uz = copysignf(log1pf(fabsf(cz) / s_km), cz) * inv + 0.5f;
+  } else {
+    float inv = (float)(0.5 / R);
+    ux = (0.5f * (L.x + H.x)) * inv + 0.5f;
+    uy = (0.5f * (L.y + H.y)) * inv + 0.5f;
+    uz = (0.5f * (L.z + H.z)) * inv + 0.5f;
+  }
   float ut = (float)((0.5 * (double)(tlo + thi)) / (double)(a.T + 1)) * a.time_scale;
   unsigned long long key = morton4(quantize(ux, a.bits), quantize(uy, a.bits),
                                    quantize(uz, a.bits), quantize(ut, a.bits), a.bits);
@@ -305,6 +318,7 @@ int launch_build_boxes(scd_scene *s) {
   a.mode = s->box_mode;
   a.bits = s->tune.morton_bits;
   a.time_scale = s->tune.time_scale;
+  a.space_warp = s->tune.space_warp;
   a.ctr = s->d_ctr.p;
   a.lo = s->d_lo.p;
   a.hi = s->d_hi.p;

@@ -52,6 +52,7 @@ struct DevCounters {
   unsigned long long n_raw;
   unsigned long long node_tests;
   unsigned long long leaf_tests;
+  unsigned long long work_next;  // next query claimed by the persistent traversal
   unsigned int trav_flags;   // ERR_STACK, ERR_ZIP
   unsigned int pad0;
   unsigned long long extent_bits;  // max object extent [km] as double bits

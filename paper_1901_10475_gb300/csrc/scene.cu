@@ -70,12 +70,13 @@ extern "C" SCD_API const char *scd_status_string(int status) {
 
 extern "C" SCD_API int scd_default_tuning(scd_tuning *t) {
   if (!t) return SCD_ERR_INVALID_ARG;
-  t->leaf_size = 4;
+  t->leaf_size = 1;  // one box per leaf: the persistent lock-step traversal
   t->stack_depth = 64;
   t->block_threads = 128;
   t->morton_bits = 8;
   t->time_scale = 1.0f;
   t->use_graph = 0;
+  t->space_warp = 0;
   return SCD_OK;
 }
 
@@ -86,7 +87,8 @@ static bool tuning_ok(const scd_tuning *t) {
   bool mb = t->morton_bits == 8 || t->morton_bits == 10 || t->morton_bits == 12 ||
             t->morton_bits == 16;
   bool ts = t->time_scale > 0.0f && t->time_scale <= 1.0f;
-  return leaf && st && bs && mb && ts;
+  bool sw = t->space_warp == 0 || t->space_warp == 1;
+  return leaf && st && bs && mb && ts && sw;
 }
 
 static bool element_ok(const scd_element &x) {
@@ -213,7 +215,8 @@ extern "C" SCD_API int scd_scene_set_elements_device(scd_scene *s, const scd_ele
 
 extern "C" SCD_API int scd_scene_set_tuning(scd_scene *s, const scd_tuning *t) {
   if (!s || !t || !tuning_ok(t)) return SCD_ERR_INVALID_ARG;
-  bool rekey = t->morton_bits != s->tune.morton_bits || t->time_scale != s->tune.time_scale;
+  bool rekey = t->morton_bits != s->tune.morton_bits || t->time_scale != s->tune.time_scale ||
+               t->space_warp != s->tune.space_warp;
   s->tune = *t;
   if (rekey) s->boxes_built = false;
   return SCD_OK;

@@ -14,6 +14,8 @@
 // by stepping one segment back or forward on the object whose segment
 // begins (ends) at the cell's boundary.  Sorting starts and ends separately
 // then pairs them up one to one.
+#include <algorithm>
+
 #include "scd_internal.cuh"
 
 namespace scd {
@@ -58,31 +60,28 @@ struct Query {
   uint32_t obj, uid;
 };
 
-__device__ __forceinline__ void on_candidate(const TravArgs &a, const Query &q, int64_t pb,
-                                             unsigned long long &leaf_tests) {
-  float4 bl = __ldg(a.slo + pb), bh = __ldg(a.shi + pb);
-  ++leaf_tests;
-  if (!box_overlap(q.lo, q.hi, bl, bh)) return;
-  uint32_t bo = __ldg(a.sobj + pb);
-  if (bo == q.obj) return;
-  uint32_t bu = __ldg(a.sid + pb);
+// Records of one overlapping box pair (q, b) of different objects.  `valid`
+// lanes carry a pair; the others only take part in the warp votes.
+__device__ __forceinline__ void pair_records(const TravArgs &a, bool valid, const Query &q,
+                                             float4 bl, float4 bh, uint32_t bo, uint32_t bu) {
   int qt0 = (int)q.lo.w, qt1 = (int)q.hi.w, bt0 = (int)bl.w, bt1 = (int)bh.w;
   int s = max(qt0, bt0), e = min(qt1, bt1);
   unsigned long long i = min(q.obj, bo), j = max(q.obj, bo);
   unsigned long long pk = (i << (a.obj_bits + a.t_bits)) | (j << a.t_bits);
   if (a.raw) {
-    emit(a.starts, a.rawval, &a.ctr->n_raw, a.cap, true, pk | (unsigned long long)s, (uint32_t)e);
+    emit(a.starts, a.rawval, &a.ctr->n_raw, a.cap, valid, pk | (unsigned long long)s,
+         (uint32_t)e);
     return;
   }
-  bool start = true, end = true;
-  if (s > 0) {
+  bool start = valid, end = valid;
+  if (valid && s > 0) {
     // the cell holding tick s-1: step back on whichever segment starts at s
     float4 ql = q.lo, qh = q.hi, cl = bl, ch = bh;
     if (qt0 == s) { ql = __ldg(a.lo + q.uid - 1); qh = __ldg(a.hi + q.uid - 1); }
     if (bt0 == s) { cl = __ldg(a.lo + bu - 1); ch = __ldg(a.hi + bu - 1); }
     start = !box_overlap(ql, qh, cl, ch);
   }
-  if (e < a.T) {
+  if (valid && e < a.T) {
     float4 ql = q.lo, qh = q.hi, cl = bl, ch = bh;
     if (qt1 == e) { ql = __ldg(a.lo + q.uid + 1); qh = __ldg(a.hi + q.uid + 1); }
     if (bt1 == e) { cl = __ldg(a.lo + bu + 1); ch = __ldg(a.hi + bu + 1); }
@@ -90,6 +89,16 @@ __device__ __forceinline__ void on_candidate(const TravArgs &a, const Query &q, 
   }
   emit(a.starts, nullptr, &a.ctr->n_starts, a.cap, start, pk | (unsigned long long)s, 0u);
   emit(a.ends, nullptr, &a.ctr->n_ends, a.cap, end, pk | (unsigned long long)e, 0u);
+}
+
+__device__ __forceinline__ void on_candidate(const TravArgs &a, const Query &q, int64_t pb,
+                                             unsigned long long &leaf_tests) {
+  float4 bl = __ldg(a.slo + pb), bh = __ldg(a.shi + pb);
+  ++leaf_tests;
+  if (!box_overlap(q.lo, q.hi, bl, bh)) return;
+  uint32_t bo = __ldg(a.sobj + pb);
+  if (bo == q.obj) return;
+  pair_records(a, true, q, bl, bh, bo, __ldg(a.sid + pb));
 }
 
 __device__ __forceinline__ void visit_leaf(const TravArgs &a, const Query &q, int64_t leaf,
@@ -160,6 +169,133 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent traversal for one box per leaf.  Every loop iteration of every
+// lane is the same step (load one node, test its two child boxes), so lanes
+// stay in lock step; a lane whose query is done claims the next one at once;
+// overlapping box pairs go to a per-warp buffer and their records are worked
+// out by the whole warp together.
+// ---------------------------------------------------------------------------
+constexpr int kT2Threads = 128;
+constexpr int kT2Warps = kT2Threads / 32;
+constexpr int kHitCap = 256;  // per warp; drained when fewer than 64 slots remain
+
+__device__ __forceinline__ void drain_hits(const TravArgs &a, const uint2 *buf, int cnt) {
+  const int lane = threadIdx.x & 31;
+  for (int base = 0; base < cnt; base += 32) {
+    int k = base + lane;
+    bool valid = k < cnt;
+    Query q;
+    float4 bl = make_float4(0.f, 0.f, 0.f, 0.f), bh = bl;
+    uint32_t bo = 0, bu = 0;
+    q.lo = q.hi = bl;
+    q.obj = q.uid = 0;
+    if (valid) {
+      uint2 h = buf[k];
+      q.lo = __ldg(a.slo + h.x);
+      q.hi = __ldg(a.shi + h.x);
+      q.obj = __ldg(a.sobj + h.x);
+      q.uid = __ldg(a.sid + h.x);
+      bl = __ldg(a.slo + h.y);
+      bh = __ldg(a.shi + h.y);
+      bo = __ldg(a.sobj + h.y);
+      bu = __ldg(a.sid + h.y);
+      valid = bo != q.obj;
+    }
+    pair_records(a, valid, q, bl, bh, bo, bu);
+  }
+}
+
+template <int kDepth>
+__global__ void __launch_bounds__(kT2Threads) k_traverse2(TravArgs a) {
+  __shared__ uint2 hits[kT2Warps][kHitCap];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  uint2 *buf = hits[w];
+  int nhit = 0;  // warp-uniform
+  unsigned long long nt = 0;
+  int64_t p = -1;  // current query (sorted position), -1 = none
+  bool exhausted = false;
+  Query q;
+  q.lo = q.hi = make_float4(0.f, 0.f, 0.f, 0.f);
+  int32_t stack[kDepth];
+  int sp = 0;
+  int32_t node = 0;
+  for (;;) {
+    // lanes without a query claim the next ones (one atomic per warp)
+    unsigned need = __ballot_sync(0xffffffffu, p < 0 && !exhausted);
+    if (need) {
+      unsigned long long base = 0;
+      if (lane == __ffs(need) - 1) base = atomicAdd(&a.ctr->work_next, (unsigned long long)__popc(need));
+      base = __shfl_sync(0xffffffffu, base, __ffs(need) - 1);
+      if (need & (1u << lane)) {
+        unsigned long long mine = base + __popc(need & lt);
+        if (mine + 1 < (unsigned long long)a.N) {  // the last box has no later partner
+          p = (int64_t)mine;
+          q.lo = __ldg(a.slo + p);
+          q.hi = __ldg(a.shi + p);
+          node = 0;
+          sp = 0;
+        } else {
+          exhausted = true;
+        }
+      }
+    }
+    bool active = p >= 0;
+    if (__ballot_sync(0xffffffffu, active) == 0) break;
+    const uint32_t pq = (uint32_t)p;  // this step's query, before p may end
+    bool hl = false, hr = false;
+    int32_t cl = 0, cr = 0;
+    if (active) {
+      const float4 *np = reinterpret_cast<const float4 *>(a.nodes + node);
+      float4 lol = __ldg(np + 0), hil = __ldg(np + 1), lor = __ldg(np + 2), hir = __ldg(np + 3);
+      int4 lk = __ldg(reinterpret_cast<const int4 *>(np + 4));
+      nt += 2;
+      bool gl = lk.z > p && box_overlap(q.lo, q.hi, lol, hil);
+      bool gr = lk.w > p && box_overlap(q.lo, q.hi, lor, hir);
+      cl = lk.x & ~kLeafBit;
+      cr = lk.y & ~kLeafBit;
+      // a leaf child that passes is an overlapping box with a later position
+      if (gl && (lk.x & kLeafBit)) { hl = true; gl = false; }
+      if (gr && (lk.y & kLeafBit)) { hr = true; gr = false; }
+      if (gl && gr) {
+        if (sp < kDepth) {
+          stack[sp++] = cr;
+          node = cl;
+        } else {
+          atomicOr(&a.ctr->trav_flags, ERR_STACK);
+          p = -1;
+        }
+      } else if (gl) {
+        node = cl;
+      } else if (gr) {
+        node = cr;
+      } else if (sp > 0) {
+        node = stack[--sp];
+      } else {
+        p = -1;  // query done
+      }
+    }
+    // append this step's hits to the warp buffer
+    unsigned vl = __ballot_sync(0xffffffffu, hl), vr = __ballot_sync(0xffffffffu, hr);
+    if (hl) buf[nhit + __popc(vl & lt)] = make_uint2(pq, (uint32_t)cl);
+    int nl = __popc(vl);
+    if (hr) buf[nhit + nl + __popc(vr & lt)] = make_uint2(pq, (uint32_t)cr);
+    nhit += nl + __popc(vr);
+    __syncwarp();
+    if (nhit > kHitCap - 64) {
+      drain_hits(a, buf, nhit);
+      __syncwarp();
+      nhit = 0;
+    }
+  }
+  __syncwarp();
+  if (nhit > 0) drain_hits(a, buf, nhit);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nt += __shfl_down_sync(0xffffffffu, nt, o);
+  if (lane == 0) atomicAdd(&a.ctr->node_tests, nt);
+}
+
 int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_bits) {
   TravArgs a;
   a.nodes = s->d_nodes.p;
@@ -181,6 +317,28 @@ int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_b
   a.rawval = s->d_rawval.p;
   a.cap = (unsigned long long)s->pair_cap;
   a.ctr = s->d_ctr.p;
+  if (a.L == 1) {
+    // persistent: as many blocks as fit on the GPU at once
+    static int sms = 0;
+    if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    int per_sm = 0;
+    switch (s->tune.stack_depth) {
+      case 32:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse2<32>, kT2Threads, 0);
+        k_traverse2<32><<<(unsigned)(sms * std::max(per_sm, 1)), kT2Threads, 0, s->stream>>>(a);
+        break;
+      case 128:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse2<128>, kT2Threads, 0);
+        k_traverse2<128><<<(unsigned)(sms * std::max(per_sm, 1)), kT2Threads, 0, s->stream>>>(a);
+        break;
+      default:
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse2<64>, kT2Threads, 0);
+        k_traverse2<64><<<(unsigned)(sms * std::max(per_sm, 1)), kT2Threads, 0, s->stream>>>(a);
+        break;
+    }
+    note_launch();
+    return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
+  }
   int bs = s->tune.block_threads;
   if (bs < 32 || bs > 256 || bs % 32) bs = 128;
   int64_t g = (s->N + bs - 1) / bs;
