@@ -97,9 +97,12 @@ __global__ void k_refit(const float4 *__restrict__ slo, const float4 *__restrict
                         int L, int64_t M, float4 *__restrict__ leaflo, float4 *__restrict__ leafhi,
                         TravNode *__restrict__ nodes, float4 *__restrict__ nlo,
                         float4 *__restrict__ nhi, const int32_t *__restrict__ parent_int,
-                        const int32_t *__restrict__ parent_leaf, uint32_t *__restrict__ flags) {
+                        const int32_t *__restrict__ parent_leaf, uint32_t *__restrict__ flags,
+                        QBox *__restrict__ qbox, uint2 *__restrict__ qlink,
+                        const DevCounters *__restrict__ ctr, int64_t T) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= M) return;
+  const QFrame fr = scene_frame(ctr, T);
   int64_t b0 = c * L, b1 = b0 + L < N ? b0 + L : N;
   float4 lo = slo[b0], hi = shi[b0];
   for (int64_t b = b0 + 1; b < b1; ++b) {
@@ -132,11 +135,19 @@ __global__ void k_refit(const float4 *__restrict__ slo, const float4 *__restrict
       rlo = __ldcg(nlo + nd.right);
       rhi = __ldcg(nhi + nd.right);
     }
-    nd.lo_l = llo;
-    nd.hi_l = lhi;
-    nd.lo_r = rlo;
-    nd.hi_r = rhi;
-    nodes[p] = nd;
+    if (qbox) {
+      qbox[2 * p] = quantize_box(fr, llo, lhi);
+      qbox[2 * p + 1] = quantize_box(fr, rlo, rhi);
+      uint32_t g = (uint32_t)nd.last_l;  // the split: left child gamma, right gamma + 1
+      uint32_t fl = ((nd.left & kLeafBit) ? kQLeftLeaf : 0u) | ((nd.right & kLeafBit) ? kQRightLeaf : 0u);
+      qlink[p] = make_uint2(g | fl, (uint32_t)nd.last_r);
+    } else {
+      nd.lo_l = llo;
+      nd.hi_l = lhi;
+      nd.lo_r = rlo;
+      nd.hi_r = rhi;
+      nodes[p] = nd;
+    }
     __stcg(nlo + p, f4min(llo, rlo));
     __stcg(nhi + p, f4max(lhi, rhi));
     p = parent_int[p];
@@ -155,6 +166,10 @@ static int build_impl(scd_scene *s, const K *keys_sorted, K *leafkey, int64_t &M
       !s->d_nhi.ensure(M > 1 ? M - 1 : 1, st) || !s->d_parent_int.ensure(M, st) ||
       !s->d_parent_leaf.ensure(M, st) || !s->d_flags.ensure(M, st))
     return SCD_ERR_OOM;
+  const bool compact = L == 1;
+  if (compact && (!s->d_qbox.ensure(2 * (M > 1 ? M - 1 : 1), st) ||
+                  !s->d_qlink.ensure(M > 1 ? M - 1 : 1, st)))
+    return SCD_ERR_OOM;
   int bs = 256;
   k_gather_sorted<K><<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(
       s->d_id.p, s->d_lo.p, s->d_hi.p, s->d_obj.p, keys_sorted, N, L, s->s_lo.p, s->s_hi.p,
@@ -167,7 +182,8 @@ static int build_impl(scd_scene *s, const K *keys_sorted, K *leafkey, int64_t &M
   }
   k_refit<<<(unsigned)((M + bs - 1) / bs), bs, 0, st>>>(
       s->s_lo.p, s->s_hi.p, N, L, M, s->d_leaflo.p, s->d_leafhi.p, s->d_nodes.p, s->d_nlo.p,
-      s->d_nhi.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p);
+      s->d_nhi.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p,
+      compact ? s->d_qbox.p : nullptr, compact ? s->d_qlink.p : nullptr, s->d_ctr.p, s->T);
   return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
 }
 

@@ -13,7 +13,7 @@ namespace scd {
 
 constexpr int kRsThreads = 256;
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsItems = 16;
+constexpr int kRsItems = 8;
 constexpr int kRsTile = kRsThreads * kRsItems;
 
 template <class K>

@@ -47,9 +47,12 @@ struct __align__(16) ObjParams {
 // block is zeroed before every traversal; the second is written by the box
 // build.
 struct DevCounters {
-  unsigned long long n_starts;
+  unsigned long long n_starts;  // record slots handed out (holes included)
   unsigned long long n_ends;
   unsigned long long n_raw;
+  unsigned long long v_starts;  // records actually written
+  unsigned long long v_ends;
+  unsigned long long v_raw;
   unsigned long long node_tests;
   unsigned long long leaf_tests;
   unsigned long long work_next;  // next query claimed by the persistent traversal
@@ -71,6 +74,54 @@ struct __align__(16) TravNode {
 };
 
 constexpr int32_t kLeafBit = (int32_t)0x80000000u;
+
+// Compact node of the one-box-per-leaf traversal (40 bytes): both child
+// boxes quantised to 16 bits per face in the scene frame (lower faces
+// rounded down, upper faces up, so a quantised test never rejects a pair
+// that overlaps in FP32), the split gamma (left child gamma, right child
+// gamma + 1) with two leaf flags, and the rightmost leaf under the right
+// child (the left child's rightmost leaf is gamma itself).
+struct __align__(16) QBox {
+  uint32_t lo_xy, lo_zt, hi_xy, hi_zt;  // u16 pairs: x | y << 16, z | t << 16
+};
+constexpr uint32_t kQLeftLeaf = 0x80000000u, kQRightLeaf = 0x40000000u;
+constexpr uint32_t kQIndex = 0x3fffffffu;
+
+// the scene frame of the quantisation: x, y, z in [-R, R] km, t in [0, T]
+struct QFrame {
+  float R, sx, st;  // sx = 65535 / (2R), st = 65535 / T
+};
+
+// the frame of a scene, from the extent found by the box build; every kernel
+// that quantises derives it with this same code, so the values agree
+__device__ inline QFrame scene_frame(const DevCounters *ctr, int64_t T) {
+  QFrame f;
+  f.R = (float)__longlong_as_double((long long)ctr->extent_bits);
+  f.sx = 65535.0f / (2.0f * f.R);
+  f.st = 65535.0f / (float)(T > 0 ? T : 1);
+  return f;
+}
+
+__host__ __device__ inline uint32_t q16_lo(float v) {
+  float f = floorf(v);
+  f = f < 0.f ? 0.f : (f > 65535.f ? 65535.f : f);
+  return (uint32_t)f;
+}
+__host__ __device__ inline uint32_t q16_hi(float v) {
+  float f = ceilf(v);
+  f = f < 0.f ? 0.f : (f > 65535.f ? 65535.f : f);
+  return (uint32_t)f;
+}
+// quantise a box outward; the map x -> (x + R) * sx is monotone in FP32, so
+// box order relations survive it
+__host__ __device__ inline QBox quantize_box(const QFrame &f, float4 lo, float4 hi) {
+  QBox q;
+  q.lo_xy = q16_lo((lo.x + f.R) * f.sx) | (q16_lo((lo.y + f.R) * f.sx) << 16);
+  q.lo_zt = q16_lo((lo.z + f.R) * f.sx) | (q16_lo(lo.w * f.st) << 16);
+  q.hi_xy = q16_hi((hi.x + f.R) * f.sx) | (q16_hi((hi.y + f.R) * f.sx) << 16);
+  q.hi_zt = q16_hi((hi.z + f.R) * f.sx) | (q16_hi(hi.w * f.st) << 16);
+  return q;
+}
 
 __host__ __device__ inline bool box_overlap(const float4 &la, const float4 &ha,
                                             const float4 &lb, const float4 &hb) {
@@ -178,6 +229,8 @@ struct scd_scene {
   scd::DevBuf<uint32_t> s_leafkey32;
   scd::DevBuf<unsigned long long> s_leafkey64;
   scd::DevBuf<scd::TravNode> d_nodes;
+  scd::DevBuf<scd::QBox> d_qbox;     // 2 per internal node (one box per leaf)
+  scd::DevBuf<uint2> d_qlink;        // per internal node: gamma | flags, last_r
   scd::DevBuf<float4> d_nlo, d_nhi;     // internal node boxes (refit)
   scd::DevBuf<float4> d_leaflo, d_leafhi;
   scd::DevBuf<int32_t> d_parent_int, d_parent_leaf;

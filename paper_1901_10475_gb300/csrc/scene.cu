@@ -305,7 +305,7 @@ static int find_pairs_impl(scd_scene *s, const scd_decomp *d, int raw_mode) {
   if (!done) return SCD_ERR_INTERNAL;
   if (s->h_ctr.build_flags & ERR_INVALID) return SCD_ERR_INVALID_ARG;
   if (s->h_ctr.build_flags & ERR_KEPLER) return SCD_ERR_KEPLER_NOCONV;
-  if (!raw_mode && s->h_ctr.n_starts != s->h_ctr.n_ends) return SCD_ERR_INTERNAL;
+  if (!raw_mode && s->h_ctr.v_starts != s->h_ctr.v_ends) return SCD_ERR_INTERNAL;
   if (s->events_ready) cudaEventRecord(s->ev[5], st);
   // A9: canonical list
   TRY(canonicalize(s, raw_mode, ob, tb));
@@ -316,7 +316,7 @@ static int find_pairs_impl(scd_scene *s, const scd_decomp *d, int raw_mode) {
   if (flags & ERR_ZIP) return SCD_ERR_INTERNAL;
   s->last_node_tests = s->h_ctr.node_tests;
   s->last_leaf_tests = s->h_ctr.leaf_tests;
-  s->last_runs = raw_mode ? s->h_ctr.n_raw : s->h_ctr.n_starts;
+  s->last_runs = raw_mode ? s->h_ctr.v_raw : s->h_ctr.v_starts;
   s->last_launches = launch_count() - s->launch_mark;
   if (s->events_ready) {
     float ms = 0;
@@ -432,6 +432,7 @@ extern "C" SCD_API void scd_scene_destroy(scd_scene *s) {
   s->s_lo.release(st); s->s_hi.release(st); s->s_obj.release(st);
   s->s_leafkey32.release(st); s->s_leafkey64.release(st);
   s->d_nodes.release(st); s->d_nlo.release(st); s->d_nhi.release(st);
+  s->d_qbox.release(st); s->d_qlink.release(st);
   s->d_leaflo.release(st); s->d_leafhi.release(st);
   s->d_parent_int.release(st); s->d_parent_leaf.release(st); s->d_flags.release(st);
   s->d_first_last.release(st);

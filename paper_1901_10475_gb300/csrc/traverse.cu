@@ -1,6 +1,6 @@
 // traverse.cu -- step A8: every box queries the hierarchy for the boxes it
 // meets (the tree query of Sec. 3.2, run for all boxes at once) and the
-// candidate records are emitted with warp-aggregated atomics.
+// candidate records are emitted; step A9: the canonical list.
 //
 // Each box pair is found once: box p only visits subtrees whose rightmost
 // leaf lies after its own leaf, and inside its own leaf only later boxes.
@@ -22,6 +22,8 @@ namespace scd {
 
 struct TravArgs {
   const TravNode *nodes;
+  const QBox *qbox;           // compact nodes (one box per leaf)
+  const uint2 *qlink;
   const float4 *slo, *shi;    // sorted boxes
   const uint32_t *sobj, *sid; // object and unsorted id of each sorted box
   const float4 *lo, *hi;      // unsorted boxes (object-major)
@@ -37,22 +39,76 @@ struct TravArgs {
   DevCounters *ctr;
 };
 
-__device__ __forceinline__ void emit(unsigned long long *buf, uint32_t *vbuf,
-                                     unsigned long long *counter, unsigned long long cap,
-                                     bool pred, unsigned long long key, uint32_t v) {
-  unsigned mask = __activemask();
-  unsigned vote = __ballot_sync(mask, pred);
-  if (!pred) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(vote) - 1;
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(vote));
-  base = __shfl_sync(vote, base, leader);
-  unsigned long long idx = base + (unsigned long long)__popc(vote & ((1u << lane) - 1u));
-  if (idx < cap) {
-    buf[idx] = key;
-    if (vbuf) vbuf[idx] = v;
+// a slot that holds no record: all key bits set, so it sorts after every
+// real record (whose object fields can never be all ones)
+constexpr unsigned long long kHole = ~0ull;
+
+// One record per predicate-true lane, each with its own atomic slot range
+// (used by the one-thread-per-box traversal, whose lanes are not in step).
+struct DirectEmit {
+  __device__ __forceinline__ void put(unsigned long long *buf, uint32_t *vbuf,
+                                      unsigned long long *slots, unsigned long long *valid,
+                                      unsigned long long cap, bool pred, unsigned long long key,
+                                      uint32_t v) {
+    unsigned mask = __activemask();
+    unsigned vote = __ballot_sync(mask, pred);
+    if (!pred) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(vote) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) {
+      base = atomicAdd(slots, (unsigned long long)__popc(vote));
+      atomicAdd(valid, (unsigned long long)__popc(vote));
+    }
+    base = __shfl_sync(vote, base, leader);
+    unsigned long long idx = base + (unsigned long long)__popc(vote & ((1u << lane) - 1u));
+    if (idx < cap) {
+      buf[idx] = key;
+      if (vbuf) vbuf[idx] = v;
+    }
   }
+};
+
+// Whole-warp emission into a chunk of slots reserved by the warp (one atomic
+// per kChunk records).  A chunk's unused tail is filled with holes.  Every
+// lane of the warp calls put() together; the chunk state is warp-uniform.
+constexpr unsigned kChunk = 512;
+struct ChunkCursor {
+  unsigned long long next = 0, end = 0, count = 0;
+};
+
+__device__ __forceinline__ void chunk_fill_holes(ChunkCursor &c, unsigned long long *buf,
+                                                 unsigned long long cap) {
+  const int lane = threadIdx.x & 31;
+  for (unsigned long long k = c.next + lane; k < c.end; k += 32)
+    if (k < cap) buf[k] = kHole;
+  c.next = c.end;
+}
+
+__device__ __forceinline__ void chunk_put(ChunkCursor &c, unsigned long long *buf, uint32_t *vbuf,
+                                          unsigned long long *slots, unsigned long long cap,
+                                          bool pred, unsigned long long key, uint32_t v) {
+  const int lane = threadIdx.x & 31;
+  unsigned vote = __ballot_sync(0xffffffffu, pred);
+  unsigned cnt = __popc(vote);
+  if (cnt == 0) return;
+  if (c.next + cnt > c.end) {
+    chunk_fill_holes(c, buf, cap);
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(slots, (unsigned long long)kChunk);
+    b = __shfl_sync(0xffffffffu, b, 0);
+    c.next = b;
+    c.end = b + kChunk;
+  }
+  if (pred) {
+    unsigned long long idx = c.next + __popc(vote & ((1u << lane) - 1u));
+    if (idx < cap) {
+      buf[idx] = key;
+      if (vbuf) vbuf[idx] = v;
+    }
+  }
+  c.next += cnt;
+  c.count += cnt;
 }
 
 struct Query {
@@ -60,37 +116,34 @@ struct Query {
   uint32_t obj, uid;
 };
 
-// Records of one overlapping box pair (q, b) of different objects.  `valid`
-// lanes carry a pair; the others only take part in the warp votes.
-__device__ __forceinline__ void pair_records(const TravArgs &a, bool valid, const Query &q,
-                                             float4 bl, float4 bh, uint32_t bo, uint32_t bu) {
+// Is (q, b) the first / last cell of its run?  Both need the neighbouring
+// cell: one segment back (forward) on whichever box starts (ends) there.
+__device__ __forceinline__ void run_ends(const TravArgs &a, const Query &q, float4 bl, float4 bh,
+                                         uint32_t bu, int s, int e, bool &start, bool &end) {
   int qt0 = (int)q.lo.w, qt1 = (int)q.hi.w, bt0 = (int)bl.w, bt1 = (int)bh.w;
-  int s = max(qt0, bt0), e = min(qt1, bt1);
-  unsigned long long i = min(q.obj, bo), j = max(q.obj, bo);
-  unsigned long long pk = (i << (a.obj_bits + a.t_bits)) | (j << a.t_bits);
-  if (a.raw) {
-    emit(a.starts, a.rawval, &a.ctr->n_raw, a.cap, valid, pk | (unsigned long long)s,
-         (uint32_t)e);
-    return;
-  }
-  bool start = valid, end = valid;
-  if (valid && s > 0) {
-    // the cell holding tick s-1: step back on whichever segment starts at s
+  if (start && s > 0) {
     float4 ql = q.lo, qh = q.hi, cl = bl, ch = bh;
     if (qt0 == s) { ql = __ldg(a.lo + q.uid - 1); qh = __ldg(a.hi + q.uid - 1); }
     if (bt0 == s) { cl = __ldg(a.lo + bu - 1); ch = __ldg(a.hi + bu - 1); }
     start = !box_overlap(ql, qh, cl, ch);
   }
-  if (valid && e < a.T) {
+  if (end && e < a.T) {
     float4 ql = q.lo, qh = q.hi, cl = bl, ch = bh;
     if (qt1 == e) { ql = __ldg(a.lo + q.uid + 1); qh = __ldg(a.hi + q.uid + 1); }
     if (bt1 == e) { cl = __ldg(a.lo + bu + 1); ch = __ldg(a.hi + bu + 1); }
     end = !box_overlap(ql, qh, cl, ch);
   }
-  emit(a.starts, nullptr, &a.ctr->n_starts, a.cap, start, pk | (unsigned long long)s, 0u);
-  emit(a.ends, nullptr, &a.ctr->n_ends, a.cap, end, pk | (unsigned long long)e, 0u);
 }
 
+__device__ __forceinline__ unsigned long long pair_key(const TravArgs &a, uint32_t oa,
+                                                       uint32_t ob) {
+  unsigned long long i = min(oa, ob), j = max(oa, ob);
+  return (i << (a.obj_bits + a.t_bits)) | (j << a.t_bits);
+}
+
+// ---------------------------------------------------------------------------
+// One thread per box, for leaves of several boxes.
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ void on_candidate(const TravArgs &a, const Query &q, int64_t pb,
                                              unsigned long long &leaf_tests) {
   float4 bl = __ldg(a.slo + pb), bh = __ldg(a.shi + pb);
@@ -98,7 +151,21 @@ __device__ __forceinline__ void on_candidate(const TravArgs &a, const Query &q, 
   if (!box_overlap(q.lo, q.hi, bl, bh)) return;
   uint32_t bo = __ldg(a.sobj + pb);
   if (bo == q.obj) return;
-  pair_records(a, true, q, bl, bh, bo, __ldg(a.sid + pb));
+  uint32_t bu = __ldg(a.sid + pb);
+  int s = max((int)q.lo.w, (int)bl.w), e = min((int)q.hi.w, (int)bh.w);
+  unsigned long long pk = pair_key(a, q.obj, bo);
+  DirectEmit em;
+  if (a.raw) {
+    em.put(a.starts, a.rawval, &a.ctr->n_raw, &a.ctr->v_raw, a.cap, true,
+           pk | (unsigned long long)s, (uint32_t)e);
+    return;
+  }
+  bool start = true, end = true;
+  run_ends(a, q, bl, bh, bu, s, e, start, end);
+  em.put(a.starts, nullptr, &a.ctr->n_starts, &a.ctr->v_starts, a.cap, start,
+         pk | (unsigned long long)s, 0u);
+  em.put(a.ends, nullptr, &a.ctr->n_ends, &a.ctr->v_ends, a.cap, end,
+         pk | (unsigned long long)e, 0u);
 }
 
 __device__ __forceinline__ void visit_leaf(const TravArgs &a, const Query &q, int64_t leaf,
@@ -171,16 +238,23 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a) {
 
 // ---------------------------------------------------------------------------
 // Persistent traversal for one box per leaf.  Every loop iteration of every
-// lane is the same step (load one node, test its two child boxes), so lanes
-// stay in lock step; a lane whose query is done claims the next one at once;
-// overlapping box pairs go to a per-warp buffer and their records are worked
-// out by the whole warp together.
+// lane is the same step (load one compact node, test its two child boxes), so
+// lanes stay in lock step; a lane whose query is done takes the next one from
+// a pool its warp claims in blocks; overlapping box pairs go to a per-warp
+// buffer and their records are worked out by the whole warp together, into
+// output chunks the warp reserves kChunk slots at a time.
 // ---------------------------------------------------------------------------
 constexpr int kT2Threads = 128;
 constexpr int kT2Warps = kT2Threads / 32;
 constexpr int kHitCap = 256;  // per warp; drained when fewer than 64 slots remain
+constexpr unsigned kQueryChunk = 256;  // queries claimed per warp atomic
 
-__device__ __forceinline__ void drain_hits(const TravArgs &a, const uint2 *buf, int cnt) {
+struct WarpEmit {
+  ChunkCursor s, e;  // start and end record chunks (raw cells use s)
+};
+
+__device__ __forceinline__ void drain_hits(const TravArgs &a, const uint2 *buf, int cnt,
+                                           WarpEmit &we) {
   const int lane = threadIdx.x & 31;
   for (int base = 0; base < cnt; base += 32) {
     int k = base + lane;
@@ -200,45 +274,71 @@ __device__ __forceinline__ void drain_hits(const TravArgs &a, const uint2 *buf, 
       bh = __ldg(a.shi + h.y);
       bo = __ldg(a.sobj + h.y);
       bu = __ldg(a.sid + h.y);
-      valid = bo != q.obj;
+      // the tree test was on quantised boxes: decide on the exact ones
+      valid = bo != q.obj && box_overlap(q.lo, q.hi, bl, bh);
     }
-    pair_records(a, valid, q, bl, bh, bo, bu);
+    int s = max((int)q.lo.w, (int)bl.w), e = min((int)q.hi.w, (int)bh.w);
+    unsigned long long pk = pair_key(a, q.obj, bo);
+    if (a.raw) {
+      chunk_put(we.s, a.starts, a.rawval, &a.ctr->n_raw, a.cap, valid,
+                pk | (unsigned long long)s, (uint32_t)e);
+      continue;
+    }
+    bool start = valid, end = valid;
+    if (valid) run_ends(a, q, bl, bh, bu, s, e, start, end);
+    chunk_put(we.s, a.starts, nullptr, &a.ctr->n_starts, a.cap, start,
+              pk | (unsigned long long)s, 0u);
+    chunk_put(we.e, a.ends, nullptr, &a.ctr->n_ends, a.cap, end, pk | (unsigned long long)e, 0u);
   }
 }
 
 template <int kDepth>
-__global__ void __launch_bounds__(kT2Threads) k_traverse2(TravArgs a) {
+__global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
   __shared__ uint2 hits[kT2Warps][kHitCap];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   uint2 *buf = hits[w];
   int nhit = 0;  // warp-uniform
-  unsigned long long nt = 0;
+  unsigned long long nt = 0, ntests = 0;
   int64_t p = -1;  // current query (sorted position), -1 = none
   bool exhausted = false;
-  Query q;
-  q.lo = q.hi = make_float4(0.f, 0.f, 0.f, 0.f);
+  // the last box has no later partner: queries are 0 .. N-2
+  const unsigned long long nq = a.N > 1 ? (unsigned long long)(a.N - 1) : 0ull;
+  unsigned long long q_next = 0, q_end = 0;  // the warp's query pool
+  WarpEmit we;
+  const QFrame fr = scene_frame(a.ctr, a.T);
+  QBox q = {0u, 0u, 0u, 0u};  // the query box, quantised outward like the nodes
   int32_t stack[kDepth];
   int sp = 0;
   int32_t node = 0;
   for (;;) {
-    // lanes without a query claim the next ones (one atomic per warp)
+    // lanes without a query take the next ones from the warp's pool
     unsigned need = __ballot_sync(0xffffffffu, p < 0 && !exhausted);
     if (need) {
-      unsigned long long base = 0;
-      if (lane == __ffs(need) - 1) base = atomicAdd(&a.ctr->work_next, (unsigned long long)__popc(need));
-      base = __shfl_sync(0xffffffffu, base, __ffs(need) - 1);
+      unsigned cnt = __popc(need);
+      unsigned long long have = q_end - q_next;
+      unsigned long long nb = 0;
+      if (have < cnt) {
+        if (lane == 0) nb = atomicAdd(&a.ctr->work_next, (unsigned long long)kQueryChunk);
+        nb = __shfl_sync(0xffffffffu, nb, 0);
+      }
       if (need & (1u << lane)) {
-        unsigned long long mine = base + __popc(need & lt);
-        if (mine + 1 < (unsigned long long)a.N) {  // the last box has no later partner
+        unsigned r = __popc(need & lt);
+        unsigned long long mine = r < have ? q_next + r : nb + (r - have);
+        if (mine < nq) {
           p = (int64_t)mine;
-          q.lo = __ldg(a.slo + p);
-          q.hi = __ldg(a.shi + p);
+          q = quantize_box(fr, __ldg(a.slo + p), __ldg(a.shi + p));
           node = 0;
           sp = 0;
         } else {
           exhausted = true;
         }
+      }
+      if (have < cnt) {
+        q_next = nb + (cnt - have);
+        q_end = nb + kQueryChunk;
+      } else {
+        q_next += cnt;
       }
     }
     bool active = p >= 0;
@@ -247,17 +347,23 @@ __global__ void __launch_bounds__(kT2Threads) k_traverse2(TravArgs a) {
     bool hl = false, hr = false;
     int32_t cl = 0, cr = 0;
     if (active) {
-      const float4 *np = reinterpret_cast<const float4 *>(a.nodes + node);
-      float4 lol = __ldg(np + 0), hil = __ldg(np + 1), lor = __ldg(np + 2), hir = __ldg(np + 3);
-      int4 lk = __ldg(reinterpret_cast<const int4 *>(np + 4));
+      const uint4 *np = reinterpret_cast<const uint4 *>(a.qbox + 2 * (int64_t)node);
+      uint4 bl = __ldg(np), br = __ldg(np + 1);
+      uint2 lk = __ldg(a.qlink + node);
       nt += 2;
-      bool gl = lk.z > p && box_overlap(q.lo, q.hi, lol, hil);
-      bool gr = lk.w > p && box_overlap(q.lo, q.hi, lor, hir);
-      cl = lk.x & ~kLeafBit;
-      cr = lk.y & ~kLeafBit;
-      // a leaf child that passes is an overlapping box with a later position
-      if (gl && (lk.x & kLeafBit)) { hl = true; gl = false; }
-      if (gr && (lk.y & kLeafBit)) { hr = true; gr = false; }
+      uint32_t g = lk.x & kQIndex;
+      cl = (int32_t)g;
+      cr = (int32_t)g + 1;
+      // per 16-bit lane: child lo <= query hi and query lo <= child hi
+      uint32_t ml = __vcmpleu2(bl.x, q.hi_xy) & __vcmpleu2(q.lo_xy, bl.z) &
+                    __vcmpleu2(bl.y, q.hi_zt) & __vcmpleu2(q.lo_zt, bl.w);
+      uint32_t mr = __vcmpleu2(br.x, q.hi_xy) & __vcmpleu2(q.lo_xy, br.z) &
+                    __vcmpleu2(br.y, q.hi_zt) & __vcmpleu2(q.lo_zt, br.w);
+      bool gl = (int64_t)g > p && ml == 0xffffffffu;
+      bool gr = (int64_t)lk.y > p && mr == 0xffffffffu;
+      // a leaf child that passes is a candidate box with a later position
+      if (gl && (lk.x & kQLeftLeaf)) { hl = true; gl = false; }
+      if (gr && (lk.x & kQRightLeaf)) { hr = true; gr = false; }
       if (gl && gr) {
         if (sp < kDepth) {
           stack[sp++] = cr;
@@ -284,21 +390,36 @@ __global__ void __launch_bounds__(kT2Threads) k_traverse2(TravArgs a) {
     nhit += nl + __popc(vr);
     __syncwarp();
     if (nhit > kHitCap - 64) {
-      drain_hits(a, buf, nhit);
+      drain_hits(a, buf, nhit, we);
       __syncwarp();
+      ntests += nhit;  // exact box tests, counted once per warp
       nhit = 0;
     }
   }
   __syncwarp();
-  if (nhit > 0) drain_hits(a, buf, nhit);
+  if (nhit > 0) drain_hits(a, buf, nhit, we);
+  ntests += nhit;
+  chunk_fill_holes(we.s, a.starts, a.cap);
+  if (!a.raw) chunk_fill_holes(we.e, a.ends, a.cap);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nt += __shfl_down_sync(0xffffffffu, nt, o);
-  if (lane == 0) atomicAdd(&a.ctr->node_tests, nt);
+  if (lane == 0) {
+    atomicAdd(&a.ctr->node_tests, nt);
+    atomicAdd(&a.ctr->leaf_tests, ntests);
+    if (a.raw) {
+      atomicAdd(&a.ctr->v_raw, we.s.count);
+    } else {
+      atomicAdd(&a.ctr->v_starts, we.s.count);
+      atomicAdd(&a.ctr->v_ends, we.e.count);
+    }
+  }
 }
 
 int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_bits) {
   TravArgs a;
   a.nodes = s->d_nodes.p;
+  a.qbox = s->d_qbox.p;
+  a.qlink = s->d_qlink.p;
   a.slo = s->s_lo.p;
   a.shi = s->s_hi.p;
   a.sobj = s->s_obj.p;
@@ -353,7 +474,8 @@ int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_b
 }
 
 // ---------------------------------------------------------------------------
-// Step A9: sort starts and ends (or the raw cells) and pair them up.
+// Step A9: sort starts and ends (or the raw cells) and pair them up.  Holes
+// sort last, so the first n slots of each sorted array are the n records.
 // ---------------------------------------------------------------------------
 __global__ void k_zip(const unsigned long long *__restrict__ starts,
                       const unsigned long long *__restrict__ ends, const uint32_t *__restrict__ rawv,
@@ -378,17 +500,20 @@ __global__ void k_zip(const unsigned long long *__restrict__ starts,
 
 int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits) {
   cudaStream_t st = s->stream;
-  int64_t n = raw_mode ? (int64_t)s->h_ctr.n_raw : (int64_t)s->h_ctr.n_starts;
+  // slots to sort (records plus holes) and records to keep
+  int64_t ns = raw_mode ? (int64_t)s->h_ctr.n_raw : (int64_t)s->h_ctr.n_starts;
+  int64_t ne = (int64_t)s->h_ctr.n_ends;
+  int64_t n = raw_mode ? (int64_t)s->h_ctr.v_raw : (int64_t)s->h_ctr.v_starts;
   int bits = 2 * obj_bits + t_bits;
   if (!s->d_out.ensure(n > 0 ? n : 1, st)) return SCD_ERR_OOM;
   int rc;
   if (raw_mode) {
-    rc = radix_sort_u64(s->d_starts.p, s->d_rawval.p, n, bits, s->sort_sc, st);
+    rc = radix_sort_u64(s->d_starts.p, s->d_rawval.p, ns, bits, s->sort_sc, st);
     if (rc) return rc;
   } else {
-    rc = radix_sort_u64(s->d_starts.p, nullptr, n, bits, s->sort_sc, st);
+    rc = radix_sort_u64(s->d_starts.p, nullptr, ns, bits, s->sort_sc, st);
     if (rc) return rc;
-    rc = radix_sort_u64(s->d_ends.p, nullptr, n, bits, s->sort_sc, st);
+    rc = radix_sort_u64(s->d_ends.p, nullptr, ne, bits, s->sort_sc, st);
     if (rc) return rc;
   }
   if (n > 0)
