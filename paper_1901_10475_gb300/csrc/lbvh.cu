@@ -16,14 +16,30 @@ __global__ void k_gather_sorted(const uint32_t *__restrict__ id, const float4 *_
                                 const float4 *__restrict__ hi, const uint32_t *__restrict__ obj,
                                 const K *__restrict__ keys, int64_t N, int L,
                                 float4 *__restrict__ slo, float4 *__restrict__ shi,
-                                uint32_t *__restrict__ sobj, K *__restrict__ leafkey) {
+                                uint32_t *__restrict__ sobj, K *__restrict__ leafkey,
+                                uint32_t *__restrict__ posof) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   uint32_t b = id[p];
   slo[p] = lo[b];
   shi[p] = hi[b];
   sobj[p] = obj[b];
+  if (posof) posof[b] = (uint32_t)p;
   if (p % L == 0) leafkey[p / L] = keys[p];
+}
+
+// Sorted positions of each box's previous and next segment of the same
+// object (-1 at the ends of the horizon).  Adjacent segments lie close in
+// space and time, so these positions stay near p in the Morton order.
+__global__ void k_neighbors(const uint32_t *__restrict__ id, const uint32_t *__restrict__ obj,
+                            const uint32_t *__restrict__ posof, int64_t N, int2 *__restrict__ nb) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  uint32_t u = id[p];
+  uint32_t o = obj[u];
+  int prev = (u > 0 && obj[u - 1] == o) ? (int)posof[u - 1] : -1;
+  int next = ((int64_t)u + 1 < N && obj[u + 1] == o) ? (int)posof[u + 1] : -1;
+  nb[p] = make_int2(prev, next);
 }
 
 template <class K>
@@ -170,11 +186,17 @@ static int build_impl(scd_scene *s, const K *keys_sorted, K *leafkey, int64_t &M
   if (compact && (!s->d_qbox.ensure(2 * (M > 1 ? M - 1 : 1), st) ||
                   !s->d_qlink.ensure(M > 1 ? M - 1 : 1, st)))
     return SCD_ERR_OOM;
+  if (compact && (!s->d_posof.ensure(N, st) || !s->s_nb.ensure(N, st))) return SCD_ERR_OOM;
   int bs = 256;
   k_gather_sorted<K><<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(
       s->d_id.p, s->d_lo.p, s->d_hi.p, s->d_obj.p, keys_sorted, N, L, s->s_lo.p, s->s_hi.p,
-      s->s_obj.p, leafkey);
+      s->s_obj.p, leafkey, compact ? s->d_posof.p : nullptr);
   note_launch(2);
+  if (compact) {
+    k_neighbors<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(s->d_id.p, s->d_obj.p,
+                                                              s->d_posof.p, N, s->s_nb.p);
+    note_launch();
+  }
   if (M > 1) {
     k_karras<K><<<(unsigned)((M - 1 + bs - 1) / bs), bs, 0, st>>>(
         leafkey, M, s->d_nodes.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p);

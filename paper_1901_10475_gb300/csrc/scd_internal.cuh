@@ -226,6 +226,8 @@ struct scd_scene {
   // sorted leaves and hierarchy
   scd::DevBuf<float4> s_lo, s_hi;
   scd::DevBuf<uint32_t> s_obj;
+  scd::DevBuf<uint32_t> d_posof;  // sorted position of each box id
+  scd::DevBuf<int2> s_nb;         // sorted positions of the previous / next segment (-1: none)
   scd::DevBuf<uint32_t> s_leafkey32;
   scd::DevBuf<unsigned long long> s_leafkey64;
   scd::DevBuf<scd::TravNode> d_nodes;

@@ -430,6 +430,7 @@ extern "C" SCD_API void scd_scene_destroy(scd_scene *s) {
   s->d_lo.release(st); s->d_hi.release(st); s->d_obj.release(st);
   s->d_key64.release(st); s->d_key32.release(st); s->d_id.release(st);
   s->s_lo.release(st); s->s_hi.release(st); s->s_obj.release(st);
+  s->d_posof.release(st); s->s_nb.release(st);
   s->s_leafkey32.release(st); s->s_leafkey64.release(st);
   s->d_nodes.release(st); s->d_nlo.release(st); s->d_nhi.release(st);
   s->d_qbox.release(st); s->d_qlink.release(st);

@@ -26,6 +26,7 @@ struct TravArgs {
   const uint2 *qlink;
   const float4 *slo, *shi;    // sorted boxes
   const uint32_t *sobj, *sid; // object and unsorted id of each sorted box
+  const int2 *nb;             // sorted positions of the previous / next segment
   const float4 *lo, *hi;      // unsorted boxes (object-major)
   int64_t N;
   int L;
@@ -131,6 +132,26 @@ __device__ __forceinline__ void run_ends(const TravArgs &a, const Query &q, floa
     float4 ql = q.lo, qh = q.hi, cl = bl, ch = bh;
     if (qt1 == e) { ql = __ldg(a.lo + q.uid + 1); qh = __ldg(a.hi + q.uid + 1); }
     if (bt1 == e) { cl = __ldg(a.lo + bu + 1); ch = __ldg(a.hi + bu + 1); }
+    end = !box_overlap(ql, qh, cl, ch);
+  }
+}
+
+// The same test with the neighbouring segments found by sorted position
+// (they lie close to the pair in the Morton order, so the loads hit cache).
+__device__ __forceinline__ void run_ends_sorted(const TravArgs &a, float4 ql0, float4 qh0,
+                                                int2 qn, float4 bl, float4 bh, int2 bn, int s,
+                                                int e, bool &start, bool &end) {
+  int qt0 = (int)ql0.w, qt1 = (int)qh0.w, bt0 = (int)bl.w, bt1 = (int)bh.w;
+  if (start && s > 0) {
+    float4 ql = ql0, qh = qh0, cl = bl, ch = bh;
+    if (qt0 == s) { ql = __ldg(a.slo + qn.x); qh = __ldg(a.shi + qn.x); }
+    if (bt0 == s) { cl = __ldg(a.slo + bn.x); ch = __ldg(a.shi + bn.x); }
+    start = !box_overlap(ql, qh, cl, ch);
+  }
+  if (end && e < a.T) {
+    float4 ql = ql0, qh = qh0, cl = bl, ch = bh;
+    if (qt1 == e) { ql = __ldg(a.slo + qn.y); qh = __ldg(a.shi + qn.y); }
+    if (bt1 == e) { cl = __ldg(a.slo + bn.y); ch = __ldg(a.shi + bn.y); }
     end = !box_overlap(ql, qh, cl, ch);
   }
 }
@@ -247,7 +268,9 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a) {
 constexpr int kT2Threads = 128;
 constexpr int kT2Warps = kT2Threads / 32;
 constexpr int kHitCap = 256;  // per warp; drained when fewer than 64 slots remain
-constexpr unsigned kQueryChunk = 256;  // queries claimed per warp atomic
+// queries claimed per warp atomic; small, so that the queries in flight stay
+// a narrow window of the Morton order and their nodes stay in L2
+constexpr unsigned kQueryChunk = 32;
 
 struct WarpEmit {
   ChunkCursor s, e;  // start and end record chunks (raw cells use s)
@@ -259,33 +282,30 @@ __device__ __forceinline__ void drain_hits(const TravArgs &a, const uint2 *buf, 
   for (int base = 0; base < cnt; base += 32) {
     int k = base + lane;
     bool valid = k < cnt;
-    Query q;
-    float4 bl = make_float4(0.f, 0.f, 0.f, 0.f), bh = bl;
-    uint32_t bo = 0, bu = 0;
-    q.lo = q.hi = bl;
-    q.obj = q.uid = 0;
+    float4 ql = make_float4(0.f, 0.f, 0.f, 0.f), qh = ql, bl = ql, bh = ql;
+    uint32_t qo = 0, bo = 0;
+    uint2 h = make_uint2(0u, 0u);
     if (valid) {
-      uint2 h = buf[k];
-      q.lo = __ldg(a.slo + h.x);
-      q.hi = __ldg(a.shi + h.x);
-      q.obj = __ldg(a.sobj + h.x);
-      q.uid = __ldg(a.sid + h.x);
+      h = buf[k];
+      ql = __ldg(a.slo + h.x);
+      qh = __ldg(a.shi + h.x);
+      qo = __ldg(a.sobj + h.x);
       bl = __ldg(a.slo + h.y);
       bh = __ldg(a.shi + h.y);
       bo = __ldg(a.sobj + h.y);
-      bu = __ldg(a.sid + h.y);
       // the tree test was on quantised boxes: decide on the exact ones
-      valid = bo != q.obj && box_overlap(q.lo, q.hi, bl, bh);
+      valid = bo != qo && box_overlap(ql, qh, bl, bh);
     }
-    int s = max((int)q.lo.w, (int)bl.w), e = min((int)q.hi.w, (int)bh.w);
-    unsigned long long pk = pair_key(a, q.obj, bo);
+    int s = max((int)ql.w, (int)bl.w), e = min((int)qh.w, (int)bh.w);
+    unsigned long long pk = pair_key(a, qo, bo);
     if (a.raw) {
       chunk_put(we.s, a.starts, a.rawval, &a.ctr->n_raw, a.cap, valid,
                 pk | (unsigned long long)s, (uint32_t)e);
       continue;
     }
     bool start = valid, end = valid;
-    if (valid) run_ends(a, q, bl, bh, bu, s, e, start, end);
+    if (valid)
+      run_ends_sorted(a, ql, qh, __ldg(a.nb + h.x), bl, bh, __ldg(a.nb + h.y), s, e, start, end);
     chunk_put(we.s, a.starts, nullptr, &a.ctr->n_starts, a.cap, start,
               pk | (unsigned long long)s, 0u);
     chunk_put(we.e, a.ends, nullptr, &a.ctr->n_ends, a.cap, end, pk | (unsigned long long)e, 0u);
@@ -424,6 +444,7 @@ int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_b
   a.shi = s->s_hi.p;
   a.sobj = s->s_obj.p;
   a.sid = s->d_id.p;
+  a.nb = s->s_nb.p;
   a.lo = s->d_lo.p;
   a.hi = s->d_hi.p;
   a.N = s->N;
