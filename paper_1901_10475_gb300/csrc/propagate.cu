@@ -38,13 +38,45 @@ __device__ __forceinline__ double kepler_E(double M, double e, int &iters) {
   return E;
 }
 
+// Kepler's equation for M in [-pi, pi], mixed precision: Newton in FP32 to
+// about 3e-7 rad, then one FP64 Newton step, which squares that error (to
+// below 2e-13 rad for e <= 0.75, i.e. below 1e-8 km of position at GEO
+// distance).  Returns E with sin E and cos E, corrected to second order in
+// the last step, so the caller needs no further FP64 sincos.
+__device__ __forceinline__ double kepler_E_sc(double M, double e, double &sE, double &cE,
+                                              int &iters) {
+  if (e == 0.0) {
+    sincos(M, &sE, &cE);
+    iters = 0;
+    return M;
+  }
+  const float Mf = (float)M, ef = (float)e;
+  float E = (ef <= 0.5f) ? Mf + ef * sinf(Mf) : Mf + 0.85f * ef * (Mf >= 0.f ? 1.f : -1.f);
+  int it = 0;
+  for (; it < kKeplerMaxIter; ++it) {
+    float s, c;
+    sincosf(E, &s, &c);
+    float d = (E - ef * s - Mf) / (1.0f - ef * c);
+    E -= d;
+    if (fabsf(d) <= 1e-6f) break;
+  }
+  iters = it + 1;
+  double Ed = (double)E, s, c;
+  sincos(Ed, &s, &c);
+  double d = (Ed - e * s - M) / (1.0 - e * c);
+  // sin(E - d), cos(E - d) to second order in d
+  double h = 0.5 * d * d;
+  sE = s - d * c - h * s;
+  cE = c + d * s - h * c;
+  return Ed - d;
+}
+
 // position at time t [s] from the per-object constants
 __device__ __forceinline__ void position_at(const ObjParams &p, double t, double out[3],
                                             int &iters) {
   double M = reduce_2pi(p.M0 + p.n * t);
-  double E = kepler_E(M, p.e, iters);
   double s, c;
-  sincos(E, &s, &c);
+  kepler_E_sc(M, p.e, s, c, iters);
   double ce = c - p.e;
 #pragma unroll
   for (int k = 0; k < 3; ++k) out[k] = fma(p.A[k], ce, p.B[k] * s);
