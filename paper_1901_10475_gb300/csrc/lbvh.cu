@@ -17,14 +17,17 @@ __global__ void k_gather_sorted(const uint32_t *__restrict__ id, const float4 *_
                                 const K *__restrict__ keys, int64_t N, int L,
                                 float4 *__restrict__ slo, float4 *__restrict__ shi,
                                 uint32_t *__restrict__ sobj, K *__restrict__ leafkey,
-                                uint32_t *__restrict__ posof) {
+                                uint32_t *__restrict__ posof, int cell_shift,
+                                uint32_t *__restrict__ scell) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   uint32_t b = id[p];
   slo[p] = lo[b];
   shi[p] = hi[b];
   sobj[p] = obj[b];
+  // a box referenced from several cells: any copy will do, their data agree
   if (posof) posof[b] = (uint32_t)p;
+  if (scell) scell[p] = (uint32_t)((unsigned long long)keys[p] >> cell_shift);
   if (p % L == 0) leafkey[p / L] = keys[p];
 }
 
@@ -32,13 +35,14 @@ __global__ void k_gather_sorted(const uint32_t *__restrict__ id, const float4 *_
 // object (-1 at the ends of the horizon).  Adjacent segments lie close in
 // space and time, so these positions stay near p in the Morton order.
 __global__ void k_neighbors(const uint32_t *__restrict__ id, const uint32_t *__restrict__ obj,
-                            const uint32_t *__restrict__ posof, int64_t N, int2 *__restrict__ nb) {
+                            const uint32_t *__restrict__ posof, int64_t Nq, int64_t nbox,
+                            int2 *__restrict__ nb) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= N) return;
+  if (p >= Nq) return;
   uint32_t u = id[p];
   uint32_t o = obj[u];
   int prev = (u > 0 && obj[u - 1] == o) ? (int)posof[u - 1] : -1;
-  int next = ((int64_t)u + 1 < N && obj[u + 1] == o) ? (int)posof[u + 1] : -1;
+  int next = ((int64_t)u + 1 < nbox && obj[u + 1] == o) ? (int)posof[u + 1] : -1;
   nb[p] = make_int2(prev, next);
 }
 
@@ -63,7 +67,7 @@ __device__ __forceinline__ int delta(const K *__restrict__ keys, int64_t M, int6
 template <class K>
 __global__ void k_karras(const K *__restrict__ keys, int64_t M, TravNode *__restrict__ nodes,
                          int32_t *__restrict__ parent_int, int32_t *__restrict__ parent_leaf,
-                         uint32_t *__restrict__ flags) {
+                         uint32_t *__restrict__ flags, int32_t *__restrict__ first_out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M - 1) return;
   // direction of the node's range
@@ -98,6 +102,7 @@ __global__ void k_karras(const K *__restrict__ keys, int64_t M, TravNode *__rest
   if (last == gamma + 1) parent_leaf[gamma + 1] = (int32_t)i; else parent_int[gamma + 1] = (int32_t)i;
   if (i == 0) parent_int[0] = -1;
   flags[i] = 0;
+  if (first_out) first_out[i] = (int32_t)first;
 }
 
 __device__ __forceinline__ float4 f4min(float4 a, float4 b) {
@@ -171,53 +176,64 @@ __global__ void k_refit(const float4 *__restrict__ slo, const float4 *__restrict
 }
 
 template <class K>
-static int build_impl(scd_scene *s, const K *keys_sorted, K *leafkey, int64_t &M) {
+int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, int64_t Nq,
+               K *leafkey, int cell_shift, int64_t &M) {
   cudaStream_t st = s->stream;
-  int64_t N = s->N;
   int L = s->tune.leaf_size;
-  M = (N + L - 1) / L;
-  if (!s->s_lo.ensure(N, st) || !s->s_hi.ensure(N, st) || !s->s_obj.ensure(N, st) ||
+  M = (Nq + L - 1) / L;
+  if (!s->s_lo.ensure(Nq, st) || !s->s_hi.ensure(Nq, st) || !s->s_obj.ensure(Nq, st) ||
       !s->d_leaflo.ensure(M, st) || !s->d_leafhi.ensure(M, st) ||
       !s->d_nodes.ensure(M > 1 ? M - 1 : 1, st) || !s->d_nlo.ensure(M > 1 ? M - 1 : 1, st) ||
       !s->d_nhi.ensure(M > 1 ? M - 1 : 1, st) || !s->d_parent_int.ensure(M, st) ||
       !s->d_parent_leaf.ensure(M, st) || !s->d_flags.ensure(M, st))
     return SCD_ERR_OOM;
   const bool compact = L == 1;
+  const bool cells = cell_shift >= 0;
   if (compact && (!s->d_qbox.ensure(2 * (M > 1 ? M - 1 : 1), st) ||
                   !s->d_qlink.ensure(M > 1 ? M - 1 : 1, st)))
     return SCD_ERR_OOM;
-  if (compact && (!s->d_posof.ensure(N, st) || !s->s_nb.ensure(N, st))) return SCD_ERR_OOM;
+  if (compact && (!s->d_posof.ensure(s->N, st) || !s->s_nb.ensure(Nq, st))) return SCD_ERR_OOM;
+  if (cells && (!s->s_cell.ensure(Nq, st) || !s->d_first.ensure(M > 1 ? M - 1 : 1, st)))
+    return SCD_ERR_OOM;
   int bs = 256;
-  k_gather_sorted<K><<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(
-      s->d_id.p, s->d_lo.p, s->d_hi.p, s->d_obj.p, keys_sorted, N, L, s->s_lo.p, s->s_hi.p,
-      s->s_obj.p, leafkey, compact ? s->d_posof.p : nullptr);
+  k_gather_sorted<K><<<(unsigned)((Nq + bs - 1) / bs), bs, 0, st>>>(
+      ids_sorted, s->d_lo.p, s->d_hi.p, s->d_obj.p, keys_sorted, Nq, L, s->s_lo.p, s->s_hi.p,
+      s->s_obj.p, leafkey, compact ? s->d_posof.p : nullptr, cell_shift,
+      cells ? s->s_cell.p : nullptr);
   note_launch(2);
   if (compact) {
-    k_neighbors<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(s->d_id.p, s->d_obj.p,
-                                                              s->d_posof.p, N, s->s_nb.p);
+    k_neighbors<<<(unsigned)((Nq + bs - 1) / bs), bs, 0, st>>>(ids_sorted, s->d_obj.p,
+                                                               s->d_posof.p, Nq, s->N, s->s_nb.p);
     note_launch();
   }
   if (M > 1) {
     k_karras<K><<<(unsigned)((M - 1 + bs - 1) / bs), bs, 0, st>>>(
-        leafkey, M, s->d_nodes.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p);
+        leafkey, M, s->d_nodes.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p,
+        cells ? s->d_first.p : nullptr);
     note_launch();
   }
   k_refit<<<(unsigned)((M + bs - 1) / bs), bs, 0, st>>>(
-      s->s_lo.p, s->s_hi.p, N, L, M, s->d_leaflo.p, s->d_leafhi.p, s->d_nodes.p, s->d_nlo.p,
+      s->s_lo.p, s->s_hi.p, Nq, L, M, s->d_leaflo.p, s->d_leafhi.p, s->d_nodes.p, s->d_nlo.p,
       s->d_nhi.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p,
       compact ? s->d_qbox.p : nullptr, compact ? s->d_qlink.p : nullptr, s->d_ctr.p, s->T);
   return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
 }
 
+template int build_tree<uint32_t>(scd_scene *, const uint32_t *, const uint32_t *, int64_t,
+                                  uint32_t *, int, int64_t &);
+template int build_tree<unsigned long long>(scd_scene *, const unsigned long long *,
+                                            const uint32_t *, int64_t, unsigned long long *, int,
+                                            int64_t &);
+
 int build_hierarchy(scd_scene *s, int64_t &n_leaves) {
-  if (s->tune.morton_bits > 8) {
-    int64_t Mx = (s->N + s->tune.leaf_size - 1) / s->tune.leaf_size;
-    if (!s->s_leafkey64.ensure(Mx, s->stream)) return SCD_ERR_OOM;
-    return build_impl<unsigned long long>(s, s->d_key64.p, s->s_leafkey64.p, n_leaves);
-  }
   int64_t Mx = (s->N + s->tune.leaf_size - 1) / s->tune.leaf_size;
+  if (s->tune.morton_bits > 8) {
+    if (!s->s_leafkey64.ensure(Mx, s->stream)) return SCD_ERR_OOM;
+    return build_tree<unsigned long long>(s, s->d_key64.p, s->d_id.p, s->N, s->s_leafkey64.p, -1,
+                                          n_leaves);
+  }
   if (!s->s_leafkey32.ensure(Mx, s->stream)) return SCD_ERR_OOM;
-  return build_impl<uint32_t>(s, s->d_key32.p, s->s_leafkey32.p, n_leaves);
+  return build_tree<uint32_t>(s, s->d_key32.p, s->d_id.p, s->N, s->s_leafkey32.p, -1, n_leaves);
 }
 
 }  // namespace scd

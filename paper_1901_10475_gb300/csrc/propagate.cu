@@ -234,25 +234,6 @@ __device__ __forceinline__ void cos_range(double x0, double x1, double &lo, doub
   if (ceil((x0 - kPi) * (1.0 / kTwoPi)) * kTwoPi + kPi <= x1) lo = -1.0;
 }
 
-__device__ __forceinline__ uint32_t quantize(float u, int bits) {
-  float s = (float)(1u << bits);
-  float q = floorf(u * s);
-  q = fminf(fmaxf(q, 0.0f), s - 1.0f);
-  return (uint32_t)q;
-}
-
-__device__ __forceinline__ unsigned long long morton4(uint32_t x, uint32_t y, uint32_t z,
-                                                      uint32_t t, int bits) {
-  unsigned long long key = 0;
-  for (int b = 0; b < bits; ++b) {
-    key |= (unsigned long long)((t >> b) & 1u) << (4 * b + 0);
-    key |= (unsigned long long)((z >> b) & 1u) << (4 * b + 1);
-    key |= (unsigned long long)((y >> b) & 1u) << (4 * b + 2);
-    key |= (unsigned long long)((x >> b) & 1u) << (4 * b + 3);
-  }
-  return key;
-}
-
 __global__ void __launch_bounds__(256) k_build_boxes(BoxArgs a) {
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.N) return;
@@ -315,25 +296,7 @@ __global__ void __launch_bounds__(256) k_build_boxes(BoxArgs a) {
 
   // 4D Morton key of the box centre in the scene's bounding cube
   double R = __longlong_as_double((long long)a.ctr->extent_bits);
-  float ux, uy, uz;
-  if (a.space_warp) {
-    // sign(x) log(1 + |x|/s) / log(1 + R/s): monotone, so any key order is a
-    // valid tree order; it spends more key bits where most boxes are
-    const float s_km = 1000.0f;
-    float inv = 0.5f / log1pf((float)R / s_km);
-    float cx = 0.5f * (L.x + H.x), cy = 0.5f * (L.y + H.y), cz = 0.5f * (L.z + H.z);
-    ux = copysignf(log1pf(fabsf(cx) / s_km), cx) * inv + 0.5f;
-    uy = copysignf(log1pf(fabsf(cy) / s_km), cy) * inv + 0.5f;
-    uz = copysignf(log1pf(fabsf(cz) / s_km), cz) * inv + 0.5f;
-  } else {
-    float inv = (float)(0.5 / R);
-    ux = (0.5f * (L.x + H.x)) * inv + 0.5f;
-    uy = (0.5f * (L.y + H.y)) * inv + 0.5f;
-    uz = (0.5f * (L.z + H.z)) * inv + 0.5f;
-  }
-  float ut = (float)((0.5 * (double)(tlo + thi)) / (double)(a.T + 1)) * a.time_scale;
-  unsigned long long key = morton4(quantize(ux, a.bits), quantize(uy, a.bits),
-                                   quantize(uz, a.bits), quantize(ut, a.bits), a.bits);
+  unsigned long long key = box_morton(L, H, R, a.T, a.bits, a.time_scale, a.space_warp);
   if (a.key64) a.key64[b] = key;
   else a.key32[b] = (uint32_t)key;
 }

@@ -123,6 +123,63 @@ __host__ __device__ inline QBox quantize_box(const QFrame &f, float4 lo, float4 
   return q;
 }
 
+__device__ inline uint32_t quantize(float u, int bits) {
+  float s = (float)(1u << bits);
+  float q = floorf(u * s);
+  q = fminf(fmaxf(q, 0.0f), s - 1.0f);
+  return (uint32_t)q;
+}
+
+__device__ inline unsigned long long morton4(uint32_t x, uint32_t y, uint32_t z, uint32_t t,
+                                             int bits) {
+  unsigned long long key = 0;
+  for (int b = 0; b < bits; ++b) {
+    key |= (unsigned long long)((t >> b) & 1u) << (4 * b + 0);
+    key |= (unsigned long long)((z >> b) & 1u) << (4 * b + 1);
+    key |= (unsigned long long)((y >> b) & 1u) << (4 * b + 2);
+    key |= (unsigned long long)((x >> b) & 1u) << (4 * b + 3);
+  }
+  return key;
+}
+
+// 4D Morton key (bits per axis) of a box centre in the scene cube [-R, R]^3
+// x [0, T]; optionally log-compressed in space (a monotone map, so any key
+// order is a valid tree order)
+__device__ inline unsigned long long box_morton(float4 L, float4 H, double R, int64_t T, int bits,
+                                                float time_scale, int space_warp) {
+  float ux, uy, uz;
+  if (space_warp) {
+    const float s_km = 1000.0f;
+    float inv = 0.5f / log1pf((float)R / s_km);
+    float cx = 0.5f * (L.x + H.x), cy = 0.5f * (L.y + H.y), cz = 0.5f * (L.z + H.z);
+    ux = copysignf(log1pf(fabsf(cx) / s_km), cx) * inv + 0.5f;
+    uy = copysignf(log1pf(fabsf(cy) / s_km), cy) * inv + 0.5f;
+    uz = copysignf(log1pf(fabsf(cz) / s_km), cz) * inv + 0.5f;
+  } else {
+    float inv = (float)(0.5 / R);
+    ux = (0.5f * (L.x + H.x)) * inv + 0.5f;
+    uy = (0.5f * (L.y + H.y)) * inv + 0.5f;
+    uz = (0.5f * (L.z + H.z)) * inv + 0.5f;
+  }
+  float ut = (float)((0.5 * ((double)L.w + (double)H.w)) / (double)(T + 1)) * time_scale;
+  return morton4(quantize(ux, bits), quantize(uy, bits), quantize(uz, bits), quantize(ut, bits),
+                 bits);
+}
+
+// decomposition cells: the tick slab of t, and the altitude band of radius x
+// (the number of band edges <= x)
+__device__ inline int slab_of(int64_t t, int n_slabs, int64_t T) {
+  return (int)((t * (int64_t)n_slabs) / (T + 1));
+}
+__device__ inline int band_of(double x, const double *edges, int p) {
+  int lo = 0, hi = p - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (edges[mid] <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
 __host__ __device__ inline bool box_overlap(const float4 &la, const float4 &ha,
                                             const float4 &lb, const float4 &hb) {
   // closed boxes: overlap iff every axis overlaps
@@ -228,6 +285,20 @@ struct scd_scene {
   scd::DevBuf<uint32_t> s_obj;
   scd::DevBuf<uint32_t> d_posof;  // sorted position of each box id
   scd::DevBuf<int2> s_nb;         // sorted positions of the previous / next segment (-1: none)
+  scd::DevBuf<uint32_t> s_cell;   // decomposition cell of each sorted reference
+  scd::DevBuf<int32_t> d_first;   // first leaf under each internal node
+
+  // static decomposition: references (cell, box) and per-cell subtrees
+  int64_t n_refs = 0;
+  int n_cells = 0;
+  int dkind = 0, n_slabs = 0, p_bands = 0;  // decomposition of the last find_pairs
+  scd::DevBuf<int64_t> d_refcnt, d_refoff;
+  scd::DevBuf<unsigned long long> d_refkey;
+  scd::DevBuf<uint32_t> d_refid;
+  scd::DevBuf<double2> d_rr;       // padded radial range of each object
+  scd::DevBuf<double> d_edges;     // altitude band edges (p - 1)
+  scd::DevBuf<unsigned long long> d_abits;  // semi-major axes as sortable bits
+  scd::DevBuf<int32_t> d_cellroot; // root node of each cell (-1: fewer than 2 refs)
   scd::DevBuf<uint32_t> s_leafkey32;
   scd::DevBuf<unsigned long long> s_leafkey64;
   scd::DevBuf<scd::TravNode> d_nodes;
@@ -262,6 +333,11 @@ int launch_build_boxes(scd_scene *s);
 int launch_propagate(const scd_element *d_el, int64_t n, const uint32_t *obj, const double *t,
                      int64_t m, double *out, cudaStream_t st);
 int build_hierarchy(scd_scene *s, int64_t &n_leaves);
+template <class K>
+int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, int64_t Nq,
+               K *leafkey, int cell_shift, int64_t &M);
+// decomposed screen: references, their sort, the tree and each cell's root
+int build_decomposed(scd_scene *s, const scd_decomp *d, int64_t &n_leaves);
 int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_bits);
 int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits);
 }  // namespace scd

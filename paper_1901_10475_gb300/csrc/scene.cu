@@ -257,27 +257,51 @@ static int bits_for(int64_t v) {
 static int find_pairs_impl(scd_scene *s, const scd_decomp *d, int raw_mode) {
   if (!s) return SCD_ERR_INVALID_ARG;
   if (!s->boxes_built) return SCD_ERR_STATE;
-  if (d && d->kind != SCD_DECOMP_NONE) {
-    if (d->kind != SCD_DECOMP_ALT_BANDS && d->kind != SCD_DECOMP_SLAB_OCT)
+  int dkind = d ? d->kind : SCD_DECOMP_NONE;
+  if (dkind != SCD_DECOMP_NONE) {
+    if (dkind == SCD_DECOMP_SLAB_OCT) {
+      if (d->n_slabs < 1 || d->n_slabs > 4096) return SCD_ERR_INVALID_ARG;
+    } else if (dkind == SCD_DECOMP_ALT_BANDS) {
+      if (d->p_bands < 1 || d->p_bands > 4096 || d->p_bands > s->n) return SCD_ERR_INVALID_ARG;
+    } else {
       return SCD_ERR_INVALID_ARG;
-    return SCD_ERR_INVALID_ARG;  // decompositions are served by the batched path
+    }
+    if (raw_mode) return SCD_ERR_INVALID_ARG;
   }
   cudaStream_t st = s->stream;
   int ob = bits_for(s->n - 1), tb = bits_for(s->T);
   if (2 * ob + tb > 64) return SCD_ERR_INVALID_ARG;
   int64_t N = s->N;
+  s->dkind = dkind;
+  s->n_slabs = dkind == SCD_DECOMP_SLAB_OCT ? d->n_slabs : 0;
+  s->p_bands = dkind == SCD_DECOMP_ALT_BANDS ? d->p_bands : 0;
+  // the decomposed traversal runs on one-box leaves
+  const int leaf_saved = s->tune.leaf_size;
+  if (dkind != SCD_DECOMP_NONE) s->tune.leaf_size = 1;
+  struct Restore {
+    scd_scene *s;
+    int leaf;
+    ~Restore() { s->tune.leaf_size = leaf; }
+  } restore{s, leaf_saved};
   if (s->events_ready) cudaEventRecord(s->ev[2], st);
-  // A5: sort box ids along the Morton curve (ids were reset by build_boxes)
-  int kb = 4 * s->tune.morton_bits;
-  if (s->tune.morton_bits > 8) {
-    TRY(radix_sort_u64(s->d_key64.p, s->d_id.p, N, kb, s->sort_sc, st));
-  } else {
-    TRY(radix_sort_u32(s->d_key32.p, s->d_id.p, N, kb, s->sort_sc, st));
-  }
-  if (s->events_ready) cudaEventRecord(s->ev[3], st);
-  // A6-A7: hierarchy and refit
   int64_t M = 0;
-  TRY(build_hierarchy(s, M));
+  if (dkind == SCD_DECOMP_NONE) {
+    // A5: sort box ids along the Morton curve
+    int kb = 4 * s->tune.morton_bits;
+    if (s->tune.morton_bits > 8) {
+      TRY(radix_sort_u64(s->d_key64.p, s->d_id.p, N, kb, s->sort_sc, st));
+    } else {
+      TRY(radix_sort_u32(s->d_key32.p, s->d_id.p, N, kb, s->sort_sc, st));
+    }
+    if (s->events_ready) cudaEventRecord(s->ev[3], st);
+    // A6-A7: hierarchy and refit
+    TRY(build_hierarchy(s, M));
+  } else {
+    // A10: references per cell, their sort, the hierarchy and cell roots
+    if (s->events_ready) cudaEventRecord(s->ev[3], st);
+    TRY(build_decomposed(s, d, M));
+    N = s->n_refs;
+  }
   if (s->events_ready) cudaEventRecord(s->ev[4], st);
   // A8: traversal, retried with more room when the buffers overflow
   if (s->pair_cap == 0) s->pair_cap = std::max<int64_t>(1 << 16, N / 4);
@@ -440,6 +464,10 @@ extern "C" SCD_API void scd_scene_destroy(scd_scene *s) {
   s->d_starts.release(st); s->d_ends.release(st); s->d_rawval.release(st);
   s->d_out.release(st);
   s->sort_sc.release(st);
+  s->s_cell.release(st); s->d_first.release(st);
+  s->d_refcnt.release(st); s->d_refoff.release(st); s->d_refkey.release(st);
+  s->d_refid.release(st); s->d_rr.release(st); s->d_edges.release(st);
+  s->d_abits.release(st); s->d_cellroot.release(st);
   if (s->events_ready)
     for (int k = 0; k < 8; ++k) cudaEventDestroy(s->ev[k]);
   if (s->h_ctr_pinned) cudaFreeHost(s->h_ctr_pinned);

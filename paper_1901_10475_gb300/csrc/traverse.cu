@@ -38,7 +38,35 @@ struct TravArgs {
   uint32_t *rawval;
   unsigned long long cap;
   DevCounters *ctr;
+  // static decomposition (kind SCD_DECOMP_NONE: one tree, root 0)
+  int dkind;
+  int n_slabs, p_bands;
+  const uint32_t *scell;     // cell of each sorted reference
+  const int32_t *cellroot;   // root node of each cell's subtree (-1: none)
+  const double2 *rr;         // radial ranges (ALT_BANDS)
+  const double *edges;       // band edges (ALT_BANDS)
 };
+
+// Is `cell` the one cell that reports the overlapping pair (q, b)?  The
+// lower corner of the boxes' intersection (SLAB_OCT), or the lower end of
+// the two objects' common radial range (ALT_BANDS, which also drops pairs
+// with no potential-collision edge).
+__device__ __forceinline__ bool reports_here(const TravArgs &a, uint32_t cell, float4 ql, float4 bl,
+                                             uint32_t qo, uint32_t bo) {
+  if (a.dkind == SCD_DECOMP_SLAB_OCT) {
+    float cx = fmaxf(ql.x, bl.x), cy = fmaxf(ql.y, bl.y), cz = fmaxf(ql.z, bl.z);
+    int64_t ct = (int64_t)fmaxf(ql.w, bl.w);
+    uint32_t c = (uint32_t)(slab_of(ct, a.n_slabs, a.T) * 8 + ((cx >= 0.f) << 2) +
+                            ((cy >= 0.f) << 1) + (cz >= 0.f));
+    return c == cell;
+  }
+  if (a.dkind == SCD_DECOMP_ALT_BANDS) {
+    double2 r1 = a.rr[qo], r2 = a.rr[bo];
+    double lo = fmax(r1.x, r2.x), hi = fmin(r1.y, r2.y);
+    return lo <= hi && (uint32_t)band_of(lo, a.edges, a.p_bands) == cell;
+  }
+  return true;
+}
 
 // a slot that holds no record: all key bits set, so it sorts after every
 // real record (whose object fields can never be all ones)
@@ -295,6 +323,8 @@ __device__ __forceinline__ void drain_hits(const TravArgs &a, const uint2 *buf, 
       bo = __ldg(a.sobj + h.y);
       // the tree test was on quantised boxes: decide on the exact ones
       valid = bo != qo && box_overlap(ql, qh, bl, bh);
+      if (valid && a.dkind != SCD_DECOMP_NONE)
+        valid = reports_here(a, __ldg(a.scell + h.x), ql, bl, qo, bo);
     }
     int s = max((int)ql.w, (int)bl.w), e = min((int)qh.w, (int)bh.w);
     unsigned long long pk = pair_key(a, qo, bo);
@@ -348,8 +378,10 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
         if (mine < nq) {
           p = (int64_t)mine;
           q = quantize_box(fr, __ldg(a.slo + p), __ldg(a.shi + p));
-          node = 0;
+          // the query starts at the root of its own cell's subtree
+          node = a.dkind == SCD_DECOMP_NONE ? 0 : __ldg(a.cellroot + __ldg(a.scell + p));
           sp = 0;
+          if (node < 0) p = -1;  // alone in its cell: nothing to find
         } else {
           exhausted = true;
         }
@@ -459,6 +491,14 @@ int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_b
   a.rawval = s->d_rawval.p;
   a.cap = (unsigned long long)s->pair_cap;
   a.ctr = s->d_ctr.p;
+  a.dkind = s->dkind;
+  a.n_slabs = s->n_slabs;
+  a.p_bands = s->p_bands;
+  a.scell = s->s_cell.p;
+  a.cellroot = s->d_cellroot.p;
+  a.rr = s->d_rr.p;
+  a.edges = s->d_edges.p;
+  if (a.dkind != SCD_DECOMP_NONE) a.N = s->n_refs;  // one query per reference
   if (a.L == 1) {
     // persistent: as many blocks as fit on the GPU at once
     static int sms = 0;
