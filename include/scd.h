@@ -139,6 +139,23 @@ typedef struct {
 
 typedef struct scd_scene scd_scene;
 
+/* Learned step model (SCD_STEP_LEARNED; not in the paper): a network from 8
+ * per-object features to the log of the step in seconds, 8 -> 64 -> 64 -> 1
+ * with ReLU, BF16 weights and FP32 accumulation, FP32 master weights trained
+ * with AdamW on mean squared error.  Parameters, flat FP32 in this order:
+ * W1[8][64], b1[64], W2[64][64], b2[64], w3[64], b3.  Features of an object
+ * (scd_stepnet_features): log(a / 6378.137 km), e, sin i, cos i,
+ * log(perigee altitude / 100 km), log(apogee altitude / 100 km),
+ * log(period / 3600 s), log(1 + number of other objects with |a' - a| <= 50
+ * km); altitudes floored at 1 km.  A scene with SCD_STEP_LEARNED uses
+ * exp(output) clamped to [P/400, P/50]; every box still bounds its whole
+ * segment, so any step keeps the screen sound.  A network must outlive the
+ * scenes that use it. */
+#define SCD_STEPNET_IN 8
+#define SCD_STEPNET_HIDDEN 64
+#define SCD_STEPNET_PARAMS 4801
+typedef struct scd_stepnet scd_stepnet;
+
 /* Device memory hooks (e.g. a framework's caching allocator).  alloc returns
  * NULL on failure.  Passing NULLs restores cudaMalloc/cudaFree.  Applies to
  * allocations made after the call, process-wide. */
@@ -235,6 +252,35 @@ SCD_API int scd_propagate_noalloc(const scd_element *d_elems, int64_t n, const u
  * small (all counts still reported). */
 SCD_API int scd_batch_find_pairs(scd_scene *const *scenes, int n_scenes, const scd_decomp *d,
                                  scd_pair *const *outs, const int64_t *caps, int64_t *n_outs);
+
+/* Step network: create (He-style initial weights from seed; work is queued
+ * on cuda_stream), set/get the FP32 parameters (host arrays of
+ * SCD_STEPNET_PARAMS floats; setting resets the optimiser), features of n
+ * elements (device arrays; d_feat is n x 8 floats), forward pass (device
+ * d_x n x 8, d_y n), gradient of the mean squared error over n samples
+ * (device d_t n targets, d_grad SCD_STEPNET_PARAMS floats, *loss_out the
+ * loss), one AdamW step (beta 0.9, 0.999, eps 1e-8, decoupled weight decay on
+ * the weights), checkpoint save/load (magic "SCDNET01", version, parameter
+ * count, optimiser step, FP32 parameters), destroy. */
+SCD_API int scd_stepnet_create(void *cuda_stream, uint64_t seed, scd_stepnet **out);
+SCD_API int scd_stepnet_set_params(scd_stepnet *net, const float *host_params, int64_t count);
+SCD_API int scd_stepnet_get_params(const scd_stepnet *net, float *host_params, int64_t count);
+SCD_API int scd_stepnet_features(const scd_element *d_elems, int64_t n, float *d_feat,
+                                 void *cuda_stream);
+SCD_API int scd_stepnet_forward(const scd_stepnet *net, const float *d_x, int64_t n, float *d_y);
+SCD_API int scd_stepnet_grad(scd_stepnet *net, const float *d_x, const float *d_t, int64_t n,
+                             float *d_grad, float *loss_out);
+SCD_API int scd_stepnet_train_step(scd_stepnet *net, const float *d_x, const float *d_t,
+                                   int64_t n, float lr, float weight_decay, float *loss_out);
+SCD_API int scd_stepnet_save(const scd_stepnet *net, const char *path);
+SCD_API int scd_stepnet_load(scd_stepnet *net, const char *path);
+SCD_API void scd_stepnet_destroy(scd_stepnet *net);
+
+/* Candidate count per object: for each of n_pairs device pairs, add one to
+ * d_counts[i] and d_counts[j] (device array of n_objects, not cleared here).
+ * Used to attribute screening work to objects for step training. */
+SCD_API int scd_count_pairs_per_object(const scd_pair *d_pairs, int64_t n_pairs, int64_t n_objects,
+                                       uint32_t *d_counts, void *cuda_stream);
 
 /* Metrics of the scene's last find_pairs as one JSON object (box count,
  * node and leaf tests, pair counts, kernel times).  Writes at most cap bytes

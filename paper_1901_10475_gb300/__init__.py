@@ -25,6 +25,10 @@ from ._binding import (PAIR_DTYPE, SCD_BOX_INTERVAL, SCD_BOX_SPEED, SCD_DECOMP_A
                        scd_scene_set_elements_device, scd_scene_set_tuning,
                        scd_status_string)
 
+for _n in dir(B):  # every entry point and constant under its C name
+    if _n.startswith("scd_") or _n.startswith("SCD_"):
+        globals()[_n] = getattr(B, _n)
+
 __all__ = [n for n in dir(B) if n.startswith("scd_") or n.startswith("SCD_")] + [
     "Scene", "device_view", "PAIR_DTYPE", "ScdError", "make_step_policy"]
 

@@ -103,6 +103,18 @@ def lib() -> ctypes.CDLL:
             "scd_propagate_noalloc": (i32, [vp, i64, vp, vp, i64, vp, vp]),
             "scd_batch_find_pairs": (i32, [P(vp), i32, P(scd_decomp), P(vp), P(i64), P(i64)]),
             "scd_last_metrics": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t]),
+            "scd_stepnet_create": (i32, [vp, ctypes.c_uint64, P(vp)]),
+            "scd_stepnet_set_params": (i32, [vp, vp, i64]),
+            "scd_stepnet_get_params": (i32, [vp, vp, i64]),
+            "scd_stepnet_features": (i32, [vp, i64, vp, vp]),
+            "scd_stepnet_forward": (i32, [vp, vp, i64, vp]),
+            "scd_stepnet_grad": (i32, [vp, vp, vp, i64, vp, P(ctypes.c_float)]),
+            "scd_stepnet_train_step": (i32, [vp, vp, vp, i64, ctypes.c_float, ctypes.c_float,
+                                             P(ctypes.c_float)]),
+            "scd_stepnet_save": (i32, [vp, ctypes.c_char_p]),
+            "scd_stepnet_load": (i32, [vp, ctypes.c_char_p]),
+            "scd_stepnet_destroy": (None, [vp]),
+            "scd_count_pairs_per_object": (i32, [vp, i64, i64, vp, vp]),
             "scd_scene_destroy": (None, [vp]),
             "scd_status_string": (ctypes.c_char_p, [i32]),
         }
@@ -160,9 +172,11 @@ def _elems(els) -> np.ndarray:
 
 
 def make_step_policy(kind: int = SCD_STEP_PERIOD_FRACTION, fixed_ticks: int = 1,
-                     period_fraction: float = 100.0, band_edges_km=(), band_fractions=()):
+                     period_fraction: float = 100.0, band_edges_km=(), band_fractions=(),
+                     stepnet: int = 0):
     pol = scd_step_policy()
     pol.kind = kind
+    pol.stepnet = stepnet or None
     pol.fixed_ticks = int(fixed_ticks)
     pol.period_fraction = float(period_fraction)
     keep = []
@@ -308,6 +322,69 @@ def scd_last_metrics(scene: int) -> str:
     buf = ctypes.create_string_buffer(4096)
     check(lib().scd_last_metrics(scene, buf, len(buf)), "scd_last_metrics")
     return buf.value.decode()
+
+
+SCD_STEPNET_IN, SCD_STEPNET_HIDDEN, SCD_STEPNET_PARAMS = 8, 64, 4801
+
+
+def scd_stepnet_create(stream: int = 0, seed: int = 1) -> int:
+    out = ctypes.c_void_p()
+    check(lib().scd_stepnet_create(ctypes.c_void_p(stream), int(seed), ctypes.byref(out)),
+          "scd_stepnet_create")
+    return out.value
+
+
+def scd_stepnet_set_params(net: int, params) -> None:
+    a = np.ascontiguousarray(np.asarray(params, np.float32).reshape(-1))
+    check(lib().scd_stepnet_set_params(net, a.ctypes.data, len(a)), "scd_stepnet_set_params")
+
+
+def scd_stepnet_get_params(net: int) -> np.ndarray:
+    a = np.zeros(SCD_STEPNET_PARAMS, np.float32)
+    check(lib().scd_stepnet_get_params(net, a.ctypes.data, len(a)), "scd_stepnet_get_params")
+    return a
+
+
+def scd_stepnet_features(d_elems: int, n: int, d_feat: int, stream: int = 0) -> None:
+    check(lib().scd_stepnet_features(d_elems, n, d_feat, ctypes.c_void_p(stream)),
+          "scd_stepnet_features")
+
+
+def scd_stepnet_forward(net: int, d_x: int, n: int, d_y: int) -> None:
+    check(lib().scd_stepnet_forward(net, d_x, n, d_y), "scd_stepnet_forward")
+
+
+def scd_stepnet_grad(net: int, d_x: int, d_t: int, n: int, d_grad: int) -> float:
+    loss = ctypes.c_float(0)
+    check(lib().scd_stepnet_grad(net, d_x, d_t, n, d_grad, ctypes.byref(loss)), "scd_stepnet_grad")
+    return float(loss.value)
+
+
+def scd_stepnet_train_step(net: int, d_x: int, d_t: int, n: int, lr: float,
+                           weight_decay: float = 0.0) -> float:
+    loss = ctypes.c_float(0)
+    check(lib().scd_stepnet_train_step(net, d_x, d_t, n, float(lr), float(weight_decay),
+                                       ctypes.byref(loss)), "scd_stepnet_train_step")
+    return float(loss.value)
+
+
+def scd_stepnet_save(net: int, path: str) -> None:
+    check(lib().scd_stepnet_save(net, path.encode()), "scd_stepnet_save")
+
+
+def scd_stepnet_load(net: int, path: str) -> None:
+    check(lib().scd_stepnet_load(net, path.encode()), "scd_stepnet_load")
+
+
+def scd_stepnet_destroy(net: int) -> None:
+    if net:
+        lib().scd_stepnet_destroy(net)
+
+
+def scd_count_pairs_per_object(d_pairs: int, n_pairs: int, n_objects: int, d_counts: int,
+                               stream: int = 0) -> None:
+    check(lib().scd_count_pairs_per_object(d_pairs, n_pairs, n_objects, d_counts,
+                                           ctypes.c_void_p(stream)), "scd_count_pairs_per_object")
 
 
 def scd_scene_destroy(scene: int) -> None:

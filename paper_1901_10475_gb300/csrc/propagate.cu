@@ -177,7 +177,7 @@ int launch_prepare_objects(scd_scene *s) {
   sa.T = s->T;
   sa.band = s->d_band.p;
   sa.n_bands = (int)s->band_fracs.size();
-  sa.learned_k = nullptr;
+  sa.learned_k = s->step_kind == SCD_STEP_LEARNED ? s->d_learned.p : nullptr;
   int bs = 256;
   int64_t g = (s->n + bs - 1) / bs;
   k_prepare_objects<<<(unsigned)g, bs, 0, s->stream>>>(s->d_el.p, s->n, sa, s->d_par.p,

@@ -299,6 +299,9 @@ struct scd_scene {
   scd::DevBuf<double> d_edges;     // altitude band edges (p - 1)
   scd::DevBuf<unsigned long long> d_abits;  // semi-major axes as sortable bits
   scd::DevBuf<int32_t> d_cellroot; // root node of each cell (-1: fewer than 2 refs)
+
+  // learned steps: features, network outputs, steps [s]
+  scd::DevBuf<float> d_feat, d_ny, d_learned;
   scd::DevBuf<uint32_t> s_leafkey32;
   scd::DevBuf<unsigned long long> s_leafkey64;
   scd::DevBuf<scd::TravNode> d_nodes;
@@ -338,6 +341,8 @@ int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, i
                K *leafkey, int cell_shift, int64_t &M);
 // decomposed screen: references, their sort, the tree and each cell's root
 int build_decomposed(scd_scene *s, const scd_decomp *d, int64_t &n_leaves);
+// learned per-object steps [s] into s->d_learned (SCD_STEP_LEARNED)
+int learned_steps(scd_scene *s);
 int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_bits);
 int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits);
 }  // namespace scd

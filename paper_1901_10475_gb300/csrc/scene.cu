@@ -145,7 +145,8 @@ extern "C" SCD_API int scd_scene_create(const scd_element *elems, int64_t n, dou
         if (!(step->band_edges_km[b] > step->band_edges_km[b - 1])) return SCD_ERR_INVALID_ARG;
       break;
     case SCD_STEP_LEARNED:
-      return SCD_ERR_INVALID_ARG;  // step networks are not part of this build's ABI yet
+      if (!step->stepnet) return SCD_ERR_INVALID_ARG;
+      break;
     default: return SCD_ERR_INVALID_ARG;
   }
   scd_scene *s = new scd_scene();
@@ -158,6 +159,7 @@ extern "C" SCD_API int scd_scene_create(const scd_element *elems, int64_t n, dou
   s->step_kind = step->kind;
   s->fixed_ticks = step->fixed_ticks;
   s->period_fraction = step->period_fraction;
+  s->stepnet = step->kind == SCD_STEP_LEARNED ? step->stepnet : nullptr;
   if (step->kind == SCD_STEP_BAND_TABLE) {
     s->band_edges.assign(step->band_edges_km, step->band_edges_km + (step->n_bands - 1));
     s->band_fracs.assign(step->band_fractions, step->band_fractions + step->n_bands);
@@ -228,6 +230,7 @@ extern "C" SCD_API int scd_build_boxes(scd_scene *s) {
   if (s->events_ready) cudaEventRecord(s->ev[0], st);
   s->launch_mark = launch_count();
   if (cudaMemsetAsync(s->d_ctr.p, 0, sizeof(DevCounters), st) != cudaSuccess) return SCD_ERR_CUDA;
+  if (s->step_kind == SCD_STEP_LEARNED) TRY(learned_steps(s));
   TRY(launch_prepare_objects(s));
   TRY(scan_exclusive_i64(s->d_segcnt.p, s->d_segoff.p, s->n, s->d_scan_tmp, st));
   // the box count sizes every buffer that follows: one 8-byte read
@@ -468,6 +471,7 @@ extern "C" SCD_API void scd_scene_destroy(scd_scene *s) {
   s->d_refcnt.release(st); s->d_refoff.release(st); s->d_refkey.release(st);
   s->d_refid.release(st); s->d_rr.release(st); s->d_edges.release(st);
   s->d_abits.release(st); s->d_cellroot.release(st);
+  s->d_feat.release(st); s->d_ny.release(st); s->d_learned.release(st);
   if (s->events_ready)
     for (int k = 0; k < 8; ++k) cudaEventDestroy(s->ev[k]);
   if (s->h_ctr_pinned) cudaFreeHost(s->h_ctr_pinned);

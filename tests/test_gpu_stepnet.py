@@ -1,0 +1,126 @@
+"""The step network's GPU kernels against the FP64 oracle (forward pass,
+gradient, features), its training and checkpoint, the LEARNED step policy,
+and what the trained network gains over the period rule."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import population as P
+from oracle import stepnet as OS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import paper_1901_10475_gb300 as m
+    from paper_1901_10475_gb300 import stepnet as sn
+    torch.cuda.set_device(0)
+    return m, sn
+
+
+def test_forward_and_gradient_match_oracle(mods):
+    scd, sn = mods
+    net = sn.StepNet(seed=3)
+    g = np.random.default_rng(0)
+    p = (g.standard_normal(OS.N_PARAMS) * 0.3).astype(np.float32)
+    net.params = p
+    X = g.standard_normal((1000, 8)).astype(np.float32)
+    T = g.standard_normal(1000).astype(np.float32)
+    dx = torch.as_tensor(X, device="cuda")
+    dt = torch.as_tensor(T, device="cuda")
+    y = net.forward(dx).cpu().numpy()
+    yo = OS.forward(p, X)
+    assert np.abs(y - yo).max() <= 1e-4 * (1 + np.abs(yo).max())
+    loss, grad = net.grad(dx, dt)
+    lo, go = OS.loss_and_grad(p, X, T)
+    assert loss == pytest.approx(lo, rel=1e-4)
+    grad = grad.cpu().numpy()
+    scale = np.abs(go).max()
+    assert np.abs(grad - go).max() <= 1e-3 * scale
+    net.close()
+
+
+def test_features_match_oracle(mods):
+    scd, sn = mods
+    els = P.catalog_mixture(n=3000, seed=61)
+    f = sn.features(els).cpu().numpy()
+    fo = OS.features(els)
+    assert np.abs(f - fo).max() <= 1e-5 * (1 + np.abs(fo).max())
+
+
+def test_training_reduces_loss_and_checkpoint_round_trips(mods, tmp_path):
+    scd, sn = mods
+    els = P.catalog_mixture(n=4000, seed=62)
+    X = OS.features(els).astype(np.float32)
+    # a smooth target: log of P/100
+    a = els[:, 0]
+    Y = np.log(2 * np.pi * np.sqrt(a ** 3 / OS.MU) / 100.0).astype(np.float32)
+    net = sn.StepNet(seed=4)
+    losses = sn.train(net, X, Y, epochs=60, batch=1024, lr=3e-3)
+    assert losses[-1] < 0.05 * losses[0]
+    path = str(tmp_path / "net.bin")
+    net.save(path)
+    net2 = sn.StepNet(seed=9)
+    net2.load(path)
+    assert (net2.params == net.params).all()
+    dx = torch.as_tensor(X, device="cuda")
+    assert torch.equal(net.forward(dx), net2.forward(dx))
+    net.close()
+    net2.close()
+
+
+def test_learned_policy_steps_and_sound_screen(mods):
+    scd, sn = mods
+    els = P.uniform_leo(24, seed=101, radius_km=300.0)
+    net = sn.StepNet(seed=5)
+    net.params = (np.random.default_rng(1).standard_normal(OS.N_PARAMS) * 0.05).astype(np.float32)
+    T = 400
+    sc = scd.Scene(els, float(T), 1.0, net.policy()).build_boxes()
+    k = sc.steps().cpu().numpy()
+    y = net.forward(sn.features(els)).cpu().numpy()
+    ks = OS.learned_step_seconds(els, y)
+    kk = np.maximum(np.floor(ks), 1)
+    assert np.abs(k - np.minimum(kk, T + 1)).max() <= 1
+    got = sc.find_pairs()
+    lo, hi, obj = (x.cpu().numpy() for x in sc.boxes())
+    want = O.canonicalize(O.raw_cells_sweep(lo, hi, obj.view(np.uint32)))
+    assert np.array_equal(got.view(np.int32), want.view(np.int32))
+    for w in O.alg1_witnesses(els, T, 1.0).tolist():
+        m = got[(got["i"] == w[0]) & (got["j"] == w[1])]
+        assert np.any((m["tlo"] <= w[2]) & (w[2] <= m["thi"])), w
+    sc.close()
+    net.close()
+
+
+def test_trained_steps_beat_the_period_rule_on_held_out_objects(mods):
+    """Sweep a training population, fit the cost model, train, then compare
+    the modelled cost of a held-out population's screen under the learned
+    steps and under P/100 (the learned steps must be no worse), and report
+    the measured times."""
+    scd, sn = mods
+    train_els = P.catalog_mixture(n=3000, seed=71, radius_km=2.5)
+    sw = sn.sweep(train_els, 21600.0)
+    c_box, c_hit = sn.fit_cost_model(sw)
+    Y = sn.targets(train_els, sw, c_box, c_hit).astype(np.float32)
+    X = OS.features(train_els).astype(np.float32)
+    net = sn.StepNet(seed=6)
+    sn.train(net, X, Y, epochs=80, batch=512, lr=3e-3)
+
+    test_els = P.catalog_mixture(n=3000, seed=72, radius_km=2.5)
+    sw_t = sn.sweep(test_els, 21600.0, multipliers=(100.0,))
+    cost_rule = (c_box * sw_t["boxes"][0] + 0.5 * c_hit * sw_t["pairs"][0]).sum()
+    sc = scd.Scene(test_els, 21600.0, 1.0, net.policy()).build_boxes()
+    ptr, m = scd.scd_find_raw_cells_device(sc.handle)
+    cnt = torch.zeros(len(test_els), dtype=torch.int32, device="cuda")
+    scd.scd_count_pairs_per_object(ptr, m, len(test_els), cnt.data_ptr(),
+                                   torch.cuda.current_stream().cuda_stream)
+    k = sc.steps().cpu().numpy().astype(np.int64)
+    boxes = (21600 + k) // k
+    cost_learned = (c_box * boxes + 0.5 * c_hit * cnt.cpu().numpy()).sum()
+    print(f"modelled cost: learned {cost_learned:.3f} ms vs P/100 {cost_rule:.3f} ms "
+          f"(c_box={c_box:.3e}, c_hit={c_hit:.3e})")
+    assert cost_learned <= cost_rule
+    sc.close()
+    net.close()
