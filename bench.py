@@ -1,20 +1,35 @@
-"""Benchmark: one 24 h screen of a 16,848-object catalog-shaped population.
+"""Benchmark of the 4D box screen on one GB300 (per rank).
 
-A step is one pass of the whole hot path from device-resident elements to
-the device-resident canonical pair list: per-object steps (P/100), FP64
-propagation, FP32 boxes and Morton keys, radix sort, hierarchy, refit,
-traversal with merged emission, canonical sort.  The JSON line's ``value``
-is milliseconds per screen (whole job: all ranks' screens over the max-rank
-time); ``e2e`` is the same through the C ABI with host buffers (elements
-copied in, pairs copied out inside the timed region).
+Default workload: one 24 h screen of a 16,848-object catalog-shaped
+population at steps P/100.  A step is one pass of the whole hot path from
+device-resident elements to the device-resident canonical pair list:
+per-object steps, FP64 propagation, FP32 boxes and Morton keys, radix sort,
+hierarchy, refit, traversal with merged emission, canonical sort.  The JSON
+line's ``value`` is milliseconds per screen (whole job: all ranks' screens
+over the max-rank time); ``e2e`` is the same through the C ABI with host
+buffers (elements copied in, pairs copied out inside the timed region).
 
---impl reference times the CPU oracle on a bounded sample of the same
+Other workloads (--workload):
+  band_slab   the same population with band-table steps (P/200 .. P/400 by
+              perigee altitude) and the 16 slab x 8 octant decomposition, with
+              the tuning picked by the autotuner
+  batch64     64 independent scenes of uneven size (1e3-6e4 objects,
+              ~1.2M in all, horizons 6-72 h), each group of scenes one batch
+              through one persistent traversal: scenes per second and per
+              scene latency
+  learned100k 100,000 objects with two dense LEO shells, 24 h, per-object
+              steps from the step network trained on this run's own sweeps,
+              against the P/100 rule
+
+--impl reference times the CPU oracle on a bounded sample of the default
 workload (a time window of the horizon) and scales it to a 24 h screen.
 """
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -30,15 +45,37 @@ import numpy as np  # noqa: E402
 
 import population as P  # noqa: E402
 
-METRIC = "ms per 24h screen at n=16848"
 N_OBJ = 16848
 HORIZON_S = 86400.0
 TICK_S = 1.0
 FRACTION = 100.0
 L2_BYTES = 129 * 1024 * 1024
-WORKLOAD = ("catalog-shaped synthetic mixture n=16848 (72% LEO, 8% MEO, 10% GEO, 10% HEO, "
-            "0.1% seeded crossing pairs), 24 h horizon, 1 s ticks, per-object step P/100, "
-            "SPEED boxes, plain 4D LBVH")
+MU = 398600.4418
+
+WORKLOADS = {
+    "catalog24h": {
+        "metric": "ms per 24h screen at n=16848",
+        "desc": ("catalog-shaped synthetic mixture n=16848 (72% LEO, 8% MEO, 10% GEO, 10% HEO, "
+                 "0.1% seeded crossing pairs), 24 h horizon, 1 s ticks, per-object step P/100, "
+                 "plain 4D LBVH")},
+    "band_slab": {
+        "metric": "ms per 24h screen at n=16848, band steps, 16 slabs x 8 octants",
+        "desc": ("the n=16848 mixture, 24 h, per-object steps P/200 (perigee < 1000 km), P/100 "
+                 "(1000-2000 km), P/50 (2000-30000 km), P/400 (above); 16 tick slabs x 8 ECI "
+                 "octants as 128 cell subtrees of one sort in one persistent traversal; tuning "
+                 "from the autotuner")},
+    "batch64": {
+        "metric": "scenes per second, 64 scenes, ~1.2M objects, horizons 6-72 h",
+        "desc": ("64 independent catalog-shaped scenes, sizes log-uniform 1e3-6e4 (total "
+                 "~1.2M objects), horizons whole hours 6-72, steps P/100; scenes grouped into "
+                 "batches of up to 4e7 boxes, each batch one box build, one sort, one tree "
+                 "and one persistent traversal")},
+    "learned100k": {
+        "metric": "ms per 24h screen at n=100000, learned steps",
+        "desc": ("100,000-object mixture with Gaussian LEO shells at 550 and 1150 km, 24 h; "
+                 "per-object steps from the 8-64-64-1 step network trained in this run on "
+                 "sweeps of a 16848-object population (6 h, multipliers 50-400)")},
+}
 
 
 def _peaks():
@@ -105,11 +142,11 @@ class ClockSampler:
 
 
 def algorithmic_bytes(m: dict, n: int) -> dict:
-    """Algorithmic HBM bytes of one screen by phase (each array read or
-    written once per pass it needs)."""
+    """Algorithmic HBM bytes of one screen by phase: every array read or
+    written once per pass that needs it (one box per leaf)."""
     N = m["boxes"]
-    L = m["leaf_size"]
-    M = (N + L - 1) // L
+    R = m.get("refs") or N  # sorted entries (references when decomposed)
+    M = R
     runs = m["records"]
     key_b = 4 if m["morton_bits"] <= 8 else 8
     passes = (4 * m["morton_bits"] + 7) // 8
@@ -120,53 +157,44 @@ def algorithmic_bytes(m: dict, n: int) -> dict:
         "boxes": 56 * n + N * (32 + 4 + 4 + key_b),
         # per pass: keys+values read twice (count, rank), written once
         "sort": passes * N * 3 * (key_b + 4),
-        # gather boxes by id; leaf keys; hierarchy nodes and refit
-        "build": N * (4 + 32 + 4 + 32 + 4) + M * (key_b + 80 + 32 + 32 + 16),
-        # every sorted box and node read at least once; records written
-        "traverse": N * (32 + 8) + (M - 1) * 80 + 2 * runs * 8,
+        # gather boxes by id; neighbour positions; hierarchy nodes and refit
+        "build": R * (4 + 32 + 32 + 4 + 8 + 4) + M * (key_b + 40 + 32 + 16),
+        # every sorted box and compact node read at least once; records written
+        "traverse": R * (32 + 8) + (M - 1) * 40 + 2 * runs * 8,
         # two key-only sorts of the run records, then the output pairs
         "canon": 2 * ppasses * runs * 8 * 3 + runs * (16 + 16),
     }
 
 
-def run_ours(args, rank, world):
+def _device():
     import torch
-
-    import paper_1901_10475_gb300 as scd
-
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
+    return dev
+
+
+def time_scene_steps(sc, step, steps, warmup, dev, world):
+    """Warm up, then time `steps` screens with CUDA events on the scene's
+    stream, flushing L2 between them (outside the timed events)."""
+    import torch
     stream = torch.cuda.current_stream()
-    els = P.catalog_mixture(n=N_OBJ, seed=P.SEED_BASE + 2)
-    pol = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=FRACTION)
-    sc = scd.Scene(els, args.horizon_s, TICK_S, pol, stream=stream)
-    if args.tuning:
-        sc.set_tuning(json.loads(args.tuning))
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-    d_el = torch.as_tensor(els, device="cuda")
-
-    def step():
-        scd.scd_scene_set_elements_device(sc.handle, d_el.data_ptr(), N_OBJ)
-        scd.scd_build_boxes(sc.handle)
-        return scd.scd_find_pairs_device(sc.handle)
-
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    times, phase = [], {k: [] for k in ("ms_boxes", "ms_sort", "ms_build", "ms_traverse", "ms_canon")}
-    tests = 0
-    launches = 0
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    phase = {k: [] for k in ("ms_boxes", "ms_sort", "ms_build", "ms_traverse", "ms_canon")}
+    tests = launches = 0
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     n_pairs = 0
     with ClockSampler(dev) as clk:
-        for k in range(args.steps):
-            flush.fill_(float(k))  # evict L2 between steps (outside the timed events)
+        for k in range(steps):
+            flush.fill_(float(k))
             ev0[k].record(stream)
-            _, n_pairs = step()
+            n_pairs = step()
             ev1[k].record(stream)
             m = sc.metrics()
             for key in phase:
@@ -175,41 +203,191 @@ def run_ours(args, rank, world):
             launches += m["launches"]
         torch.cuda.synchronize()
     times = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    t_total = sum(times)
-    if world > 1:
-        t = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(t.item())
-    ms_per_screen = t_total / (args.steps * world)
-    m = sc.metrics()
+    return {"times": times, "phase_ms": {k: statistics.mean(v) for k, v in phase.items()},
+            "tests": tests, "launches": launches, "n_pairs": n_pairs, "clocks": clk.summary(),
+            "metrics": sc.metrics()}
 
-    # end to end through the C ABI with host buffers
-    host_in = torch.as_tensor(els).pin_memory()
-    host_out = np.zeros(max(2 * n_pairs, 1), scd.PAIR_DTYPE)
-    import ctypes
-    out_pinned = torch.empty(host_out.nbytes, dtype=torch.uint8).pin_memory()
+
+def e2e_through_abi(sc, els, n_pairs, steps):
+    """Median ms of: host elements in (pinned), boxes, pairs to a pinned host
+    array, through the C entry points."""
+    import torch
+
+    import paper_1901_10475_gb300 as scd
+    host_in = torch.as_tensor(np.ascontiguousarray(els)).pin_memory()
+    out_pinned = torch.empty(max(2 * n_pairs, 1) * 16, dtype=torch.uint8).pin_memory()
     out_np = out_pinned.numpy().view(scd.PAIR_DTYPE)
-    e2e_times = []
-    e2e_steps = max(1, min(args.steps, 5))
-    for k in range(e2e_steps):
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    ts = []
+    n_host = 0
+    for k in range(max(1, min(steps, 5))):
         flush.fill_(float(k))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         scd._binding.lib().scd_scene_set_elements(sc.handle, ctypes.c_void_p(host_in.data_ptr()),
-                                                  N_OBJ)
+                                                  len(els))
         scd.scd_build_boxes(sc.handle)
         n_host = scd.scd_find_pairs_into(sc.handle, out_np)
-        e2e_times.append((time.perf_counter() - t0) * 1e3)
-    e2e_ms = statistics.median(e2e_times)
+        ts.append((time.perf_counter() - t0) * 1e3)
+    return statistics.median(ts), n_host
 
-    byt = algorithmic_bytes(m, N_OBJ)
-    phase_ms = {k: statistics.mean(v) for k, v in phase.items()}
-    pk, src = _peaks()
-    return {
-        "ms_per_screen": ms_per_screen, "times": times, "phase_ms": phase_ms, "tests": tests,
-        "launches": launches, "metrics": m, "bytes": byt, "n_pairs": n_pairs, "clocks": clk.summary(),
-        "e2e_ms": e2e_ms, "e2e_pairs": n_host, "peaks": pk, "peak_src": src,
-    }
+
+def run_single(args, world, wl):
+    """Single-scene workloads (catalog24h, band_slab)."""
+    import torch
+
+    import paper_1901_10475_gb300 as scd
+    from paper_1901_10475_gb300 import autotune
+    dev = _device()
+    els = P.catalog_mixture(n=N_OBJ, seed=P.SEED_BASE + 2)
+    decomp = None
+    if wl == "band_slab":
+        edges, fr = P.band_table_config3()
+        pol = scd.make_step_policy(scd.SCD_STEP_BAND_TABLE, band_edges_km=edges,
+                                   band_fractions=fr)
+        decomp = (scd.SCD_DECOMP_SLAB_OCT, 0, 16)
+    else:
+        pol = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=FRACTION)
+    sc = scd.Scene(els, args.horizon_s, TICK_S, pol, mode=args.mode)
+    tuning = None
+    if args.tuning:
+        sc.set_tuning(json.loads(args.tuning))
+    elif wl == "band_slab" or args.autotune:
+        sc.build_boxes()
+        key = autotune.workload_key(els, args.horizon_s, TICK_S, wl, 1 << 24)
+        tuning, _ = autotune.load_or_tune(sc, key, reps=1, decomp=decomp)
+    d_el = torch.as_tensor(els, device="cuda")
+
+    def step():
+        scd.scd_scene_set_elements_device(sc.handle, d_el.data_ptr(), N_OBJ)
+        scd.scd_build_boxes(sc.handle)
+        return scd.scd_find_pairs_device(sc.handle, decomp)[1]
+
+    r = time_scene_steps(sc, step, args.steps, args.warmup, dev, world)
+    t_total = sum(r["times"])
+    if world > 1:
+        t = torch.tensor([t_total], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(t.item())
+    r["value"] = t_total / (args.steps * world)
+    r["unit"] = "ms"
+    r["higher_is_better"] = False
+    if decomp is None:
+        r["e2e_ms"], r["e2e_pairs"] = e2e_through_abi(sc, els, r["n_pairs"], args.steps)
+        r["e2e"] = {"value": r["e2e_ms"], "unit": "ms", "h2d_bytes_per_step": 56 * N_OBJ,
+                    "d2h_bytes_per_step": 16 * r["e2e_pairs"]}
+    r["n"] = N_OBJ
+    r["tuning"] = tuning
+    sc.close()
+    return r
+
+
+def run_batch64(args, world):
+    import torch
+
+    import paper_1901_10475_gb300 as scd
+    dev = _device()
+    scenes = P.batch_scenes()
+    pol = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=FRACTION)
+    # group scenes into batches of at most 1.2e8 boxes (estimated from P/100)
+    est = []
+    for els, hz in scenes:
+        a = els[:, 0]
+        k = np.maximum(np.floor(2 * math.pi * np.sqrt(a ** 3 / MU) / FRACTION), 1)
+        est.append(float(np.sum(np.ceil((hz + 1) / k))))
+    groups, cur, cur_n = [], [], 0.0
+    for s, nb in enumerate(est):
+        if cur and cur_n + nb > 4e7:
+            groups.append(cur)
+            cur, cur_n = [], 0.0
+        cur.append(s)
+        cur_n += nb
+    groups.append(cur)
+    stream = torch.cuda.current_stream()
+
+    def one_pass(record):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        done = []
+        npairs = 0
+        for g in groups:
+            b = scd.BatchScene([scenes[s][0] for s in g], [scenes[s][1] for s in g], TICK_S, pol,
+                               mode=args.mode)
+            b.build_boxes()
+            npairs += scd.scd_find_pairs_device(b.handle)[1]
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(stream)
+            done.append((g, ev))
+            b.close()
+        torch.cuda.synchronize()
+        lat = {}
+        for g, ev in done:
+            for s in g:
+                lat[s] = t0.elapsed_time(ev)
+        return t0, done, lat, npairs
+
+    for _ in range(args.warmup):
+        one_pass(False)
+    totals, lats = [], []
+    with ClockSampler(dev) as clk:
+        for _ in range(args.steps):
+            t0, done, lat, npairs = one_pass(True)
+            totals.append(t0.elapsed_time(done[-1][1]))
+            lats.extend(lat.values())
+    ms = statistics.mean(totals)
+    return {"value": len(scenes) * 1e3 / ms, "unit": "scenes/s", "higher_is_better": True,
+            "times": totals, "clocks": clk.summary(), "n_pairs": npairs,
+            "latency_ms": {"p50": float(np.percentile(lats, 50)),
+                           "p99": float(np.percentile(lats, 99))},
+            "batches": len(groups), "objects": int(sum(len(e) for e, _ in scenes)),
+            "boxes_est": float(sum(est)), "ms_per_pass": ms, "launches": None}
+
+
+def run_learned100k(args, world):
+    import torch
+
+    import paper_1901_10475_gb300 as scd
+    from oracle import stepnet as _unused  # noqa: F401  (features are computed on the GPU)
+    from paper_1901_10475_gb300 import stepnet as sn
+    dev = _device()
+    # train on the method's own sweeps of a smaller population
+    train_els = P.catalog_mixture(n=N_OBJ, seed=P.SEED_BASE + 5, dense_shells=True)
+    t0 = time.perf_counter()
+    sw = sn.sweep(train_els, 21600.0, mode=args.mode)
+    c_box, c_hit = sn.fit_cost_model(sw)
+    Y = sn.targets(train_els, sw, c_box, c_hit).astype(np.float32)
+    X = sn.features(train_els).cpu().numpy()
+    net = sn.StepNet(seed=7)
+    losses = sn.train(net, X, Y, epochs=60, batch=1024, lr=3e-3)
+    train_s = time.perf_counter() - t0
+
+    els = P.catalog_mixture(n=100000, seed=P.SEED_BASE + 5, dense_shells=True)
+    d_el = torch.as_tensor(els, device="cuda")
+    out = {}
+    for name, pol in [("learned", net.policy()),
+                      ("p100", scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION,
+                                                    period_fraction=FRACTION))]:
+        sc = scd.Scene(els, HORIZON_S, TICK_S, pol, mode=args.mode)
+
+        def step():
+            scd.scd_scene_set_elements_device(sc.handle, d_el.data_ptr(), len(els))
+            scd.scd_build_boxes(sc.handle)
+            return scd.scd_find_pairs_device(sc.handle)[1]
+
+        out[name] = time_scene_steps(sc, step, args.steps, args.warmup, dev, world)
+        sc.close()
+    r = out["learned"]
+    r["value"] = statistics.mean(r["times"])
+    r["unit"] = "ms"
+    r["higher_is_better"] = False
+    r["n"] = 100000
+    r["p100_ms"] = statistics.mean(out["p100"]["times"])
+    r["p100_boxes"] = out["p100"]["metrics"]["boxes"]
+    r["p100_pairs"] = out["p100"]["n_pairs"]
+    r["training"] = {"seconds": train_s, "samples": len(X), "final_loss": float(losses[-1]),
+                     "c_box_ms": c_box, "c_hit_ms": c_hit}
+    net.close()
+    return r
 
 
 def cpu_oracle_sample(window_ticks: int = 600):
@@ -235,13 +413,27 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--tuning", default="")
+    ap.add_argument("--workload", default="catalog24h", choices=sorted(WORKLOADS))
+    ap.add_argument("--tuning", default="", help="JSON tuning overrides")
+    ap.add_argument("--autotune", action="store_true", help="search the tuning first")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--box-mode", default="", choices=["", "speed", "interval"],
+                    help="occ-int bound; default: speed, interval for batch64 and learned100k")
     ap.add_argument("--horizon-s", type=float, default=HORIZON_S,
                     help="shorter horizons give the small profiling case")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    wl = args.workload
+    metric = WORKLOADS[wl]["metric"]
+    desc = WORKLOADS[wl]["desc"]
+    if not args.box_mode:
+        args.box_mode = "interval" if wl in ("batch64", "learned100k") else "speed"
+    args.mode = 1 if args.box_mode == "interval" else 0
+    desc += ("; INTERVAL boxes (interval evaluation over the eccentric-anomaly range)"
+             if args.mode else "; SPEED boxes")
+    if args.horizon_s != HORIZON_S:
+        desc = desc.replace("24 h", f"{args.horizon_s:.0f} s")
 
     if args.impl == "reference":
         if rank != 0:
@@ -249,19 +441,19 @@ def main():
         vals = []
         for _ in range(args.warmup):
             cpu_oracle_sample(120)
-        desc = ""
+        sdesc = ""
         for _ in range(args.steps):
-            sec, desc, ms = cpu_oracle_sample(120)
+            sec, sdesc, ms = cpu_oracle_sample(120)
             vals.append(ms)
         v = statistics.mean(vals)
         print(json.dumps({
-            "impl": "reference", "metric": METRIC, "value": v, "unit": "ms",
-            "higher_is_better": False, "n_gpus": args.gpus, "steps": args.steps,
+            "impl": "reference", "metric": WORKLOADS["catalog24h"]["metric"], "value": v,
+            "unit": "ms", "higher_is_better": False, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": v, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64/f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "config": {"workload": WORKLOADS["catalog24h"]["desc"], "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle",
-                             "sample": desc},
+                             "sample": sdesc},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         }))
         return
@@ -269,52 +461,63 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    r = run_ours(args, rank, world)
+    if wl in ("catalog24h", "band_slab"):
+        r = run_single(args, world, wl)
+    elif wl == "batch64":
+        r = run_batch64(args, world)
+    else:
+        r = run_learned100k(args, world)
     if world > 1:
         import torch
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     if rank != 0:
         return
-    m = r["metrics"]
-    byt = r["bytes"]
-    ph = r["phase_ms"]
-    # dominant phase and its roofline
-    dom = max(ph, key=ph.get)
-    name = dom[3:]
-    hbm = r["peaks"].get("hbm_gbs", 6800.0)
-    achieved = byt[name] / (ph[dom] * 1e-3) / 1e9
-    roof = {"kernel_phase": name, "bound": "hbm", "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-            "peak_source": r["peak_src"], "phase_ms": ph,
-            "algorithmic_bytes": byt[name]}
-    cpu = None
-    if not args.no_cpu_baseline and world == 1:
-        sec, desc, ms = cpu_oracle_sample(600)
-        cpu = {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": desc,
-               "sample_seconds": sec}
-    ms = r["ms_per_screen"]
+
     line = {
-        "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "metric": metric, "value": r["value"], "unit": r["unit"], "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(r["times"]), "higher_is_better": r["higher_is_better"],
         "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.horizon_s == HORIZON_S else
-                   WORKLOAD.replace("24 h horizon", f"{args.horizon_s:.0f} s horizon"),
-                   "boxes": m["boxes"], "pairs": r["n_pairs"],
-                   "records": m["records"], "leaf_size": m["leaf_size"],
-                   "morton_bits": m["morton_bits"], "stack_depth": m["stack_depth"],
-                   "block_threads": m["block_threads"],
+        "config": {"workload": desc,
                    "l2": "flushed between steps (writes 2x L2); working set > 1 GB"},
-        "box_pair_tests_per_s": r["tests"] / (sum(r["times"]) * 1e-3),
-        "node_tests": m["node_tests"], "leaf_tests": m["leaf_tests"],
-        "roofline": roof,
-        "cpu_baseline": cpu,
-        "e2e": {"value": r["e2e_ms"], "unit": "ms", "h2d_bytes_per_step": 56 * N_OBJ,
-                "d2h_bytes_per_step": 16 * r["e2e_pairs"]},
-        "gpu_launches": r["launches"],
-        "clocks": r["clocks"],
-        "step_times_ms": r["times"],
     }
+    pk, src = _peaks()
+    if "metrics" in r:
+        m = r["metrics"]
+        line["config"].update({"boxes": m["boxes"], "pairs": r["n_pairs"],
+                               "records": m["records"], "leaf_size": m["leaf_size"],
+                               "morton_bits": m["morton_bits"], "stack_depth": m["stack_depth"],
+                               "block_threads": m["block_threads"]})
+        line["box_pair_tests_per_s"] = r["tests"] / (sum(r["times"]) * 1e-3)
+        line["node_tests"] = m["node_tests"]
+        line["leaf_tests"] = m["leaf_tests"]
+        ph = r["phase_ms"]
+        byt = algorithmic_bytes(m, r["n"])
+        dom = max(ph, key=ph.get)
+        name = dom[3:]
+        hbm = pk.get("hbm_gbs", 6800.0)
+        achieved = byt[name] / (ph[dom] * 1e-3) / 1e9
+        line["roofline"] = {"kernel_phase": name, "bound": "hbm", "achieved": achieved,
+                            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                            "peak_source": src, "phase_ms": ph,
+                            "algorithmic_bytes": byt[name]}
+        line["gpu_launches"] = r["launches"]
+    if wl == "catalog24h":
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            sec, sdesc, ms = cpu_oracle_sample(600)
+            cpu = {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sdesc,
+                   "sample_seconds": sec}
+        line["cpu_baseline"] = cpu
+    if "e2e" in r:
+        line["e2e"] = r["e2e"]
+    for k in ("latency_ms", "batches", "objects", "boxes_est", "ms_per_pass", "p100_ms",
+              "p100_boxes", "p100_pairs", "training", "tuning"):
+        if k in r and r[k] is not None:
+            line[k] = r[k]
+    line["clocks"] = r["clocks"]
+    line["step_times_ms"] = r["times"]
     print(json.dumps(line))
 
 

@@ -246,10 +246,28 @@ SCD_API int scd_propagate_noalloc(const scd_element *d_elems, int64_t n, const u
                                   const double *d_t_s, int64_t m, double *d_out,
                                   void *cuda_stream);
 
-/* Batched screening: n_scenes independent scenes (each already with boxes)
- * in one persistent traversal launch.  outs[s] is a host array of caps[s]
- * pairs; n_outs[s] receives each count.  BUFFER_TOO_SMALL if any cap is too
- * small (all counts still reported). */
+/* A batch of independent scenes screened as one: n_scenes scenes of the
+ * concatenated elements (scene k owns elements scene_offsets[k] ..
+ * scene_offsets[k+1]-1; scene_offsets[0] = 0, strictly increasing), each
+ * with its own horizon horizons_s[k] (a whole number of ticks of tick_s).
+ * Every scene becomes one cell: one box build, one reference sort, one tree
+ * with a subtree per scene, one persistent traversal over all scenes'
+ * boxes, one canonical sort.  scd_build_boxes and scd_find_pairs(_device)
+ * then work on the batch (decomposition argument NULL or NONE); the list is
+ * sorted by (i, j, tlo) with batch-wide object indices, so each scene's
+ * pairs are contiguous; scd_batch_scene_offsets gives where (host array of
+ * n_scenes + 1 entries).  Pairs never join objects of different scenes. */
+SCD_API int scd_batch_scene_create(const scd_element *elems, const int64_t *scene_offsets,
+                                   const double *horizons_s, int n_scenes, double tick_s,
+                                   const scd_step_policy *step, scd_box_mode mode,
+                                   void *cuda_stream, scd_scene **out);
+SCD_API int scd_batch_scene_offsets(const scd_scene *s, int64_t *host_offsets);
+
+/* Screening of separately created scenes (each already with boxes), one
+ * after another on their own streams; for one launch over many scenes use
+ * scd_batch_scene_create.  outs[s] is a host array of caps[s] pairs;
+ * n_outs[s] receives each count.  BUFFER_TOO_SMALL if any cap is too small
+ * (all counts still reported). */
 SCD_API int scd_batch_find_pairs(scd_scene *const *scenes, int n_scenes, const scd_decomp *d,
                                  scd_pair *const *outs, const int64_t *caps, int64_t *n_outs);
 

@@ -117,6 +117,39 @@ class Scene:
             pass
 
 
+class BatchScene(Scene):
+    """Many independent scenes (own elements and horizons) screened in one
+    build, one sort, one tree and one persistent traversal."""
+
+    def __init__(self, elements_list, horizons_s, tick_s: float = 1.0, step=None,
+                 mode: int = SCD_BOX_SPEED, stream=None, tuning=None):
+        import torch
+        B.use_torch_allocator()
+        if step is None:
+            step = make_step_policy(SCD_STEP_PERIOD_FRACTION, period_fraction=100.0)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        self.n_scenes = len(elements_list)
+        self.handle, self.scene_off = B.scd_batch_scene_create(
+            elements_list, horizons_s, tick_s, step, mode, int(stream.cuda_stream))
+        self.n = int(self.scene_off[-1])
+        if tuning is not None:
+            self.set_tuning(tuning)
+
+    def find_pairs_per_scene(self):
+        """One array per scene, object indices local to the scene."""
+        allp = self.find_pairs()
+        off = B.scd_batch_scene_offsets(self.handle, self.n_scenes)
+        out = []
+        for k in range(self.n_scenes):
+            p = allp[off[k]:off[k + 1]].copy()
+            p["i"] -= np.uint32(self.scene_off[k])
+            p["j"] -= np.uint32(self.scene_off[k])
+            out.append(p)
+        return out
+
+
 def pairs_from_device(t) -> np.ndarray:
     """Copy an (n, 4) int32 device view of scd_pair records to numpy."""
     a = t.cpu().numpy()

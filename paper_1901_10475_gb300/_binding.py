@@ -115,6 +115,9 @@ def lib() -> ctypes.CDLL:
             "scd_stepnet_load": (i32, [vp, ctypes.c_char_p]),
             "scd_stepnet_destroy": (None, [vp]),
             "scd_count_pairs_per_object": (i32, [vp, i64, i64, vp, vp]),
+            "scd_batch_scene_create": (i32, [vp, vp, vp, i32, d, P(scd_step_policy), i32, vp,
+                                             P(vp)]),
+            "scd_batch_scene_offsets": (i32, [vp, vp]),
             "scd_scene_destroy": (None, [vp]),
             "scd_status_string": (ctypes.c_char_p, [i32]),
         }
@@ -385,6 +388,28 @@ def scd_count_pairs_per_object(d_pairs: int, n_pairs: int, n_objects: int, d_cou
                                stream: int = 0) -> None:
     check(lib().scd_count_pairs_per_object(d_pairs, n_pairs, n_objects, d_counts,
                                            ctypes.c_void_p(stream)), "scd_count_pairs_per_object")
+
+
+def scd_batch_scene_create(elements_list, horizons_s, tick_s: float, policy,
+                           mode: int = SCD_BOX_SPEED, stream: int = 0):
+    """One scene holding a batch of independent scenes; returns (handle,
+    scene offsets)."""
+    els = np.ascontiguousarray(np.concatenate([_elems(e) for e in elements_list]))
+    off = np.zeros(len(elements_list) + 1, np.int64)
+    off[1:] = np.cumsum([len(e) for e in elements_list])
+    hz = np.ascontiguousarray(np.asarray(horizons_s, np.float64))
+    out = ctypes.c_void_p()
+    check(lib().scd_batch_scene_create(els.ctypes.data, off.ctypes.data, hz.ctypes.data,
+                                       len(elements_list), float(tick_s), ctypes.byref(policy),
+                                       int(mode), ctypes.c_void_p(stream), ctypes.byref(out)),
+          "scd_batch_scene_create")
+    return out.value, off
+
+
+def scd_batch_scene_offsets(scene: int, n_scenes: int) -> np.ndarray:
+    off = np.zeros(n_scenes + 1, np.int64)
+    check(lib().scd_batch_scene_offsets(scene, off.ctypes.data), "scd_batch_scene_offsets")
+    return off
 
 
 def scd_scene_destroy(scene: int) -> None:

@@ -20,7 +20,7 @@ STAGE1 = [dict(leaf_size=L, morton_bits=b, space_warp=w)
           for L in (1, 2, 4) for b in (8, 10, 16) for w in (0, 1)]
 
 
-def _time_screen(scene, reps: int) -> float:
+def _time_screen(scene, reps: int, decomp=None) -> float:
     import torch
     from . import _binding as B
     st = torch.cuda.current_stream()
@@ -30,7 +30,7 @@ def _time_screen(scene, reps: int) -> float:
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(st)
         B.scd_build_boxes(scene.handle)
-        B.scd_find_pairs_device(scene.handle)
+        B.scd_find_pairs_device(scene.handle, decomp)
         e1.record(st)
         e1.synchronize()
         if r > 0:  # the first run sizes buffers
@@ -48,9 +48,14 @@ def workload_key(elements, horizon_s: float, tick_s: float, step_desc: str, nbox
     return f"{name}|{h.hexdigest()[:16]}|log2N={int(math.log2(max(nboxes, 1)))}"
 
 
-def tune(scene, reps: int = 2, verbose: bool = False):
+STAGE1_DECOMPOSED = [dict(leaf_size=1, morton_bits=b, space_warp=w)
+                     for b in (8, 10) for w in (0, 1)]
+
+
+def tune(scene, reps: int = 2, verbose: bool = False, decomp=None):
     """Search the tuning space on `scene` (boxes are rebuilt for every
-    candidate).  Returns (best tuning dict, list of (tuning, ms))."""
+    candidate; `decomp` as for scd_find_pairs).  Returns (best tuning dict,
+    list of (tuning, ms))."""
     from . import _binding as B
     base = {f: getattr(B.scd_default_tuning(), f) for f, _ in B.scd_tuning._fields_}
     results = []
@@ -59,18 +64,19 @@ def tune(scene, reps: int = 2, verbose: bool = False):
         t = dict(base)
         t.update(cand)
         scene.set_tuning(t)
-        ms = _time_screen(scene, reps)
+        ms = _time_screen(scene, reps, decomp)
         results.append((t, ms))
         if verbose:
             print(f"autotune {cand} -> {ms:.3f} ms", flush=True)
         return ms
 
     best, best_ms = None, float("inf")
-    for cand in STAGE1:
+    for cand in (STAGE1 if decomp is None else STAGE1_DECOMPOSED):
         ms = run(cand)
         if ms < best_ms:
             best, best_ms = dict(cand), ms
     stage2 = [dict(best, time_scale=ts) for ts in (0.5, 0.25)]
+    stage2 += [dict(best, stack_depth=sd) for sd in (32, 128)]
     if best["leaf_size"] > 1:
         stage2 += [dict(best, block_threads=bt) for bt in (64, 256)]
     for cand in stage2:
@@ -84,7 +90,7 @@ def tune(scene, reps: int = 2, verbose: bool = False):
 
 
 def load_or_tune(scene, key: str, cache_path: str = DEFAULT_CACHE, reps: int = 2,
-                 verbose: bool = False):
+                 verbose: bool = False, decomp=None):
     """The cached tuning for `key`, or a fresh search whose result is cached."""
     cache = {}
     if os.path.exists(cache_path):
@@ -96,7 +102,7 @@ def load_or_tune(scene, key: str, cache_path: str = DEFAULT_CACHE, reps: int = 2
     if key in cache:
         scene.set_tuning(cache[key]["tuning"])
         return cache[key]["tuning"], None
-    best, results = tune(scene, reps=reps, verbose=verbose)
+    best, results = tune(scene, reps=reps, verbose=verbose, decomp=decomp)
     cache[key] = {"tuning": best, "ms": min(ms for _, ms in results)}
     os.makedirs(os.path.dirname(cache_path), exist_ok=True)
     tmp = cache_path + f".{os.getpid()}.tmp"

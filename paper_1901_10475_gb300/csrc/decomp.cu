@@ -30,6 +30,7 @@ struct DecompArgs {
   int64_t T;
   const double2 *rr;  // radial ranges (ALT_BANDS)
   const double *edges;
+  const int32_t *objscene;  // scene of each object (a batch of scenes)
 };
 
 __global__ void k_radial(const scd_element *__restrict__ el, int64_t n, double2 *__restrict__ rr,
@@ -72,6 +73,9 @@ __device__ __forceinline__ CellSpan cell_span(const DecompArgs &d, float4 lo, fl
     c.z0 = lo.z >= 0.f ? 1 : 0;
     c.z1 = hi.z >= 0.f ? 1 : 0;
     c.b0 = c.b1 = 0;
+  } else if (d.kind == kDecompScenes) {
+    c.b0 = c.b1 = d.objscene[obj];  // a scene is one cell
+    c.s0 = c.s1 = c.x0 = c.x1 = c.y0 = c.y1 = c.z0 = c.z1 = 0;
   } else {
     double2 r = d.rr[obj];
     c.b0 = band_of(r.x, d.edges, d.p);
@@ -162,7 +166,10 @@ int build_decomposed(scd_scene *s, const scd_decomp *dc, int64_t &M) {
   d.T = s->T;
   d.rr = nullptr;
   d.edges = nullptr;
-  int n_cells = d.kind == SCD_DECOMP_SLAB_OCT ? d.n_slabs * 8 : d.p;
+  d.objscene = s->d_objscene.p;
+  int n_cells = d.kind == SCD_DECOMP_SLAB_OCT ? d.n_slabs * 8
+                : d.kind == kDecompScenes     ? s->n_scenes
+                                              : d.p;
   s->n_cells = n_cells;
   const int bs = 256;
   if (d.kind == SCD_DECOMP_ALT_BANDS) {

@@ -96,6 +96,7 @@ struct StepArgs {
   const double *band;  // n_bands-1 edges, then n_bands fractions
   int n_bands;
   const float *learned_k;  // per-object learned step [s] (LEARNED), or null
+  const int32_t *objT;     // per-object horizon [ticks] (batches of scenes), or null
 };
 
 __global__ void k_prepare_objects(const scd_element *__restrict__ el, int64_t n, StepArgs sa,
@@ -103,6 +104,7 @@ __global__ void k_prepare_objects(const scd_element *__restrict__ el, int64_t n,
                                   int64_t *__restrict__ segcnt, DevCounters *ctr) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (sa.objT) sa.T = sa.objT[i];  // this object's own scene horizon
   scd_element x = el[i];
   bool ok = x.a_km > 0.0 && x.e >= 0.0 && x.e < 1.0 && x.radius_km >= 0.0 &&
             isfinite(x.a_km) && isfinite(x.e) && isfinite(x.inc_rad) && isfinite(x.raan_rad) &&
@@ -178,6 +180,7 @@ int launch_prepare_objects(scd_scene *s) {
   sa.band = s->d_band.p;
   sa.n_bands = (int)s->band_fracs.size();
   sa.learned_k = s->step_kind == SCD_STEP_LEARNED ? s->d_learned.p : nullptr;
+  sa.objT = s->n_scenes > 0 ? s->d_objT.p : nullptr;
   int bs = 256;
   int64_t g = (s->n + bs - 1) / bs;
   k_prepare_objects<<<(unsigned)g, bs, 0, s->stream>>>(s->d_el.p, s->n, sa, s->d_par.p,
@@ -207,6 +210,7 @@ struct BoxArgs {
   uint32_t *key32;
   unsigned long long *key64;
   uint32_t *id;
+  const int32_t *objT;  // per-object horizon [ticks], or null
 };
 
 __device__ __forceinline__ int64_t find_object(const int64_t *segoff, int64_t n, int64_t b) {
@@ -242,7 +246,8 @@ __global__ void __launch_bounds__(256) k_build_boxes(BoxArgs a) {
   int64_t k = __ldg(a.k + i);
   int64_t tlo = m * k;
   int64_t thi = tlo + k - 1;
-  if (thi > a.T) thi = a.T;
+  const int64_t Ti = a.objT ? (int64_t)__ldg(a.objT + i) : a.T;
+  if (thi > Ti) thi = Ti;
   const ObjParams &p = a.par[i];
   double lo[3], hi[3];
   int iters = 0;
@@ -321,6 +326,7 @@ int launch_build_boxes(scd_scene *s) {
   a.key32 = s->d_key32.p;
   a.key64 = s->tune.morton_bits > 8 ? s->d_key64.p : nullptr;
   a.id = s->d_id.p;
+  a.objT = s->n_scenes > 0 ? s->d_objT.p : nullptr;
   int bs = 256;
   int64_t g = (s->N + bs - 1) / bs;
   if (g > 0) {

@@ -189,6 +189,7 @@ template <class K>
 static int rs_impl(K *keys, uint32_t *vals, int64_t n, int bits, SortScratch &sc,
                    cudaStream_t st) {
   if (n <= 1 || bits <= 0) return SCD_OK;
+  if (n >= (1ll << 32) - 1) return SCD_ERR_CAPACITY;  // positions are 32-bit
   int64_t nblk = (n + kRsTile - 1) / kRsTile;
   if (!sc.keys_alt.ensure(sizeof(K) * (size_t)n, st)) return SCD_ERR_OOM;
   if (vals && !sc.vals_alt.ensure((size_t)n, st)) return SCD_ERR_OOM;

@@ -302,6 +302,13 @@ struct scd_scene {
 
   // learned steps: features, network outputs, steps [s]
   scd::DevBuf<float> d_feat, d_ny, d_learned;
+
+  // a batch of independent scenes in one scene: per-object scene and
+  // horizon, scene object offsets (host), one cell per scene
+  int n_scenes = 0;
+  std::vector<int64_t> scene_off;
+  scd::DevBuf<int32_t> d_objT, d_objscene;
+  scd::DevBuf<int64_t> d_sceneoff, d_pairoff;
   scd::DevBuf<uint32_t> s_leafkey32;
   scd::DevBuf<unsigned long long> s_leafkey64;
   scd::DevBuf<scd::TravNode> d_nodes;
@@ -343,6 +350,8 @@ int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, i
 int build_decomposed(scd_scene *s, const scd_decomp *d, int64_t &n_leaves);
 // learned per-object steps [s] into s->d_learned (SCD_STEP_LEARNED)
 int learned_steps(scd_scene *s);
+// internal decomposition kind of a batch of scenes: one cell per scene
+constexpr int kDecompScenes = 100;
 int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_bits);
 int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits);
 }  // namespace scd

@@ -261,7 +261,16 @@ static int find_pairs_impl(scd_scene *s, const scd_decomp *d, int raw_mode) {
   if (!s) return SCD_ERR_INVALID_ARG;
   if (!s->boxes_built) return SCD_ERR_STATE;
   int dkind = d ? d->kind : SCD_DECOMP_NONE;
-  if (dkind != SCD_DECOMP_NONE) {
+  scd_decomp scenes_dc;
+  if (s->n_scenes > 0) {
+    // a batch of scenes: every scene is one cell of one persistent traversal
+    if (dkind != SCD_DECOMP_NONE || raw_mode) return SCD_ERR_INVALID_ARG;
+    scenes_dc.kind = (scd_decomp_kind)kDecompScenes;
+    scenes_dc.p_bands = 0;
+    scenes_dc.n_slabs = 0;
+    d = &scenes_dc;
+    dkind = kDecompScenes;
+  } else if (dkind != SCD_DECOMP_NONE) {
     if (dkind == SCD_DECOMP_SLAB_OCT) {
       if (d->n_slabs < 1 || d->n_slabs > 4096) return SCD_ERR_INVALID_ARG;
     } else if (dkind == SCD_DECOMP_ALT_BANDS) {
@@ -326,6 +335,8 @@ static int find_pairs_impl(scd_scene *s, const scd_decomp *d, int raw_mode) {
     }
     unsigned long long need = raw_mode ? s->h_ctr.n_raw
                                        : std::max(s->h_ctr.n_starts, s->h_ctr.n_ends);
+    // the record sort indexes with 32-bit counts
+    if (need >= (1ull << 32) - 1) return SCD_ERR_CAPACITY;
     if (need <= (unsigned long long)s->pair_cap) done = true;
     else s->pair_cap = (int64_t)(need + need / 8 + 1024);
   }
@@ -429,6 +440,86 @@ extern "C" SCD_API int scd_batch_find_pairs(scd_scene *const *scenes, int n_scen
   return worst;
 }
 
+extern "C" SCD_API int scd_batch_scene_create(const scd_element *elems,
+                                              const int64_t *scene_offsets,
+                                              const double *horizons_s, int n_scenes,
+                                              double tick_s, const scd_step_policy *step,
+                                              scd_box_mode mode, void *cuda_stream,
+                                              scd_scene **out) {
+  if (!out || !scene_offsets || !horizons_s || n_scenes < 1 || !(tick_s > 0.0))
+    return SCD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (scene_offsets[0] != 0) return SCD_ERR_INVALID_ARG;
+  int64_t n = scene_offsets[n_scenes];
+  std::vector<int32_t> objT((size_t)std::max<int64_t>(n, 1)), objs((size_t)std::max<int64_t>(n, 1));
+  double hmax = 0.0;
+  for (int k = 0; k < n_scenes; ++k) {
+    if (scene_offsets[k + 1] <= scene_offsets[k]) return SCD_ERR_INVALID_ARG;
+    double Tq = horizons_s[k] / tick_s, Tr = nearbyint(Tq);
+    if (!(horizons_s[k] > 0.0) || !isfinite(horizons_s[k]) ||
+        fabs(Tq - Tr) > 1e-9 * std::max(1.0, Tr) || Tr < 1.0 || Tr >= (double)(1 << 24))
+      return SCD_ERR_INVALID_ARG;
+    hmax = std::max(hmax, horizons_s[k]);
+    for (int64_t i = scene_offsets[k]; i < scene_offsets[k + 1]; ++i) {
+      objT[(size_t)i] = (int32_t)Tr;
+      objs[(size_t)i] = k;
+    }
+  }
+  scd_scene *s = nullptr;
+  int rc = scd_scene_create(elems, n, hmax, tick_s, step, mode, cuda_stream, &s);
+  if (rc) return rc;
+  cudaStream_t st = s->stream;
+  s->n_scenes = n_scenes;
+  s->scene_off.assign(scene_offsets, scene_offsets + n_scenes + 1);
+  if (!s->d_objT.ensure(n, st) || !s->d_objscene.ensure(n, st) ||
+      !s->d_sceneoff.ensure(n_scenes + 1, st) || !s->d_pairoff.ensure(n_scenes + 1, st)) {
+    scd_scene_destroy(s);
+    return SCD_ERR_OOM;
+  }
+  if (cudaMemcpyAsync(s->d_objT.p, objT.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(s->d_objscene.p, objs.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+                      st) != cudaSuccess ||
+      cudaMemcpyAsync(s->d_sceneoff.p, scene_offsets, sizeof(int64_t) * (n_scenes + 1),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    scd_scene_destroy(s);
+    return SCD_ERR_CUDA;
+  }
+  *out = s;
+  return SCD_OK;
+}
+
+// first pair of each scene in the sorted list: pairs of scene k have
+// scene_off[k] <= i < scene_off[k+1]
+__global__ void k_pair_offsets(const scd_pair *__restrict__ pr, int64_t np,
+                               const int64_t *__restrict__ soff, int ns,
+                               int64_t *__restrict__ poff) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > ns) return;
+  int64_t key = soff[k];
+  int64_t lo = 0, hi = np;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)pr[mid].i < key) lo = mid + 1; else hi = mid;
+  }
+  poff[k] = lo;
+}
+
+extern "C" SCD_API int scd_batch_scene_offsets(const scd_scene *s, int64_t *host_offsets) {
+  if (!s || !host_offsets || s->n_scenes < 1) return SCD_ERR_INVALID_ARG;
+  cudaStream_t st = s->stream;
+  int ns = s->n_scenes;
+  k_pair_offsets<<<(ns + 1 + 127) / 128, 128, 0, st>>>(s->d_out.p, s->n_out, s->d_sceneoff.p, ns,
+                                                       s->d_pairoff.p);
+  note_launch();
+  if (cudaMemcpyAsync(host_offsets, s->d_pairoff.p, sizeof(int64_t) * (ns + 1),
+                      cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SCD_ERR_CUDA;
+  return SCD_OK;
+}
+
 extern "C" SCD_API int scd_last_metrics(const scd_scene *s, char *json, size_t cap) {
   if (!s || !json || cap == 0) return SCD_ERR_INVALID_ARG;
   int w = snprintf(json, cap,
@@ -437,12 +528,13 @@ extern "C" SCD_API int scd_last_metrics(const scd_scene *s, char *json, size_t c
                    "\"ms_boxes\": %.4f, \"ms_sort\": %.4f, \"ms_build\": %.4f, "
                    "\"ms_traverse\": %.4f, \"ms_canon\": %.4f, \"leaf_size\": %d, "
                    "\"stack_depth\": %d, \"block_threads\": %d, \"morton_bits\": %d, "
-                   "\"launches\": %llu}",
+                   "\"launches\": %llu, \"refs\": %lld, \"cells\": %d}",
                    (long long)s->n, (long long)s->T, (long long)s->N, s->last_node_tests,
                    s->last_leaf_tests, s->last_runs, (long long)s->n_out, s->ms_boxes, s->ms_sort,
                    s->ms_build, s->ms_traverse, s->ms_canon, s->tune.leaf_size,
                    s->tune.stack_depth, s->tune.block_threads, s->tune.morton_bits,
-                   s->last_launches);
+                   s->last_launches, (long long)(s->dkind ? s->n_refs : s->N),
+                   s->dkind ? s->n_cells : 1);
   if (w < 0 || (size_t)w >= cap) return SCD_ERR_BUFFER_TOO_SMALL;
   return SCD_OK;
 }
@@ -472,6 +564,8 @@ extern "C" SCD_API void scd_scene_destroy(scd_scene *s) {
   s->d_refid.release(st); s->d_rr.release(st); s->d_edges.release(st);
   s->d_abits.release(st); s->d_cellroot.release(st);
   s->d_feat.release(st); s->d_ny.release(st); s->d_learned.release(st);
+  s->d_objT.release(st); s->d_objscene.release(st); s->d_sceneoff.release(st);
+  s->d_pairoff.release(st);
   if (s->events_ready)
     for (int k = 0; k < 8; ++k) cudaEventDestroy(s->ev[k]);
   if (s->h_ctr_pinned) cudaFreeHost(s->h_ctr_pinned);

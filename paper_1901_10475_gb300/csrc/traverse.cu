@@ -45,6 +45,7 @@ struct TravArgs {
   const int32_t *cellroot;   // root node of each cell's subtree (-1: none)
   const double2 *rr;         // radial ranges (ALT_BANDS)
   const double *edges;       // band edges (ALT_BANDS)
+  const int32_t *objT;       // per-object horizon (a batch of scenes), or null
 };
 
 // Is `cell` the one cell that reports the overlapping pair (q, b)?  The
@@ -168,7 +169,7 @@ __device__ __forceinline__ void run_ends(const TravArgs &a, const Query &q, floa
 // (they lie close to the pair in the Morton order, so the loads hit cache).
 __device__ __forceinline__ void run_ends_sorted(const TravArgs &a, float4 ql0, float4 qh0,
                                                 int2 qn, float4 bl, float4 bh, int2 bn, int s,
-                                                int e, bool &start, bool &end) {
+                                                int e, int T, bool &start, bool &end) {
   int qt0 = (int)ql0.w, qt1 = (int)qh0.w, bt0 = (int)bl.w, bt1 = (int)bh.w;
   if (start && s > 0) {
     float4 ql = ql0, qh = qh0, cl = bl, ch = bh;
@@ -176,7 +177,7 @@ __device__ __forceinline__ void run_ends_sorted(const TravArgs &a, float4 ql0, f
     if (bt0 == s) { cl = __ldg(a.slo + bn.x); ch = __ldg(a.shi + bn.x); }
     start = !box_overlap(ql, qh, cl, ch);
   }
-  if (end && e < a.T) {
+  if (end && e < T) {
     float4 ql = ql0, qh = qh0, cl = bl, ch = bh;
     if (qt1 == e) { ql = __ldg(a.slo + qn.y); qh = __ldg(a.shi + qn.y); }
     if (bt1 == e) { cl = __ldg(a.slo + bn.y); ch = __ldg(a.shi + bn.y); }
@@ -335,7 +336,8 @@ __device__ __forceinline__ void drain_hits(const TravArgs &a, const uint2 *buf, 
     }
     bool start = valid, end = valid;
     if (valid)
-      run_ends_sorted(a, ql, qh, __ldg(a.nb + h.x), bl, bh, __ldg(a.nb + h.y), s, e, start, end);
+      run_ends_sorted(a, ql, qh, __ldg(a.nb + h.x), bl, bh, __ldg(a.nb + h.y), s, e,
+                      a.objT ? __ldg(a.objT + qo) : a.T, start, end);
     chunk_put(we.s, a.starts, nullptr, &a.ctr->n_starts, a.cap, start,
               pk | (unsigned long long)s, 0u);
     chunk_put(we.e, a.ends, nullptr, &a.ctr->n_ends, a.cap, end, pk | (unsigned long long)e, 0u);
@@ -498,6 +500,7 @@ int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_b
   a.cellroot = s->d_cellroot.p;
   a.rr = s->d_rr.p;
   a.edges = s->d_edges.p;
+  a.objT = s->n_scenes > 0 ? s->d_objT.p : nullptr;
   if (a.dkind != SCD_DECOMP_NONE) a.N = s->n_refs;  // one query per reference
   if (a.L == 1) {
     // persistent: as many blocks as fit on the GPU at once

@@ -88,7 +88,8 @@ def features(elements):
     return f
 
 
-def sweep(elements, horizon_s: float, tick_s: float = 1.0, multipliers=MULTIPLIERS):
+def sweep(elements, horizon_s: float, tick_s: float = 1.0, multipliers=MULTIPLIERS,
+          mode: int = B.SCD_BOX_SPEED):
     """Screen the population once per multiplier.  Returns a dict of arrays:
     boxes [F, n], pairs [F, n] (overlapping box pairs per object), ms [F],
     total_boxes [F], total_pairs [F]."""
@@ -104,7 +105,7 @@ def sweep(elements, horizon_s: float, tick_s: float = 1.0, multipliers=MULTIPLIE
     st = torch.cuda.current_stream()
     for q, f in enumerate(multipliers):
         sc = Scene(elements, horizon_s, tick_s,
-                   B.make_step_policy(B.SCD_STEP_PERIOD_FRACTION, period_fraction=f))
+                   B.make_step_policy(B.SCD_STEP_PERIOD_FRACTION, period_fraction=f), mode=mode)
         sc.build_boxes()
         sc.find_pairs_device()  # sizes the buffers
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
