@@ -74,7 +74,7 @@ WORKLOADS = {
         "metric": "ms per 24h screen at n=100000, learned steps",
         "desc": ("100,000-object mixture with Gaussian LEO shells at 550 and 1150 km, 24 h; "
                  "per-object steps from the 8-64-64-1 step network trained in this run on "
-                 "sweeps of a 16848-object population (6 h, multipliers 50-400)")},
+                 "sweeps of another 100,000-object population of the same shape (2 h, multipliers 50-400)")},
 }
 
 
@@ -351,9 +351,9 @@ def run_learned100k(args, world):
     from paper_1901_10475_gb300 import stepnet as sn
     dev = _device()
     # train on the method's own sweeps of a smaller population
-    train_els = P.catalog_mixture(n=N_OBJ, seed=P.SEED_BASE + 5, dense_shells=True)
+    train_els = P.catalog_mixture(n=100000, seed=P.SEED_BASE + 6, dense_shells=True)
     t0 = time.perf_counter()
-    sw = sn.sweep(train_els, 21600.0, mode=args.mode)
+    sw = sn.sweep(train_els, 7200.0, mode=args.mode)
     c_box, c_hit = sn.fit_cost_model(sw)
     Y = sn.targets(train_els, sw, c_box, c_hit).astype(np.float32)
     X = sn.features(train_els).cpu().numpy()
