@@ -101,7 +101,7 @@ __global__ void k_ref_count(const float4 *__restrict__ lo, const float4 *__restr
 __global__ void k_ref_scatter(const float4 *__restrict__ lo, const float4 *__restrict__ hi,
                               const uint32_t *__restrict__ obj, int64_t N, DecompArgs d,
                               const int64_t *__restrict__ off, const DevCounters *__restrict__ ctr,
-                              int bits, float time_scale, int space_warp,
+                              int bits, float time_scale, int space_warp, int64_t cap,
                               unsigned long long *__restrict__ key, uint32_t *__restrict__ id) {
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= N) return;
@@ -118,14 +118,18 @@ __global__ void k_ref_scatter(const float4 *__restrict__ lo, const float4 *__res
         for (int y = c.y0; y <= c.y1; ++y)
           for (int z = c.z0; z <= c.z1; ++z) {
             unsigned long long cell = (unsigned long long)(s * 8 + (x << 2) + (y << 1) + z);
-            key[o] = (cell << 32) | m;
-            id[o] = (uint32_t)b;
+            if (o < cap) {
+              key[o] = (cell << 32) | m;
+              id[o] = (uint32_t)b;
+            }
             ++o;
           }
   } else {
     for (int k = c.b0; k <= c.b1; ++k) {
-      key[o] = ((unsigned long long)k << 32) | m;
-      id[o] = (uint32_t)b;
+      if (o < cap) {
+        key[o] = ((unsigned long long)k << 32) | m;
+        id[o] = (uint32_t)b;
+      }
       ++o;
     }
   }
@@ -156,7 +160,7 @@ __global__ void k_cell_roots(const int32_t *__restrict__ cfirst, const int32_t *
   root[c] = (first[f] == f && nodes[f].last_r == l) ? f : l;
 }
 
-int build_decomposed(scd_scene *s, const scd_decomp *dc, int64_t &M) {
+int build_decomposed(scd_scene *s, const scd_decomp *dc, int64_t &M, bool capturing) {
   cudaStream_t st = s->stream;
   const int64_t N = s->N;
   DecompArgs d;
@@ -196,21 +200,27 @@ int build_decomposed(scd_scene *s, const scd_decomp *dc, int64_t &M) {
   note_launch();
   int rc = scan_exclusive_i64(s->d_refcnt.p, s->d_refoff.p, N, s->d_scan_tmp, st);
   if (rc) return rc;
-  int64_t R = 0;
-  if (cudaMemcpyAsync(&s->h_ctr_pinned->pad1, s->d_refoff.p + N, sizeof(int64_t),
-                      cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
+  // the reference total goes to the counters (checked after a graph replay)
+  if (cudaMemcpyAsync(&s->d_ctr.p->refs_total, s->d_refoff.p + N, sizeof(int64_t),
+                      cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return SCD_ERR_CUDA;
-  R = (int64_t)s->h_ctr_pinned->pad1;
-  if (R <= 0 || R >= (1ll << 30)) return SCD_ERR_CAPACITY;
-  s->n_refs = R;
+  int64_t R = s->n_refs;  // inside a capture: the size the graph is built for
+  if (!capturing) {
+    if (cudaMemcpyAsync(&s->h_ctr_pinned->refs_total, s->d_refoff.p + N, sizeof(int64_t),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return SCD_ERR_CUDA;
+    R = (int64_t)s->h_ctr_pinned->refs_total;
+    if (R <= 0 || R >= (1ll << 30)) return SCD_ERR_CAPACITY;
+    s->n_refs = R;
+  }
   if (!s->d_refkey.ensure(R, st) || !s->d_refid.ensure(R, st) ||
       !s->s_leafkey64.ensure(R, st) || !s->d_cellroot.ensure(n_cells, st) ||
       !s->d_refcnt.ensure(2 * (size_t)n_cells > (size_t)N ? 2 * n_cells : N, st))
     return SCD_ERR_OOM;
   k_ref_scatter<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(
       s->d_lo.p, s->d_hi.p, s->d_obj.p, N, d, s->d_refoff.p, s->d_ctr.p, s->tune.morton_bits,
-      s->tune.time_scale, s->tune.space_warp, s->d_refkey.p, s->d_refid.p);
+      s->tune.time_scale, s->tune.space_warp, R, s->d_refkey.p, s->d_refid.p);
   note_launch();
   int cbits = 1;
   while ((1 << cbits) < n_cells) ++cbits;

@@ -21,10 +21,21 @@ __device__ __forceinline__ uint32_t digit_of(K key, int shift) {
   return (uint32_t)(key >> shift) & 0xffu;
 }
 
+// The element count: a host value, or (inside a captured graph) a device
+// count clamped to the capacity the grid was sized for.  Blocks past the
+// count see no items: they count zeros and write nothing.
+__device__ __forceinline__ int64_t sort_count(int64_t n, const unsigned long long *d_n) {
+  if (!d_n) return n;
+  unsigned long long v = *d_n;
+  return v < (unsigned long long)n ? (int64_t)v : n;
+}
+
 template <class K>
 __global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const K *__restrict__ keys, int64_t n,
+                                                           const unsigned long long *__restrict__ d_n,
                                                            int shift, uint32_t *__restrict__ counts,
                                                            int64_t nblk) {
+  n = sort_count(n, d_n);
   __shared__ uint32_t wh[kRsWarps][256];
   int w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&wh[0][0])[i] = 0;
@@ -102,8 +113,9 @@ __device__ __forceinline__ uint32_t digit_scan_excl(uint32_t v, uint32_t *buf) {
 template <class K, bool kVals>
 __global__ void __launch_bounds__(kRsThreads) k_rs_downsweep(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
-    uint32_t *__restrict__ vout, int64_t n, int shift, const uint32_t *__restrict__ counts,
-    const uint32_t *__restrict__ totals, int64_t nblk) {
+    uint32_t *__restrict__ vout, int64_t n, const unsigned long long *__restrict__ d_n, int shift,
+    const uint32_t *__restrict__ counts, const uint32_t *__restrict__ totals, int64_t nblk) {
+  n = sort_count(n, d_n);
   extern __shared__ __align__(16) unsigned char smem[];
   K *skeys = (K *)smem;
   uint32_t *svals = (uint32_t *)(smem + sizeof(K) * kRsTile);
@@ -186,8 +198,8 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_downsweep(
 }
 
 template <class K>
-static int rs_impl(K *keys, uint32_t *vals, int64_t n, int bits, SortScratch &sc,
-                   cudaStream_t st) {
+static int rs_impl(K *keys, uint32_t *vals, int64_t n, const unsigned long long *d_n, int bits,
+                   SortScratch &sc, cudaStream_t st) {
   if (n <= 1 || bits <= 0) return SCD_OK;
   if (n >= (1ll << 32) - 1) return SCD_ERR_CAPACITY;  // positions are 32-bit
   int64_t nblk = (n + kRsTile - 1) / kRsTile;
@@ -212,14 +224,14 @@ static int rs_impl(K *keys, uint32_t *vals, int64_t n, int bits, SortScratch &sc
   }
   int passes = 0;
   for (int shift = 0; shift < bits; shift += 8, ++passes) {
-    k_rs_upsweep<K><<<(unsigned)nblk, kRsThreads, 0, st>>>(ka, n, shift, counts, nblk);
+    k_rs_upsweep<K><<<(unsigned)nblk, kRsThreads, 0, st>>>(ka, n, d_n, shift, counts, nblk);
     k_rs_scan<<<256, 1024, 0, st>>>(counts, nblk, totals);
     if (vals)
-      k_rs_downsweep<K, true><<<(unsigned)nblk, kRsThreads, smem, st>>>(ka, va, kb, vb, n, shift,
-                                                                       counts, totals, nblk);
+      k_rs_downsweep<K, true><<<(unsigned)nblk, kRsThreads, smem, st>>>(
+          ka, va, kb, vb, n, d_n, shift, counts, totals, nblk);
     else
       k_rs_downsweep<K, false><<<(unsigned)nblk, kRsThreads, smem, st>>>(
-          ka, nullptr, kb, nullptr, n, shift, counts, totals, nblk);
+          ka, nullptr, kb, nullptr, n, d_n, shift, counts, totals, nblk);
     note_launch(3);
     K *t = ka; ka = kb; kb = t;
     uint32_t *tv = va; va = vb; vb = tv;
@@ -233,12 +245,25 @@ static int rs_impl(K *keys, uint32_t *vals, int64_t n, int bits, SortScratch &sc
 
 int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int bits, SortScratch &sc,
                    cudaStream_t st) {
-  return rs_impl<uint32_t>(keys, vals, n, bits, sc, st);
+  return rs_impl<uint32_t>(keys, vals, n, nullptr, bits, sc, st);
 }
 
 int radix_sort_u64(unsigned long long *keys, uint32_t *vals, int64_t n, int bits,
                    SortScratch &sc, cudaStream_t st) {
-  return rs_impl<unsigned long long>(keys, vals, n, bits, sc, st);
+  return rs_impl<unsigned long long>(keys, vals, n, nullptr, bits, sc, st);
+}
+
+int sort_reserve(SortScratch &sc, int64_t n, size_t key_bytes, bool vals, cudaStream_t st) {
+  int64_t nblk = (n + kRsTile - 1) / kRsTile;
+  if (!sc.keys_alt.ensure(key_bytes * (size_t)n, st)) return SCD_ERR_OOM;
+  if (vals && !sc.vals_alt.ensure((size_t)n, st)) return SCD_ERR_OOM;
+  if (!sc.counts.ensure((size_t)(256 * nblk + 256), st)) return SCD_ERR_OOM;
+  return SCD_OK;
+}
+
+int radix_sort_u64_dev(unsigned long long *keys, uint32_t *vals, int64_t n_cap,
+                       const unsigned long long *d_n, int bits, SortScratch &sc, cudaStream_t st) {
+  return rs_impl<unsigned long long>(keys, vals, n_cap, d_n, bits, sc, st);
 }
 
 }  // namespace scd

@@ -62,7 +62,7 @@ struct DevCounters {
   unsigned int build_flags;        // ERR_KEPLER, ERR_INVALID
   unsigned int kepler_max_iter;
   unsigned long long n_boxes;      // seg_off[n]
-  unsigned long long pad1;
+  unsigned long long refs_total;   // references of the last decomposed build
 };
 
 // Traversal node: both children's boxes inline, child links and the
@@ -209,6 +209,21 @@ struct DevBuf {
     n = c;
     return true;
   }
+  // grow to at least `count` elements keeping the first `used`
+  bool grow_keep(size_t count, size_t used, cudaStream_t st) {
+    if (count <= n && p) return true;
+    T *q = (T *)dev_alloc((count < 1 ? 1 : count) * sizeof(T), st);
+    if (!q) return false;
+    if (p && used > 0 &&
+        cudaMemcpyAsync(q, p, used * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+      dev_free(q, st);
+      return false;
+    }
+    if (p) dev_free(p, st);
+    p = q;
+    n = count < 1 ? 1 : count;
+    return true;
+  }
   void release(cudaStream_t st) {
     if (p) dev_free(p, st);
     p = nullptr;
@@ -235,6 +250,13 @@ int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int bits, SortScra
                    cudaStream_t st);
 int radix_sort_u64(unsigned long long *keys, uint32_t *vals, int64_t n, int bits,
                    SortScratch &sc, cudaStream_t st);
+// size the scratch for sorts of up to n elements (nothing allocated later)
+int sort_reserve(SortScratch &sc, int64_t n, size_t key_bytes, bool vals, cudaStream_t st);
+// the same with the element count read on the device (min(*d_n, n_cap)), for
+// sorts inside a captured graph; grids are sized for n_cap
+int radix_sort_u64_dev(unsigned long long *keys, uint32_t *vals, int64_t n_cap,
+                       const unsigned long long *d_n, int bits, SortScratch &sc,
+                       cudaStream_t st);
 
 // process-wide count of kernel launches issued by this library
 void note_launch(int k = 1);
@@ -309,6 +331,18 @@ struct scd_scene {
   std::vector<int64_t> scene_off;
   scd::DevBuf<int32_t> d_objT, d_objscene;
   scd::DevBuf<int64_t> d_sceneoff, d_pairoff;
+
+  // graph mode: the captured find sequence and the sizes it was captured for
+  cudaGraphExec_t graph_exec = nullptr;
+  bool graph_ok = false;
+  int last_graph = 0;  // last find: 0 eager, 1 eager + capture, 2 replay
+  // capture and replay run on the scene's own stream, ordered after and
+  // before the caller's stream by events (the legacy default stream cannot
+  // be captured)
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t g_in = nullptr, g_out = nullptr;
+  int64_t graph_key[8] = {};
+  int64_t graph_M = 0;
   scd::DevBuf<uint32_t> s_leafkey32;
   scd::DevBuf<unsigned long long> s_leafkey64;
   scd::DevBuf<scd::TravNode> d_nodes;
@@ -347,11 +381,14 @@ template <class K>
 int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, int64_t Nq,
                K *leafkey, int cell_shift, int64_t &M);
 // decomposed screen: references, their sort, the tree and each cell's root
-int build_decomposed(scd_scene *s, const scd_decomp *d, int64_t &n_leaves);
+int build_decomposed(scd_scene *s, const scd_decomp *d, int64_t &n_leaves,
+                     bool capturing = false);
 // learned per-object steps [s] into s->d_learned (SCD_STEP_LEARNED)
 int learned_steps(scd_scene *s);
 // internal decomposition kind of a batch of scenes: one cell per scene
 constexpr int kDecompScenes = 100;
 int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_bits);
 int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits);
+// canonical list with every count read on the device (graph capture)
+int canonicalize_dev(scd_scene *s, int obj_bits, int t_bits);
 }  // namespace scd

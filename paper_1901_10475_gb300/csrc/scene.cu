@@ -257,6 +257,29 @@ static int bits_for(int64_t v) {
   return b;
 }
 
+static int find_eager(scd_scene *s, const scd_decomp *d, int dkind, int raw_mode, int ob, int tb);
+static int find_graph(scd_scene *s, const scd_decomp *d, int dkind, int ob, int tb);
+
+static void finish_metrics(scd_scene *s, int raw_mode) {
+  s->last_node_tests = s->h_ctr.node_tests;
+  s->last_leaf_tests = s->h_ctr.leaf_tests;
+  s->last_runs = raw_mode ? s->h_ctr.v_raw : s->h_ctr.v_starts;
+  s->last_launches = launch_count() - s->launch_mark;
+  if (s->events_ready) {
+    // phases of a replayed graph are not timed: -1
+    auto span = [](cudaEvent_t a, cudaEvent_t b) {
+      float ms = 0;
+      return cudaEventElapsedTime(&ms, a, b) == cudaSuccess ? (double)ms : -1.0;
+    };
+    s->ms_boxes = span(s->ev[0], s->ev[1]);
+    s->ms_sort = span(s->ev[2], s->ev[3]);
+    s->ms_build = span(s->ev[3], s->ev[4]);
+    s->ms_traverse = span(s->ev[4], s->ev[5]);
+    s->ms_canon = span(s->ev[5], s->ev[6]);
+    cudaGetLastError();
+  }
+}
+
 static int find_pairs_impl(scd_scene *s, const scd_decomp *d, int raw_mode) {
   if (!s) return SCD_ERR_INVALID_ARG;
   if (!s->boxes_built) return SCD_ERR_STATE;
@@ -295,6 +318,15 @@ static int find_pairs_impl(scd_scene *s, const scd_decomp *d, int raw_mode) {
     int leaf;
     ~Restore() { s->tune.leaf_size = leaf; }
   } restore{s, leaf_saved};
+  if (s->tune.use_graph && !raw_mode) return find_graph(s, d, dkind, ob, tb);
+  return find_eager(s, d, dkind, raw_mode, ob, tb);
+}
+
+// The find sequence run op by op, with host reads of the counters between
+// phases (buffer growth, stack depth, checks).
+static int find_eager(scd_scene *s, const scd_decomp *d, int dkind, int raw_mode, int ob, int tb) {
+  cudaStream_t st = s->stream;
+  int64_t N = s->N;
   if (s->events_ready) cudaEventRecord(s->ev[2], st);
   int64_t M = 0;
   if (dkind == SCD_DECOMP_NONE) {
@@ -352,19 +384,122 @@ static int find_pairs_impl(scd_scene *s, const scd_decomp *d, int raw_mode) {
   unsigned int flags = 0;
   cudaMemcpy(&flags, &s->d_ctr.p->trav_flags, sizeof(flags), cudaMemcpyDeviceToHost);
   if (flags & ERR_ZIP) return SCD_ERR_INTERNAL;
-  s->last_node_tests = s->h_ctr.node_tests;
-  s->last_leaf_tests = s->h_ctr.leaf_tests;
-  s->last_runs = raw_mode ? s->h_ctr.v_raw : s->h_ctr.v_starts;
-  s->last_launches = launch_count() - s->launch_mark;
-  if (s->events_ready) {
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, s->ev[0], s->ev[1]) == cudaSuccess) s->ms_boxes = ms;
-    cudaEventElapsedTime(&ms, s->ev[2], s->ev[3]); s->ms_sort = ms;
-    cudaEventElapsedTime(&ms, s->ev[3], s->ev[4]); s->ms_build = ms;
-    cudaEventElapsedTime(&ms, s->ev[4], s->ev[5]); s->ms_traverse = ms;
-    cudaEventElapsedTime(&ms, s->ev[5], s->ev[6]); s->ms_canon = ms;
+  s->graph_M = M;
+  finish_metrics(s, raw_mode);
+  return SCD_OK;
+}
+
+// Everything find_eager does, enqueued without any host wait (sizes from the
+// last eager run, counts of the record sorts read on the device), for
+// capture into one CUDA graph.
+static int enqueue_find(scd_scene *s, const scd_decomp *d, int dkind, int ob, int tb) {
+  cudaStream_t st = s->stream;
+  int64_t M = 0;
+  if (s->events_ready) cudaEventRecord(s->ev[2], st);
+  if (dkind == SCD_DECOMP_NONE) {
+    int kb = 4 * s->tune.morton_bits;
+    if (s->tune.morton_bits > 8) {
+      TRY(radix_sort_u64(s->d_key64.p, s->d_id.p, s->N, kb, s->sort_sc, st));
+    } else {
+      TRY(radix_sort_u32(s->d_key32.p, s->d_id.p, s->N, kb, s->sort_sc, st));
+    }
+    if (s->events_ready) cudaEventRecord(s->ev[3], st);
+    TRY(build_hierarchy(s, M));
+  } else {
+    if (s->events_ready) cudaEventRecord(s->ev[3], st);
+    TRY(build_decomposed(s, d, M, true));
+  }
+  if (M != s->graph_M) return SCD_ERR_STATE;
+  if (s->events_ready) cudaEventRecord(s->ev[4], st);
+  if (cudaMemsetAsync(s->d_ctr.p, 0, offsetof(DevCounters, extent_bits), st) != cudaSuccess)
+    return SCD_ERR_CUDA;
+  TRY(traverse(s, M, 0, ob, tb));
+  if (s->events_ready) cudaEventRecord(s->ev[5], st);
+  TRY(canonicalize_dev(s, ob, tb));
+  if (s->events_ready) cudaEventRecord(s->ev[6], st);
+  return SCD_OK;
+}
+
+static void graph_key_of(const scd_scene *s, int64_t key[8]) {
+  key[0] = s->dkind;
+  key[1] = s->n_slabs * 100000 + s->p_bands;
+  key[2] = s->N;
+  key[3] = s->pair_cap;
+  key[4] = s->tune.leaf_size * 1000 + s->tune.stack_depth;
+  key[5] = s->tune.morton_bits * 10 + s->tune.space_warp;
+  key[6] = (int64_t)(s->tune.time_scale * 1e6f);
+  key[7] = s->dkind ? s->n_refs : 0;
+}
+
+// Replay the captured find sequence; one read of the counters decides
+// whether its sizes still held (else: an eager run, then a new capture).
+static int find_graph(scd_scene *s, const scd_decomp *d, int dkind, int ob, int tb) {
+  cudaStream_t st = s->stream;
+  if (!s->gstream) {
+    if (cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->g_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->g_out, cudaEventDisableTiming) != cudaSuccess)
+      return SCD_ERR_CUDA;
+  }
+  int64_t key[8];
+  graph_key_of(s, key);
+  if (s->graph_ok && memcmp(key, s->graph_key, sizeof(key)) == 0) {
+    // the graph runs after everything queued on the caller's stream, and the
+    // caller's stream waits for it
+    if (cudaEventRecord(s->g_in, st) != cudaSuccess ||
+        cudaStreamWaitEvent(s->gstream, s->g_in, 0) != cudaSuccess ||
+        cudaGraphLaunch(s->graph_exec, s->gstream) != cudaSuccess ||
+        cudaEventRecord(s->g_out, s->gstream) != cudaSuccess ||
+        cudaStreamWaitEvent(st, s->g_out, 0) != cudaSuccess)
+      return SCD_ERR_CUDA;
+    TRY(read_counters(s));
+    const DevCounters &c = s->h_ctr;
+    if (c.build_flags & ERR_INVALID) return SCD_ERR_INVALID_ARG;
+    if (c.build_flags & ERR_KEPLER) return SCD_ERR_KEPLER_NOCONV;
+    bool fits = !(c.trav_flags & (ERR_STACK | ERR_ZIP)) &&
+                std::max(c.n_starts, c.n_ends) <= (unsigned long long)s->pair_cap &&
+                c.v_starts == c.v_ends &&
+                (!dkind || (int64_t)c.refs_total == s->n_refs);
+    if (fits) {
+      s->n_out = (int64_t)c.v_starts;
+      s->last_graph = 2;
+      finish_metrics(s, 0);
+      return SCD_OK;
+    }
+    s->graph_ok = false;
+  }
+  // eager run (sizes every buffer; its result is the answer), then capture
+  TRY(find_eager(s, d, dkind, 0, ob, tb));
+  s->last_graph = 0;
+  if (s->graph_exec) {
+    cudaGraphExecDestroy(s->graph_exec);
+    s->graph_exec = nullptr;
+  }
+  // every buffer the captured sequence touches is sized now: nothing may be
+  // allocated while capturing
+  if (!s->d_out.grow_keep(s->pair_cap, s->n_out, st) ||
+      sort_reserve(s->sort_sc, s->pair_cap, sizeof(unsigned long long), false, st) != SCD_OK ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SCD_OK;  // no graph this time; the eager result stands
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(s->gstream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return SCD_OK;
+  }
+  s->stream = s->gstream;  // every launch below goes to the captured stream
+  int rc = enqueue_find(s, d, dkind, ob, tb);
+  cudaError_t e = cudaStreamEndCapture(s->gstream, &g);
+  s->stream = st;
+  if (rc == SCD_OK && e == cudaSuccess && g &&
+      cudaGraphInstantiate(&s->graph_exec, g, 0) == cudaSuccess) {
+    graph_key_of(s, s->graph_key);
+    s->graph_ok = true;
+    s->last_graph = 1;
+  } else {
+    s->graph_exec = nullptr;
     cudaGetLastError();
   }
+  if (g) cudaGraphDestroy(g);
   return SCD_OK;
 }
 
@@ -528,13 +663,13 @@ extern "C" SCD_API int scd_last_metrics(const scd_scene *s, char *json, size_t c
                    "\"ms_boxes\": %.4f, \"ms_sort\": %.4f, \"ms_build\": %.4f, "
                    "\"ms_traverse\": %.4f, \"ms_canon\": %.4f, \"leaf_size\": %d, "
                    "\"stack_depth\": %d, \"block_threads\": %d, \"morton_bits\": %d, "
-                   "\"launches\": %llu, \"refs\": %lld, \"cells\": %d}",
+                   "\"launches\": %llu, \"refs\": %lld, \"cells\": %d, \"graph\": %d}",
                    (long long)s->n, (long long)s->T, (long long)s->N, s->last_node_tests,
                    s->last_leaf_tests, s->last_runs, (long long)s->n_out, s->ms_boxes, s->ms_sort,
                    s->ms_build, s->ms_traverse, s->ms_canon, s->tune.leaf_size,
                    s->tune.stack_depth, s->tune.block_threads, s->tune.morton_bits,
                    s->last_launches, (long long)(s->dkind ? s->n_refs : s->N),
-                   s->dkind ? s->n_cells : 1);
+                   s->dkind ? s->n_cells : 1, s->last_graph);
   if (w < 0 || (size_t)w >= cap) return SCD_ERR_BUFFER_TOO_SMALL;
   return SCD_OK;
 }
@@ -568,6 +703,10 @@ extern "C" SCD_API void scd_scene_destroy(scd_scene *s) {
   s->d_pairoff.release(st);
   if (s->events_ready)
     for (int k = 0; k < 8; ++k) cudaEventDestroy(s->ev[k]);
+  if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+  if (s->gstream) cudaStreamDestroy(s->gstream);
+  if (s->g_in) cudaEventDestroy(s->g_in);
+  if (s->g_out) cudaEventDestroy(s->g_out);
   if (s->h_ctr_pinned) cudaFreeHost(s->h_ctr_pinned);
   delete s;
 }

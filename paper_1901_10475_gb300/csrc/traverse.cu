@@ -543,8 +543,10 @@ int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_b
 // ---------------------------------------------------------------------------
 __global__ void k_zip(const unsigned long long *__restrict__ starts,
                       const unsigned long long *__restrict__ ends, const uint32_t *__restrict__ rawv,
-                      int64_t n, int ob, int tb, scd_pair *__restrict__ out, DevCounters *ctr) {
+                      int64_t n, const unsigned long long *__restrict__ d_n, int ob, int tb,
+                      scd_pair *__restrict__ out, DevCounters *ctr) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (d_n && (unsigned long long)k >= *d_n) return;  // count known on the device only
   if (k >= n) return;
   unsigned long long ks = starts[k];
   unsigned long long tmask = (1ull << tb) - 1ull, omask = (1ull << ob) - 1ull;
@@ -583,9 +585,27 @@ int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits) {
   if (n > 0)
     k_zip<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->d_starts.p, s->d_ends.p,
                                                        raw_mode ? s->d_rawval.p : nullptr, n,
-                                                       obj_bits, t_bits, s->d_out.p, s->d_ctr.p);
+                                                       nullptr, obj_bits, t_bits, s->d_out.p,
+                                                       s->d_ctr.p);
   if (n > 0) note_launch();
   s->n_out = n;
+  return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
+}
+
+int canonicalize_dev(scd_scene *s, int obj_bits, int t_bits) {
+  cudaStream_t st = s->stream;
+  const int64_t cap = s->pair_cap;
+  int bits = 2 * obj_bits + t_bits;
+  if (!s->d_out.ensure(cap, st)) return SCD_ERR_OOM;
+  DevCounters *c = s->d_ctr.p;
+  int rc = radix_sort_u64_dev(s->d_starts.p, nullptr, cap, &c->n_starts, bits, s->sort_sc, st);
+  if (rc) return rc;
+  rc = radix_sort_u64_dev(s->d_ends.p, nullptr, cap, &c->n_ends, bits, s->sort_sc, st);
+  if (rc) return rc;
+  k_zip<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(s->d_starts.p, s->d_ends.p, nullptr, cap,
+                                                       &c->v_starts, obj_bits, t_bits, s->d_out.p,
+                                                       c);
+  note_launch();
   return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
 }
 
