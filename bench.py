@@ -148,6 +148,7 @@ def algorithmic_bytes(m: dict, n: int) -> dict:
     R = m.get("refs") or N  # sorted entries (references when decomposed)
     M = R
     runs = m["records"]
+    opens = m.get("open_runs", runs)  # runs of more than one cell: one end record each
     key_b = 4 if m["morton_bits"] <= 8 else 8
     passes = (4 * m["morton_bits"] + 7) // 8
     pair_bits = 2 * max(1, int(np.ceil(np.log2(max(n, 2))))) + int(np.ceil(np.log2(m["T"] + 1)))
@@ -160,9 +161,10 @@ def algorithmic_bytes(m: dict, n: int) -> dict:
         # gather boxes by id; neighbour positions; hierarchy nodes and refit
         "build": R * (4 + 32 + 32 + 4 + 8 + 4) + M * (key_b + 40 + 32 + 16),
         # every sorted box and compact node read at least once; records written
-        "traverse": R * (32 + 8) + (M - 1) * 40 + 2 * runs * 8,
-        # two key-only sorts of the run records, then the output pairs
-        "canon": 2 * ppasses * runs * 8 * 3 + runs * (16 + 16),
+        "traverse": R * (32 + 8) + (M - 1) * 40 + (runs + opens) * 8,
+        # key-only sorts of the run starts and of the open runs' ends (keys
+        # read twice, written once per pass), the open count, the unpack
+        "canon": ppasses * (runs + opens) * 8 * 3 + runs * 8 + runs * (8 + 16) + opens * 8,
     }
 
 
@@ -486,7 +488,8 @@ def main():
     if "metrics" in r:
         m = r["metrics"]
         line["config"].update({"boxes": m["boxes"], "pairs": r["n_pairs"],
-                               "records": m["records"], "leaf_size": m["leaf_size"],
+                               "records": m["records"], "open_runs": m["open_runs"],
+                               "leaf_size": m["leaf_size"],
                                "morton_bits": m["morton_bits"], "stack_depth": m["stack_depth"],
                                "block_threads": m["block_threads"]})
         line["box_pair_tests_per_s"] = r["tests"] / (sum(r["times"]) * 1e-3)

@@ -41,11 +41,16 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const K *__restrict__
   for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&wh[0][0])[i] = 0;
   __syncthreads();
   int64_t base = (int64_t)blockIdx.x * kRsTile;
-#pragma unroll 4
+  // all loads first, so that every item's load is in flight together
+  uint32_t dig[kRsItems];
+#pragma unroll
   for (int k = 0; k < kRsItems; ++k) {
     int64_t idx = base + (int64_t)k * kRsThreads + threadIdx.x;
-    if (idx < n) atomicAdd(&wh[w][digit_of(keys[idx], shift)], 1u);
+    dig[k] = idx < n ? digit_of(keys[idx], shift) : 256u;
   }
+#pragma unroll
+  for (int k = 0; k < kRsItems; ++k)
+    if (dig[k] < 256u) atomicAdd(&wh[w][dig[k]], 1u);
   __syncthreads();
   for (int d = threadIdx.x; d < 256; d += kRsThreads) {
     uint32_t s = 0;
@@ -143,12 +148,18 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_downsweep(
   K key[kRsItems];
   uint32_t val[kRsItems];
   uint32_t rnk[kRsItems];
+  // all loads first: the ranking below synchronises the warp between items,
+  // which would otherwise hold each load back until the previous item
 #pragma unroll
   for (int k = 0; k < kRsItems; ++k) {
     int64_t idx = seg + k * 32 + lane;
     bool valid = idx < n;
     key[k] = valid ? kin[idx] : (K)0;
     if (kVals) val[k] = valid ? vin[idx] : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < kRsItems; ++k) {
+    bool valid = seg + k * 32 + lane < n;
     uint32_t d = valid ? digit_of(key[k], shift) : 256u;
     unsigned peers = __match_any_sync(0xffffffffu, d);
     uint32_t before = valid ? wcnt[w][d] : 0u;
@@ -198,9 +209,9 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_downsweep(
 }
 
 template <class K>
-static int rs_impl(K *keys, uint32_t *vals, int64_t n, const unsigned long long *d_n, int bits,
-                   SortScratch &sc, cudaStream_t st) {
-  if (n <= 1 || bits <= 0) return SCD_OK;
+static int rs_impl(K *keys, uint32_t *vals, int64_t n, const unsigned long long *d_n, int lo,
+                   int bits, SortScratch &sc, cudaStream_t st) {
+  if (n <= 1 || bits <= lo) return SCD_OK;
   if (n >= (1ll << 32) - 1) return SCD_ERR_CAPACITY;  // positions are 32-bit
   int64_t nblk = (n + kRsTile - 1) / kRsTile;
   if (!sc.keys_alt.ensure(sizeof(K) * (size_t)n, st)) return SCD_ERR_OOM;
@@ -223,7 +234,7 @@ static int rs_impl(K *keys, uint32_t *vals, int64_t n, const unsigned long long 
     attr_set[ki][vi] = true;
   }
   int passes = 0;
-  for (int shift = 0; shift < bits; shift += 8, ++passes) {
+  for (int shift = lo; shift < bits; shift += 8, ++passes) {
     k_rs_upsweep<K><<<(unsigned)nblk, kRsThreads, 0, st>>>(ka, n, d_n, shift, counts, nblk);
     k_rs_scan<<<256, 1024, 0, st>>>(counts, nblk, totals);
     if (vals)
@@ -245,12 +256,21 @@ static int rs_impl(K *keys, uint32_t *vals, int64_t n, const unsigned long long 
 
 int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int bits, SortScratch &sc,
                    cudaStream_t st) {
-  return rs_impl<uint32_t>(keys, vals, n, nullptr, bits, sc, st);
+  return rs_impl<uint32_t>(keys, vals, n, nullptr, 0, bits, sc, st);
 }
 
 int radix_sort_u64(unsigned long long *keys, uint32_t *vals, int64_t n, int bits,
                    SortScratch &sc, cudaStream_t st) {
-  return rs_impl<unsigned long long>(keys, vals, n, nullptr, bits, sc, st);
+  return rs_impl<unsigned long long>(keys, vals, n, nullptr, 0, bits, sc, st);
+}
+
+int radix_sort_u64(unsigned long long *keys, uint32_t *vals, int64_t n, int lo, int bits,
+                   SortScratch &sc, cudaStream_t st) {
+  return rs_impl<unsigned long long>(keys, vals, n, nullptr, lo, bits, sc, st);
+}
+
+void scan_u32_exclusive(uint32_t *a, int64_t n, uint32_t *total, cudaStream_t st) {
+  k_rs_scan<<<1, 1024, 0, st>>>(a, n, total);
 }
 
 int sort_reserve(SortScratch &sc, int64_t n, size_t key_bytes, bool vals, cudaStream_t st) {
@@ -262,8 +282,9 @@ int sort_reserve(SortScratch &sc, int64_t n, size_t key_bytes, bool vals, cudaSt
 }
 
 int radix_sort_u64_dev(unsigned long long *keys, uint32_t *vals, int64_t n_cap,
-                       const unsigned long long *d_n, int bits, SortScratch &sc, cudaStream_t st) {
-  return rs_impl<unsigned long long>(keys, vals, n_cap, d_n, bits, sc, st);
+                       const unsigned long long *d_n, int lo, int bits, SortScratch &sc,
+                       cudaStream_t st) {
+  return rs_impl<unsigned long long>(keys, vals, n_cap, d_n, lo, bits, sc, st);
 }
 
 }  // namespace scd

@@ -25,7 +25,7 @@ enum : uint32_t {
   ERR_KEPLER = 1u << 0,     // Kepler iteration hit its limit
   ERR_STACK = 1u << 1,      // traversal stack overflow
   ERR_INVALID = 1u << 2,    // invalid element seen on the device
-  ERR_ZIP = 1u << 3,        // run starts and ends did not pair up
+  ERR_ZIP = 1u << 3,        // open run starts and run ends did not pair up
   ERR_TIMEOUT = 1u << 4,    // a bounded wait gave up
 };
 
@@ -86,6 +86,14 @@ struct __align__(16) QBox {
 };
 constexpr uint32_t kQLeftLeaf = 0x80000000u, kQRightLeaf = 0x40000000u;
 constexpr uint32_t kQIndex = 0x3fffffffu;
+
+// Both child boxes of a compact node (32 bytes, 32-byte aligned) in one
+// 256-bit read-only load.
+__device__ __forceinline__ void ldg_qbox_pair(const QBox *p, uint4 &l, uint4 &r) {
+  asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(l.x), "=r"(l.y), "=r"(l.z), "=r"(l.w), "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p));
+}
 
 // the scene frame of the quantisation: x, y, z in [-R, R] km, t in [0, T]
 struct QFrame {
@@ -250,13 +258,30 @@ int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int bits, SortScra
                    cudaStream_t st);
 int radix_sort_u64(unsigned long long *keys, uint32_t *vals, int64_t n, int bits,
                    SortScratch &sc, cudaStream_t st);
+// the same by key bits [lo, bits) only (the bits below lo are payload)
+int radix_sort_u64(unsigned long long *keys, uint32_t *vals, int64_t n, int lo, int bits,
+                   SortScratch &sc, cudaStream_t st);
 // size the scratch for sorts of up to n elements (nothing allocated later)
 int sort_reserve(SortScratch &sc, int64_t n, size_t key_bytes, bool vals, cudaStream_t st);
 // the same with the element count read on the device (min(*d_n, n_cap)), for
 // sorts inside a captured graph; grids are sized for n_cap
 int radix_sort_u64_dev(unsigned long long *keys, uint32_t *vals, int64_t n_cap,
-                       const unsigned long long *d_n, int bits, SortScratch &sc,
+                       const unsigned long long *d_n, int lo, int bits, SortScratch &sc,
                        cudaStream_t st);
+
+// Run starts carry their last tick below the (i, j, first tick) key when
+// both fit in 64 bits and the all-ones tick field is free to tag open runs
+// (T < 2^t_bits - 1); otherwise the last tick travels as a 32-bit sort value
+// and open runs carry 0xffffffff.
+inline bool runs_packed(int obj_bits, int t_bits, int64_t T) {
+  return 2 * (obj_bits + t_bits) <= 64 && T < (1ll << t_bits) - 1;
+}
+inline uint32_t open_tag(bool packed, int t_bits) {
+  return packed ? (uint32_t)((1ull << t_bits) - 1ull) : 0xffffffffu;
+}
+
+// exclusive prefix sum of a[0..n) in place; *total = the sum (one block)
+void scan_u32_exclusive(uint32_t *a, int64_t n, uint32_t *total, cudaStream_t st);
 
 // process-wide count of kernel launches issued by this library
 void note_launch(int k = 1);
@@ -357,6 +382,7 @@ struct scd_scene {
   // pair emission and canonical list
   int64_t pair_cap = 0;
   scd::DevBuf<unsigned long long> d_starts, d_ends;
+  scd::DevBuf<uint32_t> d_tilecnt;  // open run starts per unpack tile
   scd::DevBuf<uint32_t> d_rawval;
   scd::DevBuf<scd_pair> d_out;
   int64_t n_out = 0;
@@ -364,7 +390,7 @@ struct scd_scene {
 
   // metrics of the last find_pairs
   double ms_sort = 0, ms_build = 0, ms_traverse = 0, ms_canon = 0, ms_boxes = 0;
-  unsigned long long last_node_tests = 0, last_leaf_tests = 0, last_runs = 0;
+  unsigned long long last_node_tests = 0, last_leaf_tests = 0, last_runs = 0, last_open = 0;
   unsigned long long launch_mark = 0, last_launches = 0;  // kernels of build + find
   cudaEvent_t ev[8] = {};
   bool events_ready = false;

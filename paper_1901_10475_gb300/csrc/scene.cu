@@ -264,6 +264,7 @@ static void finish_metrics(scd_scene *s, int raw_mode) {
   s->last_node_tests = s->h_ctr.node_tests;
   s->last_leaf_tests = s->h_ctr.leaf_tests;
   s->last_runs = raw_mode ? s->h_ctr.v_raw : s->h_ctr.v_starts;
+  s->last_open = raw_mode ? 0 : s->h_ctr.v_ends;
   s->last_launches = launch_count() - s->launch_mark;
   if (s->events_ready) {
     // phases of a replayed graph are not timed: -1
@@ -351,8 +352,8 @@ static int find_eager(scd_scene *s, const scd_decomp *d, int dkind, int raw_mode
   if (s->pair_cap == 0) s->pair_cap = std::max<int64_t>(1 << 16, N / 4);
   bool done = false;
   for (int attempt = 0; attempt < 6 && !done; ++attempt) {
-    if (!s->d_starts.ensure(s->pair_cap, st) || !s->d_ends.ensure(s->pair_cap, st) ||
-        !s->d_rawval.ensure(s->pair_cap, st))
+    if (!s->d_starts.ensure(s->pair_cap, st) || (!raw_mode && !s->d_ends.ensure(s->pair_cap, st)) ||
+        ((raw_mode || !runs_packed(ob, tb, s->T)) && !s->d_rawval.ensure(s->pair_cap, st)))
       return SCD_ERR_OOM;
     // zero the emission counters, keep the box-build flags
     if (cudaMemsetAsync(s->d_ctr.p, 0, offsetof(DevCounters, extent_bits), st) != cudaSuccess)
@@ -375,7 +376,6 @@ static int find_eager(scd_scene *s, const scd_decomp *d, int dkind, int raw_mode
   if (!done) return SCD_ERR_INTERNAL;
   if (s->h_ctr.build_flags & ERR_INVALID) return SCD_ERR_INVALID_ARG;
   if (s->h_ctr.build_flags & ERR_KEPLER) return SCD_ERR_KEPLER_NOCONV;
-  if (!raw_mode && s->h_ctr.v_starts != s->h_ctr.v_ends) return SCD_ERR_INTERNAL;
   if (s->events_ready) cudaEventRecord(s->ev[5], st);
   // A9: canonical list
   TRY(canonicalize(s, raw_mode, ob, tb));
@@ -458,7 +458,6 @@ static int find_graph(scd_scene *s, const scd_decomp *d, int dkind, int ob, int 
     if (c.build_flags & ERR_KEPLER) return SCD_ERR_KEPLER_NOCONV;
     bool fits = !(c.trav_flags & (ERR_STACK | ERR_ZIP)) &&
                 std::max(c.n_starts, c.n_ends) <= (unsigned long long)s->pair_cap &&
-                c.v_starts == c.v_ends &&
                 (!dkind || (int64_t)c.refs_total == s->n_refs);
     if (fits) {
       s->n_out = (int64_t)c.v_starts;
@@ -478,7 +477,9 @@ static int find_graph(scd_scene *s, const scd_decomp *d, int dkind, int ob, int 
   // every buffer the captured sequence touches is sized now: nothing may be
   // allocated while capturing
   if (!s->d_out.grow_keep(s->pair_cap, s->n_out, st) ||
-      sort_reserve(s->sort_sc, s->pair_cap, sizeof(unsigned long long), false, st) != SCD_OK ||
+      sort_reserve(s->sort_sc, s->pair_cap, sizeof(unsigned long long),
+                   !runs_packed(ob, tb, s->T), st) != SCD_OK ||
+      !s->d_tilecnt.ensure((size_t)(s->pair_cap / 2048 + 2), st) ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return SCD_OK;  // no graph this time; the eager result stands
   cudaGraph_t g = nullptr;
@@ -659,13 +660,14 @@ extern "C" SCD_API int scd_last_metrics(const scd_scene *s, char *json, size_t c
   if (!s || !json || cap == 0) return SCD_ERR_INVALID_ARG;
   int w = snprintf(json, cap,
                    "{\"n\": %lld, \"T\": %lld, \"boxes\": %lld, \"node_tests\": %llu, "
-                   "\"leaf_tests\": %llu, \"records\": %llu, \"pairs\": %lld, "
+                   "\"leaf_tests\": %llu, \"records\": %llu, \"open_runs\": %llu, "
+                   "\"pairs\": %lld, "
                    "\"ms_boxes\": %.4f, \"ms_sort\": %.4f, \"ms_build\": %.4f, "
                    "\"ms_traverse\": %.4f, \"ms_canon\": %.4f, \"leaf_size\": %d, "
                    "\"stack_depth\": %d, \"block_threads\": %d, \"morton_bits\": %d, "
                    "\"launches\": %llu, \"refs\": %lld, \"cells\": %d, \"graph\": %d}",
                    (long long)s->n, (long long)s->T, (long long)s->N, s->last_node_tests,
-                   s->last_leaf_tests, s->last_runs, (long long)s->n_out, s->ms_boxes, s->ms_sort,
+                   s->last_leaf_tests, s->last_runs, s->last_open, (long long)s->n_out, s->ms_boxes, s->ms_sort,
                    s->ms_build, s->ms_traverse, s->ms_canon, s->tune.leaf_size,
                    s->tune.stack_depth, s->tune.block_threads, s->tune.morton_bits,
                    s->last_launches, (long long)(s->dkind ? s->n_refs : s->N),
@@ -692,6 +694,7 @@ extern "C" SCD_API void scd_scene_destroy(scd_scene *s) {
   s->d_parent_int.release(st); s->d_parent_leaf.release(st); s->d_flags.release(st);
   s->d_first_last.release(st);
   s->d_starts.release(st); s->d_ends.release(st); s->d_rawval.release(st);
+  s->d_tilecnt.release(st);
   s->d_out.release(st);
   s->sort_sc.release(st);
   s->s_cell.release(st); s->d_first.release(st);

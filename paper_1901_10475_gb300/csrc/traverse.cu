@@ -8,12 +8,16 @@
 // Merged output without sorting the raw set: for one object pair the tick
 // intersections of their overlapping box pairs ("cells") are disjoint and
 // tile the horizon in order, so a merged interval is a maximal run of
-// consecutive overlapping cells.  A hit emits a "start" record when the cell
-// just before it (the one holding tick s-1) does not overlap, and an "end"
-// record when the cell just after it does not.  Both neighbours are found
-// by stepping one segment back or forward on the object whose segment
-// begins (ends) at the cell's boundary.  Sorting starts and ends separately
-// then pairs them up one to one.
+// consecutive overlapping cells.  Every hit looks at the cell just before it
+// (one segment back on whichever object's segment begins at the cell's first
+// tick) and the cell just after it (one segment forward on whichever ends at
+// its last tick).  A run's first cell emits a start record; if that cell is
+// also the run's last, the record is "closed" and carries the last tick,
+// else it is "open" and the run's last cell emits an end record.  After the
+// starts and the ends are sorted by (i, j, tick), the k-th open start pairs
+// with the k-th end.  The last tick is packed below the start's key when
+// 2 (object bits + tick bits) <= 64 and an all-ones tick field cannot be a
+// tick (the open tag), else it travels as a 32-bit sort value.
 #include <algorithm>
 
 #include "scd_internal.cuh"
@@ -34,8 +38,10 @@ struct TravArgs {
   int T;
   int raw;
   int obj_bits, t_bits;
+  int packed;                 // run starts carry their last tick in the low t_bits
+  uint32_t open_tag;          // last tick of an open run start
   unsigned long long *starts, *ends;
-  uint32_t *rawval;
+  uint32_t *rawval;           // raw cells' (or unpacked run starts') last tick
   unsigned long long cap;
   DevCounters *ctr;
   // static decomposition (kind SCD_DECOMP_NONE: one tree, root 0)
@@ -149,7 +155,8 @@ struct Query {
 // Is (q, b) the first / last cell of its run?  Both need the neighbouring
 // cell: one segment back (forward) on whichever box starts (ends) there.
 __device__ __forceinline__ void run_ends(const TravArgs &a, const Query &q, float4 bl, float4 bh,
-                                         uint32_t bu, int s, int e, bool &start, bool &end) {
+                                         uint32_t bu, int s, int e, int T, bool &start,
+                                         bool &end) {
   int qt0 = (int)q.lo.w, qt1 = (int)q.hi.w, bt0 = (int)bl.w, bt1 = (int)bh.w;
   if (start && s > 0) {
     float4 ql = q.lo, qh = q.hi, cl = bl, ch = bh;
@@ -157,7 +164,7 @@ __device__ __forceinline__ void run_ends(const TravArgs &a, const Query &q, floa
     if (bt0 == s) { cl = __ldg(a.lo + bu - 1); ch = __ldg(a.hi + bu - 1); }
     start = !box_overlap(ql, qh, cl, ch);
   }
-  if (end && e < a.T) {
+  if (end && e < T) {
     float4 ql = q.lo, qh = q.hi, cl = bl, ch = bh;
     if (qt1 == e) { ql = __ldg(a.lo + q.uid + 1); qh = __ldg(a.hi + q.uid + 1); }
     if (bt1 == e) { cl = __ldg(a.lo + bu + 1); ch = __ldg(a.hi + bu + 1); }
@@ -191,6 +198,14 @@ __device__ __forceinline__ unsigned long long pair_key(const TravArgs &a, uint32
   return (i << (a.obj_bits + a.t_bits)) | (j << a.t_bits);
 }
 
+// A start record: (i, j, first tick), with the run's last tick (or the open
+// tag) packed below it; `last` is also the sort value when unpacked.
+__device__ __forceinline__ unsigned long long start_key(const TravArgs &a, unsigned long long pk,
+                                                        int s, uint32_t last) {
+  unsigned long long key = pk | (unsigned long long)s;
+  return a.packed ? (key << a.t_bits) | (unsigned long long)last : key;
+}
+
 // ---------------------------------------------------------------------------
 // One thread per box, for leaves of several boxes.
 // ---------------------------------------------------------------------------
@@ -211,10 +226,11 @@ __device__ __forceinline__ void on_candidate(const TravArgs &a, const Query &q, 
     return;
   }
   bool start = true, end = true;
-  run_ends(a, q, bl, bh, bu, s, e, start, end);
-  em.put(a.starts, nullptr, &a.ctr->n_starts, &a.ctr->v_starts, a.cap, start,
-         pk | (unsigned long long)s, 0u);
-  em.put(a.ends, nullptr, &a.ctr->n_ends, &a.ctr->v_ends, a.cap, end,
+  run_ends(a, q, bl, bh, bu, s, e, a.objT ? __ldg(a.objT + q.obj) : a.T, start, end);
+  const uint32_t last = end ? (uint32_t)e : a.open_tag;
+  em.put(a.starts, a.packed ? nullptr : a.rawval, &a.ctr->n_starts, &a.ctr->v_starts, a.cap,
+         start, start_key(a, pk, s, last), last);
+  em.put(a.ends, nullptr, &a.ctr->n_ends, &a.ctr->v_ends, a.cap, end && !start,
          pk | (unsigned long long)e, 0u);
 }
 
@@ -338,9 +354,11 @@ __device__ __forceinline__ void drain_hits(const TravArgs &a, const uint2 *buf, 
     if (valid)
       run_ends_sorted(a, ql, qh, __ldg(a.nb + h.x), bl, bh, __ldg(a.nb + h.y), s, e,
                       a.objT ? __ldg(a.objT + qo) : a.T, start, end);
-    chunk_put(we.s, a.starts, nullptr, &a.ctr->n_starts, a.cap, start,
-              pk | (unsigned long long)s, 0u);
-    chunk_put(we.e, a.ends, nullptr, &a.ctr->n_ends, a.cap, end, pk | (unsigned long long)e, 0u);
+    const uint32_t last = end ? (uint32_t)e : a.open_tag;
+    chunk_put(we.s, a.starts, a.packed ? nullptr : a.rawval, &a.ctr->n_starts, a.cap, start,
+              start_key(a, pk, s, last), last);
+    chunk_put(we.e, a.ends, nullptr, &a.ctr->n_ends, a.cap, end && !start,
+              pk | (unsigned long long)e, 0u);
   }
 }
 
@@ -401,8 +419,8 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
     bool hl = false, hr = false;
     int32_t cl = 0, cr = 0;
     if (active) {
-      const uint4 *np = reinterpret_cast<const uint4 *>(a.qbox + 2 * (int64_t)node);
-      uint4 bl = __ldg(np), br = __ldg(np + 1);
+      uint4 bl, br;
+      ldg_qbox_pair(a.qbox + 2 * (int64_t)node, bl, br);
       uint2 lk = __ldg(a.qlink + node);
       nt += 2;
       uint32_t g = lk.x & kQIndex;
@@ -488,6 +506,8 @@ int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_b
   a.raw = raw_mode;
   a.obj_bits = obj_bits;
   a.t_bits = t_bits;
+  a.packed = !raw_mode && runs_packed(obj_bits, t_bits, s->T);
+  a.open_tag = open_tag(a.packed, t_bits);
   a.starts = s->d_starts.p;
   a.ends = s->d_ends.p;
   a.rawval = s->d_rawval.p;
@@ -503,6 +523,8 @@ int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_b
   a.objT = s->n_scenes > 0 ? s->d_objT.p : nullptr;
   if (a.dkind != SCD_DECOMP_NONE) a.N = s->n_refs;  // one query per reference
   if (a.L == 1) {
+    // the node pairs are read with 32-byte loads
+    if (reinterpret_cast<uintptr_t>(a.qbox) & 31) return SCD_ERR_INTERNAL;
     // persistent: as many blocks as fit on the GPU at once
     static int sms = 0;
     if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
@@ -538,56 +560,183 @@ int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_b
 }
 
 // ---------------------------------------------------------------------------
-// Step A9: sort starts and ends (or the raw cells) and pair them up.  Holes
-// sort last, so the first n slots of each sorted array are the n records.
+// Step A9: sort the run starts (or the raw cells) and the run ends by
+// (i, j, tick), then unpack the starts; the k-th open start takes the k-th
+// end.  Holes sort last, so the first n sorted slots are the n records.
 // ---------------------------------------------------------------------------
-__global__ void k_zip(const unsigned long long *__restrict__ starts,
-                      const unsigned long long *__restrict__ ends, const uint32_t *__restrict__ rawv,
-                      int64_t n, const unsigned long long *__restrict__ d_n, int ob, int tb,
-                      scd_pair *__restrict__ out, DevCounters *ctr) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (d_n && (unsigned long long)k >= *d_n) return;  // count known on the device only
-  if (k >= n) return;
-  unsigned long long ks = starts[k];
-  unsigned long long tmask = (1ull << tb) - 1ull, omask = (1ull << ob) - 1ull;
-  scd_pair r;
-  r.i = (uint32_t)(ks >> (ob + tb));
-  r.j = (uint32_t)((ks >> tb) & omask);
-  r.tlo = (int32_t)(ks & tmask);
-  if (rawv) {
-    r.thi = (int32_t)rawv[k];
-  } else {
-    unsigned long long ke = ends[k];
-    r.thi = (int32_t)(ke & tmask);
-    if ((ke >> tb) != (ks >> tb) || r.thi < r.tlo) atomicOr(&ctr->trav_flags, ERR_ZIP);
+constexpr int kUpThreads = 256, kUpItems = 8, kUpTile = kUpThreads * kUpItems;
+
+struct UnpackArgs {
+  const unsigned long long *starts;  // sorted starts (or raw cells)
+  const uint32_t *lastv;             // their last ticks when not packed
+  const unsigned long long *ends;    // sorted ends of the open runs
+  int64_t n;                         // starts to unpack (a capacity when d_n is set)
+  const unsigned long long *d_n;     // the count, when known on the device only
+  unsigned long long n_ends;         // ends (a capacity when d_ne is set)
+  const unsigned long long *d_ne;
+  int ob, tb;
+  int packed, raw;
+  uint32_t open_tag;
+  uint32_t *bcnt;                    // per tile: open starts, then their exclusive prefix
+  const uint32_t *open_total;
+  scd_pair *out;
+  DevCounters *ctr;
+};
+
+__device__ __forceinline__ int64_t unpack_count(const UnpackArgs &a) {
+  return a.d_n && *a.d_n < (unsigned long long)a.n ? (int64_t)*a.d_n : a.n;
+}
+
+__device__ __forceinline__ uint32_t last_of(const UnpackArgs &a, unsigned long long key,
+                                            int64_t r) {
+  return a.packed ? (uint32_t)(key & ((1ull << a.tb) - 1ull)) : __ldg(a.lastv + r);
+}
+
+// Tile items are warp-striped: item k of thread t is tile item k * 256 + t,
+// so every load and store of a warp is contiguous.
+
+// open starts per tile
+__global__ void __launch_bounds__(kUpThreads) k_open_count(UnpackArgs a) {
+  const int64_t n = unpack_count(a);
+  const int64_t base = (int64_t)blockIdx.x * kUpTile + threadIdx.x;
+  uint32_t c = 0;
+#pragma unroll
+  for (int k = 0; k < kUpItems; ++k) {
+    int64_t r = base + (int64_t)k * kUpThreads;
+    if (r < n) c += last_of(a, __ldg(a.starts + r), r) == a.open_tag;
   }
-  out[k] = r;
+  __shared__ uint32_t ws[kUpThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int q = 0; q < kUpThreads / 32; ++q) t += ws[q];
+    a.bcnt[blockIdx.x] = t;
+  }
+}
+
+static_assert(kUpItems * (kUpThreads / 32) == 64, "the tile prefix takes two counts per lane");
+
+__global__ void __launch_bounds__(kUpThreads) k_unpack(UnpackArgs a) {
+  constexpr int kWarps = kUpThreads / 32;
+  const int64_t n = unpack_count(a);
+  const int64_t base = (int64_t)blockIdx.x * kUpTile + threadIdx.x;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned long long tmask = (1ull << a.tb) - 1ull, omask = (1ull << a.ob) - 1ull;
+  unsigned long long key[kUpItems];
+  uint32_t last[kUpItems];
+  unsigned open[kUpItems];  // the warp's open-start mask per item
+  // opens per (item, warp), then their exclusive prefix in tile order
+  __shared__ uint32_t pre[kUpItems][kWarps];
+#pragma unroll
+  for (int k = 0; k < kUpItems; ++k) {
+    int64_t r = base + (int64_t)k * kUpThreads;
+    key[k] = r < n ? __ldg(a.starts + r) : 0ull;
+    last[k] = r < n ? (a.raw ? __ldg(a.lastv + r) : last_of(a, key[k], r)) : 0u;
+    open[k] = __ballot_sync(0xffffffffu, !a.raw && r < n && last[k] == a.open_tag);
+    if (lane == 0) pre[k][w] = __popc(open[k]);
+  }
+  __syncthreads();
+  if (w == 0) {
+    // kUpItems * kWarps = 64 counts, two per lane, scanned in (item, warp) order
+    uint32_t c0 = (&pre[0][0])[2 * lane], c1 = (&pre[0][0])[2 * lane + 1];
+    uint32_t x = c0 + c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    uint32_t b = (a.raw ? 0u : a.bcnt[blockIdx.x]) + x - c0 - c1;
+    (&pre[0][0])[2 * lane] = b;
+    (&pre[0][0])[2 * lane + 1] = b + c0;
+  }
+  __syncthreads();
+  const unsigned long long n_ends = a.d_ne && *a.d_ne < a.n_ends ? *a.d_ne : a.n_ends;
+  if (!a.raw && blockIdx.x == 0 && threadIdx.x == 0 && *a.open_total != n_ends)
+    atomicOr(&a.ctr->trav_flags, ERR_ZIP);
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < kUpItems; ++k) {
+    int64_t r = base + (int64_t)k * kUpThreads;
+    if (r < n) {
+      unsigned long long kk = a.packed ? key[k] >> a.tb : key[k];
+      scd_pair p;
+      p.i = (uint32_t)(kk >> (a.ob + a.tb));
+      p.j = (uint32_t)((kk >> a.tb) & omask);
+      p.tlo = (int32_t)(kk & tmask);
+      p.thi = (int32_t)last[k];
+      if (open[k] & (1u << lane)) {
+        unsigned long long rank = pre[k][w] + __popc(open[k] & lt);
+        if (rank < n_ends) {
+          unsigned long long ek = __ldg(a.ends + rank);
+          p.thi = (int32_t)(ek & tmask);
+          bad |= (ek >> a.tb) != (kk >> a.tb) || p.thi <= p.tlo;
+        } else {
+          bad = true;
+        }
+      }
+      a.out[r] = p;
+    }
+  }
+  if (bad) atomicOr(&a.ctr->trav_flags, ERR_ZIP);
+}
+
+static UnpackArgs unpack_args(scd_scene *s, int raw_mode, int obj_bits, int t_bits) {
+  UnpackArgs a;
+  a.starts = s->d_starts.p;
+  a.lastv = s->d_rawval.p;
+  a.ends = s->d_ends.p;
+  a.d_n = nullptr;
+  a.d_ne = nullptr;
+  a.ob = obj_bits;
+  a.tb = t_bits;
+  a.raw = raw_mode;
+  a.packed = !raw_mode && runs_packed(obj_bits, t_bits, s->T);
+  a.open_tag = open_tag(a.packed, t_bits);
+  a.out = s->d_out.p;
+  a.ctr = s->d_ctr.p;
+  return a;
+}
+
+// k_open_count, the prefix over the tiles, k_unpack
+static int unpack(scd_scene *s, UnpackArgs a, cudaStream_t st) {
+  int64_t tiles = (a.n + kUpTile - 1) / kUpTile;
+  if (tiles == 0) return SCD_OK;
+  if (!a.raw) {
+    if (!s->d_tilecnt.ensure((size_t)tiles + 1, st)) return SCD_ERR_OOM;
+    a.bcnt = s->d_tilecnt.p;
+    a.open_total = s->d_tilecnt.p + tiles;
+    k_open_count<<<(unsigned)tiles, kUpThreads, 0, st>>>(a);
+    scan_u32_exclusive(a.bcnt, tiles, s->d_tilecnt.p + tiles, st);
+    note_launch(2);
+  }
+  k_unpack<<<(unsigned)tiles, kUpThreads, 0, st>>>(a);
+  note_launch();
+  return SCD_OK;
 }
 
 int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits) {
   cudaStream_t st = s->stream;
   // slots to sort (records plus holes) and records to keep
   int64_t ns = raw_mode ? (int64_t)s->h_ctr.n_raw : (int64_t)s->h_ctr.n_starts;
-  int64_t ne = (int64_t)s->h_ctr.n_ends;
   int64_t n = raw_mode ? (int64_t)s->h_ctr.v_raw : (int64_t)s->h_ctr.v_starts;
-  int bits = 2 * obj_bits + t_bits;
+  UnpackArgs a = unpack_args(s, raw_mode, obj_bits, t_bits);
+  const int lo = a.packed ? t_bits : 0, bits = 2 * obj_bits + t_bits;
   if (!s->d_out.ensure(n > 0 ? n : 1, st)) return SCD_ERR_OOM;
-  int rc;
-  if (raw_mode) {
-    rc = radix_sort_u64(s->d_starts.p, s->d_rawval.p, ns, bits, s->sort_sc, st);
-    if (rc) return rc;
-  } else {
-    rc = radix_sort_u64(s->d_starts.p, nullptr, ns, bits, s->sort_sc, st);
-    if (rc) return rc;
-    rc = radix_sort_u64(s->d_ends.p, nullptr, ne, bits, s->sort_sc, st);
+  a.out = s->d_out.p;
+  int rc = radix_sort_u64(s->d_starts.p, a.packed ? nullptr : s->d_rawval.p, ns, lo, bits + lo,
+                          s->sort_sc, st);
+  if (rc) return rc;
+  if (!raw_mode && s->h_ctr.v_ends > 0) {
+    rc = radix_sort_u64(s->d_ends.p, nullptr, (int64_t)s->h_ctr.n_ends, bits, s->sort_sc, st);
     if (rc) return rc;
   }
-  if (n > 0)
-    k_zip<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->d_starts.p, s->d_ends.p,
-                                                       raw_mode ? s->d_rawval.p : nullptr, n,
-                                                       nullptr, obj_bits, t_bits, s->d_out.p,
-                                                       s->d_ctr.p);
-  if (n > 0) note_launch();
+  a.n = n;
+  a.n_ends = raw_mode ? 0 : s->h_ctr.v_ends;
+  if (int rc2 = unpack(s, a, st)) return rc2;
   s->n_out = n;
   return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
 }
@@ -595,17 +744,20 @@ int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits) {
 int canonicalize_dev(scd_scene *s, int obj_bits, int t_bits) {
   cudaStream_t st = s->stream;
   const int64_t cap = s->pair_cap;
-  int bits = 2 * obj_bits + t_bits;
   if (!s->d_out.ensure(cap, st)) return SCD_ERR_OOM;
+  UnpackArgs a = unpack_args(s, 0, obj_bits, t_bits);
+  const int lo = a.packed ? t_bits : 0, bits = 2 * obj_bits + t_bits;
   DevCounters *c = s->d_ctr.p;
-  int rc = radix_sort_u64_dev(s->d_starts.p, nullptr, cap, &c->n_starts, bits, s->sort_sc, st);
+  int rc = radix_sort_u64_dev(s->d_starts.p, a.packed ? nullptr : s->d_rawval.p, cap,
+                              &c->n_starts, lo, bits + lo, s->sort_sc, st);
   if (rc) return rc;
-  rc = radix_sort_u64_dev(s->d_ends.p, nullptr, cap, &c->n_ends, bits, s->sort_sc, st);
+  rc = radix_sort_u64_dev(s->d_ends.p, nullptr, cap, &c->n_ends, 0, bits, s->sort_sc, st);
   if (rc) return rc;
-  k_zip<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(s->d_starts.p, s->d_ends.p, nullptr, cap,
-                                                       &c->v_starts, obj_bits, t_bits, s->d_out.p,
-                                                       c);
-  note_launch();
+  a.n = cap;
+  a.d_n = &c->v_starts;
+  a.n_ends = (unsigned long long)cap;
+  a.d_ne = &c->v_ends;
+  if (int rc2 = unpack(s, a, st)) return rc2;
   return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
 }
 

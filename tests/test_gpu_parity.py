@@ -136,6 +136,22 @@ def test_mixture_variable_steps_bit_exact(scd, mode):
     assert len(got) > 100
 
 
+@pytest.mark.parametrize("leaf", [1, 4])
+def test_runs_too_wide_to_pack(scd, leaf):
+    """1 ms ticks over 6000 s (23 tick bits) and 600 objects (10 bits): a run
+    record's key and last tick no longer fit one 64-bit word together, so the
+    last tick travels as a sort value."""
+    els = P.catalog_mixture(n=600, seed=34, radius_km=25.0)
+    pol = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=100.0)
+    sc = scd.Scene(els, 6000.0, 0.001, pol, tuning=dict(leaf_size=leaf)).build_boxes()
+    got = sc.find_pairs()
+    lo, hi, obj = _host_boxes(sc)
+    want = O.canonicalize(O.raw_cells_sweep(lo, hi, obj))
+    assert len(want) > 50 and int(want["thi"].max()) >= 1 << 22
+    assert _same(got, want), (len(got), len(want))
+    sc.close()
+
+
 def test_band_table_steps_bit_exact(scd):
     els = P.catalog_mixture(n=500, seed=32, radius_km=25.0)
     edges, fr = P.band_table_config3()
