@@ -91,13 +91,13 @@ __global__ void k_karras(const K *__restrict__ keys, int64_t M, TravNode *__rest
   } while (t > 1);
   int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
   int64_t first = i < j ? i : j, last = i < j ? j : i;
-  TravNode nd;
-  nd.left = first == gamma ? (int32_t)gamma | kLeafBit : (int32_t)gamma;
-  nd.right = last == gamma + 1 ? (int32_t)(gamma + 1) | kLeafBit : (int32_t)(gamma + 1);
-  nd.last_l = (int32_t)gamma;
-  nd.last_r = (int32_t)last;
-  nd.lo_l = nd.hi_l = nd.lo_r = nd.hi_r = make_float4(0.f, 0.f, 0.f, 0.f);
-  nodes[i] = nd;
+  // the links only: the child boxes are written by the refit
+  int4 lk;
+  lk.x = first == gamma ? (int32_t)gamma | kLeafBit : (int32_t)gamma;
+  lk.y = last == gamma + 1 ? (int32_t)(gamma + 1) | kLeafBit : (int32_t)(gamma + 1);
+  lk.z = (int32_t)gamma;
+  lk.w = (int32_t)last;
+  reinterpret_cast<int4 *>(nodes + i)[4] = lk;
   if (first == gamma) parent_leaf[gamma] = (int32_t)i; else parent_int[gamma] = (int32_t)i;
   if (last == gamma + 1) parent_leaf[gamma + 1] = (int32_t)i; else parent_int[gamma + 1] = (int32_t)i;
   if (i == 0) parent_int[0] = -1;
@@ -114,8 +114,9 @@ __device__ __forceinline__ float4 f4max(float4 a, float4 b) {
 
 // Bottom-up union.  The second thread to reach a node (atomic arrival count)
 // reads both children and goes on; the first one stops.  Nobody waits.
+// With one box per leaf the sorted boxes are the leaf boxes (leaflo = slo).
 __global__ void k_refit(const float4 *__restrict__ slo, const float4 *__restrict__ shi, int64_t N,
-                        int L, int64_t M, float4 *__restrict__ leaflo, float4 *__restrict__ leafhi,
+                        int L, int64_t M, float4 *leaflo, float4 *leafhi,
                         TravNode *__restrict__ nodes, float4 *__restrict__ nlo,
                         float4 *__restrict__ nhi, const int32_t *__restrict__ parent_int,
                         const int32_t *__restrict__ parent_leaf, uint32_t *__restrict__ flags,
@@ -124,50 +125,53 @@ __global__ void k_refit(const float4 *__restrict__ slo, const float4 *__restrict
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= M) return;
   const QFrame fr = scene_frame(ctr, T);
-  int64_t b0 = c * L, b1 = b0 + L < N ? b0 + L : N;
-  float4 lo = slo[b0], hi = shi[b0];
-  for (int64_t b = b0 + 1; b < b1; ++b) {
-    lo = f4min(lo, slo[b]);
-    hi = f4max(hi, shi[b]);
+  if (L > 1) {
+    int64_t b0 = c * L, b1 = b0 + L < N ? b0 + L : N;
+    float4 lo = slo[b0], hi = shi[b0];
+    for (int64_t b = b0 + 1; b < b1; ++b) {
+      lo = f4min(lo, slo[b]);
+      hi = f4max(hi, shi[b]);
+    }
+    leaflo[c] = lo;
+    leafhi[c] = hi;
   }
-  leaflo[c] = lo;
-  leafhi[c] = hi;
   if (M == 1) return;
   int32_t p = parent_leaf[c];
   while (p >= 0) {
     __threadfence();
     if (atomicAdd(flags + p, 1u) == 0u) return;
     __threadfence();
-    TravNode nd = nodes[p];
+    // the links only (the boxes are what this pass writes)
+    const int4 lk = __ldcg(reinterpret_cast<const int4 *>(nodes + p) + 4);
     float4 llo, lhi, rlo, rhi;
-    if (nd.left & kLeafBit) {
-      int32_t q = nd.left & ~kLeafBit;
+    if (lk.x & kLeafBit) {
+      int32_t q = lk.x & ~kLeafBit;
       llo = __ldcg(leaflo + q);
       lhi = __ldcg(leafhi + q);
     } else {
-      llo = __ldcg(nlo + nd.left);
-      lhi = __ldcg(nhi + nd.left);
+      llo = __ldcg(nlo + lk.x);
+      lhi = __ldcg(nhi + lk.x);
     }
-    if (nd.right & kLeafBit) {
-      int32_t q = nd.right & ~kLeafBit;
+    if (lk.y & kLeafBit) {
+      int32_t q = lk.y & ~kLeafBit;
       rlo = __ldcg(leaflo + q);
       rhi = __ldcg(leafhi + q);
     } else {
-      rlo = __ldcg(nlo + nd.right);
-      rhi = __ldcg(nhi + nd.right);
+      rlo = __ldcg(nlo + lk.y);
+      rhi = __ldcg(nhi + lk.y);
     }
     if (qbox) {
       qbox[2 * p] = quantize_box(fr, llo, lhi);
       qbox[2 * p + 1] = quantize_box(fr, rlo, rhi);
-      uint32_t g = (uint32_t)nd.last_l;  // the split: left child gamma, right gamma + 1
-      uint32_t fl = ((nd.left & kLeafBit) ? kQLeftLeaf : 0u) | ((nd.right & kLeafBit) ? kQRightLeaf : 0u);
-      qlink[p] = make_uint2(g | fl, (uint32_t)nd.last_r);
+      uint32_t g = (uint32_t)lk.z;  // the split: left child gamma, right gamma + 1
+      uint32_t fl = ((lk.x & kLeafBit) ? kQLeftLeaf : 0u) | ((lk.y & kLeafBit) ? kQRightLeaf : 0u);
+      qlink[p] = make_uint2(g | fl, (uint32_t)lk.w);
     } else {
-      nd.lo_l = llo;
-      nd.hi_l = lhi;
-      nd.lo_r = rlo;
-      nd.hi_r = rhi;
-      nodes[p] = nd;
+      float4 *np = reinterpret_cast<float4 *>(nodes + p);
+      np[0] = llo;
+      np[1] = lhi;
+      np[2] = rlo;
+      np[3] = rhi;
     }
     __stcg(nlo + p, f4min(llo, rlo));
     __stcg(nhi + p, f4max(lhi, rhi));
@@ -182,7 +186,7 @@ int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, i
   int L = s->tune.leaf_size;
   M = (Nq + L - 1) / L;
   if (!s->s_lo.ensure(Nq, st) || !s->s_hi.ensure(Nq, st) || !s->s_obj.ensure(Nq, st) ||
-      !s->d_leaflo.ensure(M, st) || !s->d_leafhi.ensure(M, st) ||
+      (L > 1 && (!s->d_leaflo.ensure(M, st) || !s->d_leafhi.ensure(M, st))) ||
       !s->d_nodes.ensure(M > 1 ? M - 1 : 1, st) || !s->d_nlo.ensure(M > 1 ? M - 1 : 1, st) ||
       !s->d_nhi.ensure(M > 1 ? M - 1 : 1, st) || !s->d_parent_int.ensure(M, st) ||
       !s->d_parent_leaf.ensure(M, st) || !s->d_flags.ensure(M, st))
@@ -213,7 +217,8 @@ int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, i
     note_launch();
   }
   k_refit<<<(unsigned)((M + bs - 1) / bs), bs, 0, st>>>(
-      s->s_lo.p, s->s_hi.p, Nq, L, M, s->d_leaflo.p, s->d_leafhi.p, s->d_nodes.p, s->d_nlo.p,
+      s->s_lo.p, s->s_hi.p, Nq, L, M, L > 1 ? s->d_leaflo.p : s->s_lo.p,
+      L > 1 ? s->d_leafhi.p : s->s_hi.p, s->d_nodes.p, s->d_nlo.p,
       s->d_nhi.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p,
       compact ? s->d_qbox.p : nullptr, compact ? s->d_qlink.p : nullptr, s->d_ctr.p, s->T);
   return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;

@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
   const QFrame fr = scene_frame(a.ctr, a.T);
   QBox q = {0u, 0u, 0u, 0u};  // the query box, quantised outward like the nodes
   int32_t stack[kDepth];
-  int sp = 0;
+  int sp = 0, sb = 0;  // the lane's deferred subtrees are stack[sb .. sp)
   int32_t node = 0;
   for (;;) {
     // lanes without a query take the next ones from the warp's pool
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
           q = quantize_box(fr, __ldg(a.slo + p), __ldg(a.shi + p));
           // the query starts at the root of its own cell's subtree
           node = a.dkind == SCD_DECOMP_NONE ? 0 : __ldg(a.cellroot + __ldg(a.scell + p));
-          sp = 0;
+          sp = sb = 0;
           if (node < 0) p = -1;  // alone in its cell: nothing to find
         } else {
           exhausted = true;
@@ -411,6 +411,40 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
         q_end = nb + kQueryChunk;
       } else {
         q_next += cnt;
+      }
+    }
+    // Once the queue is empty, a lane without a query takes the oldest
+    // deferred subtree (the largest) of a lane that has one, with its query:
+    // one long query then spreads over the warp instead of holding it.
+    if (__ballot_sync(0xffffffffu, exhausted)) {
+      const unsigned idle = __ballot_sync(0xffffffffu, p < 0);
+      const unsigned donors = __ballot_sync(0xffffffffu, p >= 0 && sp > sb);
+      const int moves = min(__popc(idle), __popc(donors));
+      if (moves > 0) {
+        const bool is_idle = (idle >> lane) & 1u, is_donor = (donors >> lane) & 1u;
+        const int ri = __popc(idle & lt), rd = __popc(donors & lt);
+        const int32_t give = is_donor ? stack[sb] : 0;
+        // the receiver of rank k takes from the donor of rank k
+        int src = lane;
+        if (is_idle && ri < moves) {
+          unsigned m = donors;
+          for (int k = 0; k < ri; ++k) m &= m - 1u;
+          src = __ffs(m) - 1;
+        }
+        const int32_t gnode = __shfl_sync(0xffffffffu, give, src);
+        const uint32_t gp = __shfl_sync(0xffffffffu, (uint32_t)p, src);
+        QBox gq;
+        gq.lo_xy = __shfl_sync(0xffffffffu, q.lo_xy, src);
+        gq.lo_zt = __shfl_sync(0xffffffffu, q.lo_zt, src);
+        gq.hi_xy = __shfl_sync(0xffffffffu, q.hi_xy, src);
+        gq.hi_zt = __shfl_sync(0xffffffffu, q.hi_zt, src);
+        if (is_idle && ri < moves) {
+          p = (int64_t)gp;
+          q = gq;
+          node = gnode;
+          sp = sb = 0;
+        }
+        if (is_donor && rd < moves) ++sb;
       }
     }
     bool active = p >= 0;
@@ -448,10 +482,10 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
         node = cl;
       } else if (gr) {
         node = cr;
-      } else if (sp > 0) {
+      } else if (sp > sb) {
         node = stack[--sp];
       } else {
-        p = -1;  // query done
+        p = -1;  // query (or the subtree taken from another lane) done
       }
     }
     // append this step's hits to the warp buffer
