@@ -7,6 +7,8 @@
 // (3) every block ranks its tile stably in shared memory (warp match + per
 // warp counters) and writes each digit's run to its global offset.  No block
 // ever waits on another block.
+#include <algorithm>
+
 #include "scd_internal.cuh"
 
 namespace scd {
@@ -115,96 +117,191 @@ __device__ __forceinline__ uint32_t digit_scan_excl(uint32_t v, uint32_t *buf) {
   return x + add - v;
 }
 
+// --- bulk copies (TMA) of whole tiles into shared memory ------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// one contiguous global -> shared copy completing on `bar`; both addresses
+// 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// Wait for the phase with the given parity to complete; gives up after a
+// bounded number of polls (about a second) and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const uint32_t a = smem_addr(bar);
+  for (int it = 0; it < (1 << 23); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (it > 64) __nanosleep(64);
+  }
+  return false;
+}
+
+// Scatter pass, persistent: block b handles tiles b, b + G, b + 2G, ... .
+// Every full tile's keys (and values) arrive by bulk copy into one of two
+// shared buffers while the tile before is ranked and written, so a copy is
+// in flight during every block's compute; the buffer of the tile at hand
+// then serves as the staging area of its scatter.  A last partial tile is
+// read with plain loads.  Items of a tile are warp-striped: warp w holds
+// tile items [w*32*I, (w+1)*32*I), item k of lane l at w*32*I + k*32 + l,
+// so (k, lane) order is input order and ranks are stable.
 template <class K, bool kVals>
-__global__ void __launch_bounds__(kRsThreads) k_rs_downsweep(
+__global__ void __launch_bounds__(kRsThreads, 4) k_rs_downsweep(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t n, const unsigned long long *__restrict__ d_n, int shift,
-    const uint32_t *__restrict__ counts, const uint32_t *__restrict__ totals, int64_t nblk) {
+    const uint32_t *__restrict__ counts, const uint32_t *__restrict__ totals, int64_t nblk,
+    unsigned int *err) {
   n = sort_count(n, d_n);
-  extern __shared__ __align__(16) unsigned char smem[];
-  K *skeys = (K *)smem;
-  uint32_t *svals = (uint32_t *)(smem + sizeof(K) * kRsTile);
+  const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
+  extern __shared__ __align__(128) unsigned char smem[];
+  K *kbuf0 = (K *)smem;
+  K *kbuf1 = kbuf0 + kRsTile;
+  uint32_t *vbuf0 = (uint32_t *)(smem + 2 * sizeof(K) * kRsTile);
+  uint32_t *vbuf1 = vbuf0 + kRsTile;
+  __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t wcnt[kRsWarps][256];  // per warp, per digit
   __shared__ uint32_t scanbuf[256];
+  __shared__ uint32_t gdig[256];    // first global position of each digit
   __shared__ uint32_t dstart[256];  // first tile position of each digit
-  __shared__ uint32_t gbase[256];   // global position of the digit's first item
+  __shared__ uint32_t gbase[256];   // global position of the tile's first item of each digit
 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&wcnt[0][0])[i] = 0;
+  const int d = threadIdx.x;  // one thread per digit in the digit phases
+  const uint32_t tile_bytes = (uint32_t)(sizeof(K) * kRsTile);
+  auto full_tile = [&](int64_t t) { return t < ntiles && (t + 1) * kRsTile <= n; };
+  auto issue = [&](int64_t t, int b) {  // thread 0 only
+    if (!full_tile(t)) return;
+    mbar_expect_tx(&bar[b], tile_bytes + (kVals ? 4u * kRsTile : 0u));
+    bulk_load(b ? kbuf1 : kbuf0, kin + t * kRsTile, tile_bytes, &bar[b]);
+    if (kVals) bulk_load(b ? vbuf1 : vbuf0, vin + t * kRsTile, 4u * kRsTile, &bar[b]);
+  };
 
-  // (a) global base of each digit for this block
-  {
-    const int d = threadIdx.x;
-    uint32_t excl = digit_scan_excl(totals[d], scanbuf);
-    gbase[d] = excl + counts[(int64_t)d * nblk + blockIdx.x];
-  }
-
-  // (b) load the tile warp-striped and rank every item inside its warp:
-  // warp w holds tile items [w*32*I, (w+1)*32*I), item k of lane l at
-  // w*32*I + k*32 + l, so (k, lane) order is input order and ranks are stable
-  const int64_t base = (int64_t)blockIdx.x * kRsTile;
-  const int64_t seg = base + (int64_t)w * 32 * kRsItems;
-  K key[kRsItems];
-  uint32_t val[kRsItems];
-  uint32_t rnk[kRsItems];
-  // all loads first: the ranking below synchronises the warp between items,
-  // which would otherwise hold each load back until the previous item
-#pragma unroll
-  for (int k = 0; k < kRsItems; ++k) {
-    int64_t idx = seg + k * 32 + lane;
-    bool valid = idx < n;
-    key[k] = valid ? kin[idx] : (K)0;
-    if (kVals) val[k] = valid ? vin[idx] : 0u;
-  }
-#pragma unroll
-  for (int k = 0; k < kRsItems; ++k) {
-    bool valid = seg + k * 32 + lane < n;
-    uint32_t d = valid ? digit_of(key[k], shift) : 256u;
-    unsigned peers = __match_any_sync(0xffffffffu, d);
-    uint32_t before = valid ? wcnt[w][d] : 0u;
-    rnk[k] = before + __popc(peers & lt);
-    __syncwarp();
-    if (valid && lane == __ffs(peers) - 1) wcnt[w][d] = before + __popc(peers);
-    __syncwarp();
+  gdig[d] = digit_scan_excl(totals[d], scanbuf);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-
-  // (c) per digit: exclusive prefix over the warps, then over the digits
-  {
-    const int d = threadIdx.x;
-    uint32_t run = 0;
-#pragma unroll
-    for (int q = 0; q < kRsWarps; ++q) {
-      uint32_t c = wcnt[q][d];
-      wcnt[q][d] = run;
-      run += c;
+  if (threadIdx.x == 0) {
+    issue(blockIdx.x, 0);
+    issue((int64_t)blockIdx.x + gridDim.x, 1);
+  }
+  uint32_t parity0 = 0, parity1 = 0;
+  int b = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, b ^= 1) {
+    const int64_t base = tile * kRsTile;
+    const bool full = full_tile(tile);
+    K *kb = b ? kbuf1 : kbuf0;
+    uint32_t *vb = b ? vbuf1 : vbuf0;
+    for (int i = lane; i < 256; i += 32) wcnt[w][i] = 0;
+    gbase[d] = gdig[d] + counts[(int64_t)d * nblk + tile];
+    bool ok = true;
+    if (full) {
+      ok = mbar_wait(&bar[b], b ? parity1 : parity0);
+      if (b) parity1 ^= 1u; else parity0 ^= 1u;
     }
-    dstart[d] = digit_scan_excl(run, scanbuf);
-  }
-  __syncthreads();
-
-  // (d) scatter into shared memory at the tile-local rank
-#pragma unroll
-  for (int k = 0; k < kRsItems; ++k) {
-    int64_t idx = seg + k * 32 + lane;
-    if (idx < n) {
-      uint32_t d = digit_of(key[k], shift);
-      uint32_t r = dstart[d] + wcnt[w][d] + rnk[k];
-      skeys[r] = key[k];
-      if (kVals) svals[r] = val[k];
+    // the whole block decides together (a barrier; the counters above are
+    // zeroed and gbase written before it)
+    if (!__syncthreads_and(ok)) {
+      // give up: report, wait (bounded) for the other buffer's copy, leave
+      if (threadIdx.x == 0 && err) atomicOr(err, (unsigned)ERR_SORT);
+      if (full_tile(tile + gridDim.x)) mbar_wait(&bar[b ^ 1], b ? parity0 : parity1);
+      return;
     }
-  }
-  __syncthreads();
 
-  // (e) each digit's run goes to consecutive global positions
-  int64_t cnt = n - base < kRsTile ? n - base : kRsTile;
-  for (int r = threadIdx.x; r < cnt; r += kRsThreads) {
-    K kk = skeys[r];
-    uint32_t d = digit_of(kk, shift);
-    uint32_t pos = gbase[d] + (uint32_t)r - dstart[d];
-    kout[pos] = kk;
-    if (kVals) vout[pos] = svals[r];
+    // (b) rank every item inside its warp
+    const int seg = w * 32 * kRsItems;
+    K key[kRsItems];
+    uint32_t val[kRsItems];
+    uint32_t rnk[kRsItems];
+#pragma unroll
+    for (int k = 0; k < kRsItems; ++k) {
+      const int i = seg + k * 32 + lane;
+      if (full) {
+        key[k] = kb[i];
+        if (kVals) val[k] = vb[i];
+      } else {
+        const bool valid = base + i < n;
+        key[k] = valid ? kin[base + i] : (K)0;
+        if (kVals) val[k] = valid ? vin[base + i] : 0u;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kRsItems; ++k) {
+      const bool valid = base + seg + k * 32 + lane < n;
+      uint32_t dg = valid ? digit_of(key[k], shift) : 256u;
+      unsigned peers = __match_any_sync(0xffffffffu, dg);
+      uint32_t before = valid ? wcnt[w][dg] : 0u;
+      rnk[k] = before + __popc(peers & lt);
+      __syncwarp();
+      if (valid && lane == __ffs(peers) - 1) wcnt[w][dg] = before + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();  // every warp's counts are in; the tile buffer is free
+
+    // (c) per digit: exclusive prefix over the warps, then over the digits
+    {
+      uint32_t run = 0;
+#pragma unroll
+      for (int q = 0; q < kRsWarps; ++q) {
+        uint32_t c = wcnt[q][d];
+        wcnt[q][d] = run;
+        run += c;
+      }
+      dstart[d] = digit_scan_excl(run, scanbuf);
+    }
+    __syncthreads();
+
+    // (d) scatter into the tile buffer at the tile-local rank
+#pragma unroll
+    for (int k = 0; k < kRsItems; ++k) {
+      if (base + seg + k * 32 + lane < n) {
+        uint32_t dg = digit_of(key[k], shift);
+        uint32_t r = dstart[dg] + wcnt[w][dg] + rnk[k];
+        kb[r] = key[k];
+        if (kVals) vb[r] = val[k];
+      }
+    }
+    __syncthreads();
+
+    // (e) each digit's run goes to consecutive global positions
+    const int cnt = n - base < kRsTile ? (int)(n - base) : kRsTile;
+    for (int r = threadIdx.x; r < cnt; r += kRsThreads) {
+      K kk = kb[r];
+      uint32_t dg = digit_of(kk, shift);
+      uint32_t pos = gbase[dg] + (uint32_t)r - dstart[dg];
+      kout[pos] = kk;
+      if (kVals) vout[pos] = vb[r];
+    }
+    __syncthreads();  // the buffer is read out: the copy of the tile after next may land
+    if (threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(tile + 2 * (int64_t)gridDim.x, b);
+    }
   }
 }
 
@@ -213,6 +310,9 @@ static int rs_impl(K *keys, uint32_t *vals, int64_t n, const unsigned long long 
                    int bits, SortScratch &sc, cudaStream_t st) {
   if (n <= 1 || bits <= lo) return SCD_OK;
   if (n >= (1ll << 32) - 1) return SCD_ERR_CAPACITY;  // positions are 32-bit
+  // tiles are copied whole into shared memory: 16-byte aligned arrays
+  if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(vals)) & 15)
+    return SCD_ERR_INTERNAL;
   int64_t nblk = (n + kRsTile - 1) / kRsTile;
   if (!sc.keys_alt.ensure(sizeof(K) * (size_t)n, st)) return SCD_ERR_OOM;
   if (vals && !sc.vals_alt.ensure((size_t)n, st)) return SCD_ERR_OOM;
@@ -221,28 +321,39 @@ static int rs_impl(K *keys, uint32_t *vals, int64_t n, const unsigned long long 
   uint32_t *totals = sc.counts.p + 256 * nblk;
   K *ka = keys, *kb = (K *)sc.keys_alt.p;
   uint32_t *va = vals, *vb = sc.vals_alt.p;
-  size_t smem = sizeof(K) * kRsTile + (vals ? sizeof(uint32_t) * kRsTile : 0);
-  static bool attr_set[2][2] = {{false, false}, {false, false}};
+  // two tile buffers of keys (and values); persistent grid of the blocks
+  // that fit at once
+  size_t smem = 2 * (sizeof(K) * kRsTile + (vals ? sizeof(uint32_t) * kRsTile : 0));
+  static int grid_of[2][2] = {{0, 0}, {0, 0}};
   int ki = sizeof(K) == 8 ? 1 : 0, vi = vals ? 1 : 0;
-  if (!attr_set[ki][vi]) {
-    if (vals)
+  if (!grid_of[ki][vi]) {
+    int sms = 0, per_sm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (vals) {
       cudaFuncSetAttribute(k_rs_downsweep<K, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
-    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rs_downsweep<K, true>, kRsThreads,
+                                                    smem);
+    } else {
       cudaFuncSetAttribute(k_rs_downsweep<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
-    attr_set[ki][vi] = true;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rs_downsweep<K, false>,
+                                                    kRsThreads, smem);
+    }
+    grid_of[ki][vi] = std::max(1, sms) * std::max(1, per_sm);
   }
+  const unsigned grid = (unsigned)std::min<int64_t>(nblk, grid_of[ki][vi]);
   int passes = 0;
   for (int shift = lo; shift < bits; shift += 8, ++passes) {
     k_rs_upsweep<K><<<(unsigned)nblk, kRsThreads, 0, st>>>(ka, n, d_n, shift, counts, nblk);
     k_rs_scan<<<256, 1024, 0, st>>>(counts, nblk, totals);
     if (vals)
-      k_rs_downsweep<K, true><<<(unsigned)nblk, kRsThreads, smem, st>>>(
-          ka, va, kb, vb, n, d_n, shift, counts, totals, nblk);
+      k_rs_downsweep<K, true><<<grid, kRsThreads, smem, st>>>(ka, va, kb, vb, n, d_n, shift,
+                                                               counts, totals, nblk, sc.err);
     else
-      k_rs_downsweep<K, false><<<(unsigned)nblk, kRsThreads, smem, st>>>(
-          ka, nullptr, kb, nullptr, n, d_n, shift, counts, totals, nblk);
+      k_rs_downsweep<K, false><<<grid, kRsThreads, smem, st>>>(
+          ka, nullptr, kb, nullptr, n, d_n, shift, counts, totals, nblk, sc.err);
     note_launch(3);
     K *t = ka; ka = kb; kb = t;
     uint32_t *tv = va; va = vb; vb = tv;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <vector>
@@ -26,6 +27,7 @@ enum : uint32_t {
   ERR_STACK = 1u << 1,      // traversal stack overflow
   ERR_INVALID = 1u << 2,    // invalid element seen on the device
   ERR_ZIP = 1u << 3,        // open run starts and run ends did not pair up
+  ERR_SORT = 1u << 4,       // a sort's tile copy did not arrive in time
   ERR_TIMEOUT = 1u << 4,    // a bounded wait gave up
 };
 
@@ -63,6 +65,8 @@ struct DevCounters {
   unsigned int kepler_max_iter;
   unsigned long long n_boxes;      // seg_off[n]
   unsigned long long refs_total;   // references of the last decomposed build
+  unsigned int sort_flags;         // ERR_SORT (set by any sort since the box build)
+  unsigned int pad1;
 };
 
 // Traversal node: both children's boxes inline, child links and the
@@ -72,6 +76,9 @@ struct __align__(16) TravNode {
   int32_t left, right;  // child index; bit 31 set = leaf
   int32_t last_l, last_r;  // rightmost leaf index under each child
 };
+
+static_assert(sizeof(TravNode) == 80 && offsetof(TravNode, left) == 64,
+              "the links are the node's fifth 16-byte word");
 
 constexpr int32_t kLeafBit = (int32_t)0x80000000u;
 
@@ -244,6 +251,7 @@ struct SortScratch {
   DevBuf<unsigned char> keys_alt;
   DevBuf<uint32_t> vals_alt;
   DevBuf<uint32_t> counts;
+  unsigned int *err = nullptr;  // device word that receives ERR_SORT (may be null)
   void release(cudaStream_t st) {
     keys_alt.release(st);
     vals_alt.release(st);

@@ -179,6 +179,7 @@ extern "C" SCD_API int scd_scene_create(const scd_element *elems, int64_t n, dou
     scd_scene_destroy(s);
     return SCD_ERR_OOM;
   }
+  s->sort_sc.err = &s->d_ctr.p->sort_flags;
   cudaError_t e = cudaMemcpyAsync(s->d_el.p, elems, sizeof(scd_element) * (size_t)n,
                                   cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && !s->band_fracs.empty()) {
@@ -381,9 +382,10 @@ static int find_eager(scd_scene *s, const scd_decomp *d, int dkind, int raw_mode
   TRY(canonicalize(s, raw_mode, ob, tb));
   if (s->events_ready) cudaEventRecord(s->ev[6], st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return SCD_ERR_CUDA;
-  unsigned int flags = 0;
-  cudaMemcpy(&flags, &s->d_ctr.p->trav_flags, sizeof(flags), cudaMemcpyDeviceToHost);
-  if (flags & ERR_ZIP) return SCD_ERR_INTERNAL;
+  unsigned int flags[2] = {0, 0};
+  cudaMemcpy(&flags[0], &s->d_ctr.p->trav_flags, sizeof(unsigned int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(&flags[1], &s->d_ctr.p->sort_flags, sizeof(unsigned int), cudaMemcpyDeviceToHost);
+  if ((flags[0] & ERR_ZIP) || (flags[1] & ERR_SORT)) return SCD_ERR_INTERNAL;
   s->graph_M = M;
   finish_metrics(s, raw_mode);
   return SCD_OK;
@@ -456,6 +458,7 @@ static int find_graph(scd_scene *s, const scd_decomp *d, int dkind, int ob, int 
     const DevCounters &c = s->h_ctr;
     if (c.build_flags & ERR_INVALID) return SCD_ERR_INVALID_ARG;
     if (c.build_flags & ERR_KEPLER) return SCD_ERR_KEPLER_NOCONV;
+    if (c.sort_flags & ERR_SORT) return SCD_ERR_INTERNAL;
     bool fits = !(c.trav_flags & (ERR_STACK | ERR_ZIP)) &&
                 std::max(c.n_starts, c.n_ends) <= (unsigned long long)s->pair_cap &&
                 (!dkind || (int64_t)c.refs_total == s->n_refs);
