@@ -129,12 +129,16 @@ typedef struct {
 typedef struct {
   int leaf_size;      /* boxes per leaf: 1, 2, 4 or 8                      */
   int stack_depth;    /* traversal stack entries: 32, 64 or 128            */
-  int block_threads;  /* traversal block size: 64..1024, multiple of 32     */
+  int block_threads;  /* traversal block size (leaves of several boxes):
+                         32..256, a multiple of 32                         */
   int morton_bits;    /* bits per axis of the 4D Morton key: 8, 10, 12, 16  */
   float time_scale;   /* weight of the time axis in the Morton key          */
   int use_graph;      /* 1: replay find_pairs as one captured CUDA graph    */
   int space_warp;     /* 1: log-compress |x| before quantising (finer keys
                          near Earth, where most boxes are); 0: linear      */
+  int nodes_per_step; /* one box per leaf: tree nodes each lane visits per
+                         traversal step (two independent loads in flight),
+                         1 or 2                                            */
 } scd_tuning;
 
 typedef struct scd_scene scd_scene;

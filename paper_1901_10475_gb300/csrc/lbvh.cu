@@ -15,15 +15,15 @@ template <class K>
 __global__ void k_gather_sorted(const uint32_t *__restrict__ id, const float4 *__restrict__ lo,
                                 const float4 *__restrict__ hi, const uint32_t *__restrict__ obj,
                                 const K *__restrict__ keys, int64_t N, int L,
-                                float4 *__restrict__ slo, float4 *__restrict__ shi,
+                                SBox *__restrict__ sbox,
                                 uint32_t *__restrict__ sobj, K *__restrict__ leafkey,
                                 uint32_t *__restrict__ posof, int cell_shift,
                                 uint32_t *__restrict__ scell) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   uint32_t b = id[p];
-  slo[p] = lo[b];
-  shi[p] = hi[b];
+  sbox[p].lo = lo[b];
+  sbox[p].hi = hi[b];
   sobj[p] = obj[b];
   // a box referenced from several cells: any copy will do, their data agree
   if (posof) posof[b] = (uint32_t)p;
@@ -114,9 +114,9 @@ __device__ __forceinline__ float4 f4max(float4 a, float4 b) {
 
 // Bottom-up union.  The second thread to reach a node (atomic arrival count)
 // reads both children and goes on; the first one stops.  Nobody waits.
-// With one box per leaf the sorted boxes are the leaf boxes (leaflo = slo).
-__global__ void k_refit(const float4 *__restrict__ slo, const float4 *__restrict__ shi, int64_t N,
-                        int L, int64_t M, float4 *leaflo, float4 *leafhi,
+// With one box per leaf the sorted boxes are the leaf boxes.
+__global__ void k_refit(const SBox *__restrict__ sbox, int64_t N, int L, int64_t M,
+                        float4 *__restrict__ leaflo, float4 *__restrict__ leafhi,
                         TravNode *__restrict__ nodes, float4 *__restrict__ nlo,
                         float4 *__restrict__ nhi, const int32_t *__restrict__ parent_int,
                         const int32_t *__restrict__ parent_leaf, uint32_t *__restrict__ flags,
@@ -127,14 +127,23 @@ __global__ void k_refit(const float4 *__restrict__ slo, const float4 *__restrict
   const QFrame fr = scene_frame(ctr, T);
   if (L > 1) {
     int64_t b0 = c * L, b1 = b0 + L < N ? b0 + L : N;
-    float4 lo = slo[b0], hi = shi[b0];
+    float4 lo = sbox[b0].lo, hi = sbox[b0].hi;
     for (int64_t b = b0 + 1; b < b1; ++b) {
-      lo = f4min(lo, slo[b]);
-      hi = f4max(hi, shi[b]);
+      lo = f4min(lo, sbox[b].lo);
+      hi = f4max(hi, sbox[b].hi);
     }
     leaflo[c] = lo;
     leafhi[c] = hi;
   }
+  auto leaf_box = [&](int32_t q, float4 &lo, float4 &hi) {
+    if (L == 1) {
+      lo = __ldcg(&sbox[q].lo);
+      hi = __ldcg(&sbox[q].hi);
+    } else {
+      lo = __ldcg(leaflo + q);
+      hi = __ldcg(leafhi + q);
+    }
+  };
   if (M == 1) return;
   int32_t p = parent_leaf[c];
   while (p >= 0) {
@@ -145,17 +154,13 @@ __global__ void k_refit(const float4 *__restrict__ slo, const float4 *__restrict
     const int4 lk = __ldcg(reinterpret_cast<const int4 *>(nodes + p) + 4);
     float4 llo, lhi, rlo, rhi;
     if (lk.x & kLeafBit) {
-      int32_t q = lk.x & ~kLeafBit;
-      llo = __ldcg(leaflo + q);
-      lhi = __ldcg(leafhi + q);
+      leaf_box(lk.x & ~kLeafBit, llo, lhi);
     } else {
       llo = __ldcg(nlo + lk.x);
       lhi = __ldcg(nhi + lk.x);
     }
     if (lk.y & kLeafBit) {
-      int32_t q = lk.y & ~kLeafBit;
-      rlo = __ldcg(leaflo + q);
-      rhi = __ldcg(leafhi + q);
+      leaf_box(lk.y & ~kLeafBit, rlo, rhi);
     } else {
       rlo = __ldcg(nlo + lk.y);
       rhi = __ldcg(nhi + lk.y);
@@ -185,7 +190,7 @@ int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, i
   cudaStream_t st = s->stream;
   int L = s->tune.leaf_size;
   M = (Nq + L - 1) / L;
-  if (!s->s_lo.ensure(Nq, st) || !s->s_hi.ensure(Nq, st) || !s->s_obj.ensure(Nq, st) ||
+  if (!s->s_box.ensure(Nq, st) || !s->s_obj.ensure(Nq, st) ||
       (L > 1 && (!s->d_leaflo.ensure(M, st) || !s->d_leafhi.ensure(M, st))) ||
       !s->d_nodes.ensure(M > 1 ? M - 1 : 1, st) || !s->d_nlo.ensure(M > 1 ? M - 1 : 1, st) ||
       !s->d_nhi.ensure(M > 1 ? M - 1 : 1, st) || !s->d_parent_int.ensure(M, st) ||
@@ -201,7 +206,7 @@ int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, i
     return SCD_ERR_OOM;
   int bs = 256;
   k_gather_sorted<K><<<(unsigned)((Nq + bs - 1) / bs), bs, 0, st>>>(
-      ids_sorted, s->d_lo.p, s->d_hi.p, s->d_obj.p, keys_sorted, Nq, L, s->s_lo.p, s->s_hi.p,
+      ids_sorted, s->d_lo.p, s->d_hi.p, s->d_obj.p, keys_sorted, Nq, L, s->s_box.p,
       s->s_obj.p, leafkey, compact ? s->d_posof.p : nullptr, cell_shift,
       cells ? s->s_cell.p : nullptr);
   note_launch(2);
@@ -217,8 +222,7 @@ int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, i
     note_launch();
   }
   k_refit<<<(unsigned)((M + bs - 1) / bs), bs, 0, st>>>(
-      s->s_lo.p, s->s_hi.p, Nq, L, M, L > 1 ? s->d_leaflo.p : s->s_lo.p,
-      L > 1 ? s->d_leafhi.p : s->s_hi.p, s->d_nodes.p, s->d_nlo.p,
+      s->s_box.p, Nq, L, M, s->d_leaflo.p, s->d_leafhi.p, s->d_nodes.p, s->d_nlo.p,
       s->d_nhi.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p,
       compact ? s->d_qbox.p : nullptr, compact ? s->d_qlink.p : nullptr, s->d_ctr.p, s->T);
   return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;

@@ -94,6 +94,18 @@ struct __align__(16) QBox {
 constexpr uint32_t kQLeftLeaf = 0x80000000u, kQRightLeaf = 0x40000000u;
 constexpr uint32_t kQIndex = 0x3fffffffu;
 
+// A sorted box: both corners in one 32-byte record (x, y, z in km, the tick
+// in w), read with one 256-bit load.
+struct __align__(32) SBox {
+  float4 lo, hi;
+};
+__device__ __forceinline__ void ldg_box(const SBox *p, float4 &lo, float4 &hi) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w), "=f"(hi.x), "=f"(hi.y), "=f"(hi.z),
+        "=f"(hi.w)
+      : "l"(p));
+}
+
 // Both child boxes of a compact node (32 bytes, 32-byte aligned) in one
 // 256-bit read-only load.
 __device__ __forceinline__ void ldg_qbox_pair(const QBox *p, uint4 &l, uint4 &r) {
@@ -336,7 +348,7 @@ struct scd_scene {
   scd::DevBuf<uint32_t> d_id;  // box ids, sorted along with the keys
 
   // sorted leaves and hierarchy
-  scd::DevBuf<float4> s_lo, s_hi;
+  scd::DevBuf<scd::SBox> s_box;
   scd::DevBuf<uint32_t> s_obj;
   scd::DevBuf<uint32_t> d_posof;  // sorted position of each box id
   scd::DevBuf<int2> s_nb;         // sorted positions of the previous / next segment (-1: none)

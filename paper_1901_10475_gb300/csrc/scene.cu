@@ -77,6 +77,7 @@ extern "C" SCD_API int scd_default_tuning(scd_tuning *t) {
   t->time_scale = 1.0f;
   t->use_graph = 0;
   t->space_warp = 0;
+  t->nodes_per_step = 2;
   return SCD_OK;
 }
 
@@ -88,7 +89,8 @@ static bool tuning_ok(const scd_tuning *t) {
             t->morton_bits == 16;
   bool ts = t->time_scale > 0.0f && t->time_scale <= 1.0f;
   bool sw = t->space_warp == 0 || t->space_warp == 1;
-  return leaf && st && bs && mb && ts && sw;
+  bool ns = t->nodes_per_step == 1 || t->nodes_per_step == 2;
+  return leaf && st && bs && mb && ts && sw && ns;
 }
 
 static bool element_ok(const scd_element &x) {
@@ -688,7 +690,7 @@ extern "C" SCD_API void scd_scene_destroy(scd_scene *s) {
   s->d_band.release(st); s->d_ctr.release(st);
   s->d_lo.release(st); s->d_hi.release(st); s->d_obj.release(st);
   s->d_key64.release(st); s->d_key32.release(st); s->d_id.release(st);
-  s->s_lo.release(st); s->s_hi.release(st); s->s_obj.release(st);
+  s->s_box.release(st); s->s_obj.release(st);
   s->d_posof.release(st); s->s_nb.release(st);
   s->s_leafkey32.release(st); s->s_leafkey64.release(st);
   s->d_nodes.release(st); s->d_nlo.release(st); s->d_nhi.release(st);

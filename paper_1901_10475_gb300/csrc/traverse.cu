@@ -28,7 +28,7 @@ struct TravArgs {
   const TravNode *nodes;
   const QBox *qbox;           // compact nodes (one box per leaf)
   const uint2 *qlink;
-  const float4 *slo, *shi;    // sorted boxes
+  const SBox *sbox;           // sorted boxes
   const uint32_t *sobj, *sid; // object and unsorted id of each sorted box
   const int2 *nb;             // sorted positions of the previous / next segment
   const float4 *lo, *hi;      // unsorted boxes (object-major)
@@ -180,14 +180,14 @@ __device__ __forceinline__ void run_ends_sorted(const TravArgs &a, float4 ql0, f
   int qt0 = (int)ql0.w, qt1 = (int)qh0.w, bt0 = (int)bl.w, bt1 = (int)bh.w;
   if (start && s > 0) {
     float4 ql = ql0, qh = qh0, cl = bl, ch = bh;
-    if (qt0 == s) { ql = __ldg(a.slo + qn.x); qh = __ldg(a.shi + qn.x); }
-    if (bt0 == s) { cl = __ldg(a.slo + bn.x); ch = __ldg(a.shi + bn.x); }
+    if (qt0 == s) ldg_box(a.sbox + qn.x, ql, qh);
+    if (bt0 == s) ldg_box(a.sbox + bn.x, cl, ch);
     start = !box_overlap(ql, qh, cl, ch);
   }
   if (end && e < T) {
     float4 ql = ql0, qh = qh0, cl = bl, ch = bh;
-    if (qt1 == e) { ql = __ldg(a.slo + qn.y); qh = __ldg(a.shi + qn.y); }
-    if (bt1 == e) { cl = __ldg(a.slo + bn.y); ch = __ldg(a.shi + bn.y); }
+    if (qt1 == e) ldg_box(a.sbox + qn.y, ql, qh);
+    if (bt1 == e) ldg_box(a.sbox + bn.y, cl, ch);
     end = !box_overlap(ql, qh, cl, ch);
   }
 }
@@ -211,7 +211,8 @@ __device__ __forceinline__ unsigned long long start_key(const TravArgs &a, unsig
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void on_candidate(const TravArgs &a, const Query &q, int64_t pb,
                                              unsigned long long &leaf_tests) {
-  float4 bl = __ldg(a.slo + pb), bh = __ldg(a.shi + pb);
+  float4 bl, bh;
+  ldg_box(a.sbox + pb, bl, bh);
   ++leaf_tests;
   if (!box_overlap(q.lo, q.hi, bl, bh)) return;
   uint32_t bo = __ldg(a.sobj + pb);
@@ -246,8 +247,7 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a) {
   unsigned long long nt = 0, lt = 0;
   if (p < a.N) {
     Query q;
-    q.lo = __ldg(a.slo + p);
-    q.hi = __ldg(a.shi + p);
+    ldg_box(a.sbox + p, q.lo, q.hi);
     q.obj = __ldg(a.sobj + p);
     q.uid = __ldg(a.sid + p);
     int64_t c = p / a.L;
@@ -332,11 +332,9 @@ __device__ __forceinline__ void drain_hits(const TravArgs &a, const uint2 *buf, 
     uint2 h = make_uint2(0u, 0u);
     if (valid) {
       h = buf[k];
-      ql = __ldg(a.slo + h.x);
-      qh = __ldg(a.shi + h.x);
+      ldg_box(a.sbox + h.x, ql, qh);
       qo = __ldg(a.sobj + h.x);
-      bl = __ldg(a.slo + h.y);
-      bh = __ldg(a.shi + h.y);
+      ldg_box(a.sbox + h.y, bl, bh);
       bo = __ldg(a.sobj + h.y);
       // the tree test was on quantised boxes: decide on the exact ones
       valid = bo != qo && box_overlap(ql, qh, bl, bh);
@@ -362,7 +360,31 @@ __device__ __forceinline__ void drain_hits(const TravArgs &a, const uint2 *buf, 
   }
 }
 
-template <int kDepth>
+// One node's two children against the quantised query: the child nodes to
+// descend into (gl, gr) and the leaf children that are candidates (hl, hr).
+__device__ __forceinline__ void test_children(const TravArgs &a, const QBox &q, int64_t p,
+                                              int32_t node, bool &gl, bool &gr, bool &hl,
+                                              bool &hr, int32_t &cl) {
+  uint4 bl, br;
+  ldg_qbox_pair(a.qbox + 2 * (int64_t)node, bl, br);
+  const uint2 lk = __ldg(a.qlink + node);
+  const uint32_t g = lk.x & kQIndex;
+  cl = (int32_t)g;
+  // per 16-bit lane: child lo <= query hi and query lo <= child hi
+  const uint32_t ml = __vcmpleu2(bl.x, q.hi_xy) & __vcmpleu2(q.lo_xy, bl.z) &
+                      __vcmpleu2(bl.y, q.hi_zt) & __vcmpleu2(q.lo_zt, bl.w);
+  const uint32_t mr = __vcmpleu2(br.x, q.hi_xy) & __vcmpleu2(q.lo_xy, br.z) &
+                      __vcmpleu2(br.y, q.hi_zt) & __vcmpleu2(q.lo_zt, br.w);
+  // only subtrees whose rightmost leaf lies after the query's own leaf
+  gl = (int64_t)g > p && ml == 0xffffffffu;
+  gr = (int64_t)lk.y > p && mr == 0xffffffffu;
+  hl = gl && (lk.x & kQLeftLeaf);
+  hr = gr && (lk.x & kQRightLeaf);
+  gl &= !hl;
+  gr &= !hr;
+}
+
+template <int kDepth, bool kTwo>
 __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
   __shared__ uint2 hits[kT2Warps][kHitCap];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -381,6 +403,7 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
   int32_t stack[kDepth];
   int sp = 0, sb = 0;  // the lane's deferred subtrees are stack[sb .. sp)
   int32_t node = 0;
+  int32_t node2 = -1;  // a second node visited in the same step (kTwo)
   for (;;) {
     // lanes without a query take the next ones from the warp's pool
     unsigned need = __ballot_sync(0xffffffffu, p < 0 && !exhausted);
@@ -397,9 +420,12 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
         unsigned long long mine = r < have ? q_next + r : nb + (r - have);
         if (mine < nq) {
           p = (int64_t)mine;
-          q = quantize_box(fr, __ldg(a.slo + p), __ldg(a.shi + p));
+          float4 plo, phi;
+          ldg_box(a.sbox + p, plo, phi);
+          q = quantize_box(fr, plo, phi);
           // the query starts at the root of its own cell's subtree
           node = a.dkind == SCD_DECOMP_NONE ? 0 : __ldg(a.cellroot + __ldg(a.scell + p));
+          node2 = -1;
           sp = sb = 0;
           if (node < 0) p = -1;  // alone in its cell: nothing to find
         } else {
@@ -442,6 +468,7 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
           p = (int64_t)gp;
           q = gq;
           node = gnode;
+          node2 = -1;
           sp = sb = 0;
         }
         if (is_donor && rd < moves) ++sb;
@@ -450,52 +477,66 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
     bool active = p >= 0;
     if (__ballot_sync(0xffffffffu, active) == 0) break;
     const uint32_t pq = (uint32_t)p;  // this step's query, before p may end
-    bool hl = false, hr = false;
-    int32_t cl = 0, cr = 0;
+    bool hl = false, hr = false, hl2 = false, hr2 = false;
+    int32_t cl = 0, cl2 = 0;
     if (active) {
-      uint4 bl, br;
-      ldg_qbox_pair(a.qbox + 2 * (int64_t)node, bl, br);
-      uint2 lk = __ldg(a.qlink + node);
+      if (kTwo && node2 < 0 && sp > sb) node2 = stack[--sp];
+      bool gl, gr, gl2 = false, gr2 = false;
+      test_children(a, q, p, node, gl, gr, hl, hr, cl);
+      if (kTwo && node2 >= 0) {
+        test_children(a, q, p, node2, gl2, gr2, hl2, hr2, cl2);
+        nt += 2;
+      }
       nt += 2;
-      uint32_t g = lk.x & kQIndex;
-      cl = (int32_t)g;
-      cr = (int32_t)g + 1;
-      // per 16-bit lane: child lo <= query hi and query lo <= child hi
-      uint32_t ml = __vcmpleu2(bl.x, q.hi_xy) & __vcmpleu2(q.lo_xy, bl.z) &
-                    __vcmpleu2(bl.y, q.hi_zt) & __vcmpleu2(q.lo_zt, bl.w);
-      uint32_t mr = __vcmpleu2(br.x, q.hi_xy) & __vcmpleu2(q.lo_xy, br.z) &
-                    __vcmpleu2(br.y, q.hi_zt) & __vcmpleu2(q.lo_zt, br.w);
-      bool gl = (int64_t)g > p && ml == 0xffffffffu;
-      bool gr = (int64_t)lk.y > p && mr == 0xffffffffu;
-      // a leaf child that passes is a candidate box with a later position
-      if (gl && (lk.x & kQLeftLeaf)) { hl = true; gl = false; }
-      if (gr && (lk.x & kQRightLeaf)) { hr = true; gr = false; }
-      if (gl && gr) {
-        if (sp < kDepth) {
-          stack[sp++] = cr;
-          node = cl;
+      // the subtrees to visit next: the first two are this lane's next
+      // nodes, the rest go on the stack
+      int32_t first = -1, second = -1;
+      bool overflow = false;
+      auto take = [&](bool go, int32_t c) {
+        if (!go) return;
+        if (first < 0) {
+          first = c;
+        } else if (kTwo && second < 0) {
+          second = c;
+        } else if (sp < kDepth) {
+          stack[sp++] = c;
         } else {
-          atomicOr(&a.ctr->trav_flags, ERR_STACK);
-          p = -1;
+          overflow = true;
         }
-      } else if (gl) {
-        node = cl;
-      } else if (gr) {
-        node = cr;
+      };
+      take(gl, cl);
+      take(gr, cl + 1);
+      if (kTwo) {
+        take(gl2, cl2);
+        take(gr2, cl2 + 1);
+      }
+      if (overflow) {
+        atomicOr(&a.ctr->trav_flags, ERR_STACK);
+        p = -1;
+      } else if (first >= 0) {
+        node = first;
+        node2 = second;
       } else if (sp > sb) {
         node = stack[--sp];
+        node2 = -1;
       } else {
         p = -1;  // query (or the subtree taken from another lane) done
       }
     }
     // append this step's hits to the warp buffer
-    unsigned vl = __ballot_sync(0xffffffffu, hl), vr = __ballot_sync(0xffffffffu, hr);
-    if (hl) buf[nhit + __popc(vl & lt)] = make_uint2(pq, (uint32_t)cl);
-    int nl = __popc(vl);
-    if (hr) buf[nhit + nl + __popc(vr & lt)] = make_uint2(pq, (uint32_t)cr);
-    nhit += nl + __popc(vr);
+    auto append = [&](bool h, int32_t c) {
+      unsigned v = __ballot_sync(0xffffffffu, h);
+      if (h) buf[nhit + __popc(v & lt)] = make_uint2(pq, (uint32_t)c);
+      nhit += __popc(v);
+    };
+    append(hl, cl);
+    append(hr, cl + 1);
+    if (kTwo) {
+      append(hl2, cl2);
+      append(hr2, cl2 + 1);
+    }
     __syncwarp();
-    if (nhit > kHitCap - 64) {
+    if (nhit > kHitCap - (kTwo ? 128 : 64)) {
       drain_hits(a, buf, nhit, we);
       __syncwarp();
       ntests += nhit;  // exact box tests, counted once per warp
@@ -521,16 +562,24 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
   }
 }
 
+// persistent: as many blocks as fit on the GPU at once
+template <int kDepth, bool kTwo>
+static void launch_t2(const TravArgs &a, int sms, cudaStream_t st) {
+  static int per_sm = 0;
+  if (!per_sm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse2<kDepth, kTwo>,
+                                                             kT2Threads, 0);
+  k_traverse2<kDepth, kTwo><<<(unsigned)(sms * std::max(per_sm, 1)), kT2Threads, 0, st>>>(a);
+}
+
 int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_bits) {
   TravArgs a;
   a.nodes = s->d_nodes.p;
   a.qbox = s->d_qbox.p;
   a.qlink = s->d_qlink.p;
-  a.slo = s->s_lo.p;
-  a.shi = s->s_hi.p;
+  a.sbox = s->s_box.p;
   a.sobj = s->s_obj.p;
-  a.sid = s->d_id.p;
   a.nb = s->s_nb.p;
+  a.sid = s->d_id.p;
   a.lo = s->d_lo.p;
   a.hi = s->d_hi.p;
   a.N = s->N;
@@ -556,25 +605,23 @@ int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_b
   a.edges = s->d_edges.p;
   a.objT = s->n_scenes > 0 ? s->d_objT.p : nullptr;
   if (a.dkind != SCD_DECOMP_NONE) a.N = s->n_refs;  // one query per reference
+  // sorted boxes (and node pairs) are read with 32-byte loads
+  if (reinterpret_cast<uintptr_t>(a.sbox) & 31) return SCD_ERR_INTERNAL;
   if (a.L == 1) {
-    // the node pairs are read with 32-byte loads
     if (reinterpret_cast<uintptr_t>(a.qbox) & 31) return SCD_ERR_INTERNAL;
     // persistent: as many blocks as fit on the GPU at once
     static int sms = 0;
     if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-    int per_sm = 0;
+    const bool two = s->tune.nodes_per_step == 2;
     switch (s->tune.stack_depth) {
       case 32:
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse2<32>, kT2Threads, 0);
-        k_traverse2<32><<<(unsigned)(sms * std::max(per_sm, 1)), kT2Threads, 0, s->stream>>>(a);
+        two ? launch_t2<32, true>(a, sms, s->stream) : launch_t2<32, false>(a, sms, s->stream);
         break;
       case 128:
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse2<128>, kT2Threads, 0);
-        k_traverse2<128><<<(unsigned)(sms * std::max(per_sm, 1)), kT2Threads, 0, s->stream>>>(a);
+        two ? launch_t2<128, true>(a, sms, s->stream) : launch_t2<128, false>(a, sms, s->stream);
         break;
       default:
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse2<64>, kT2Threads, 0);
-        k_traverse2<64><<<(unsigned)(sms * std::max(per_sm, 1)), kT2Threads, 0, s->stream>>>(a);
+        two ? launch_t2<64, true>(a, sms, s->stream) : launch_t2<64, false>(a, sms, s->stream);
         break;
     }
     note_launch();
