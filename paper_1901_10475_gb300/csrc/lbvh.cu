@@ -147,9 +147,14 @@ __global__ void k_refit(const SBox *__restrict__ sbox, int64_t N, int L, int64_t
   if (M == 1) return;
   int32_t p = parent_leaf[c];
   while (p >= 0) {
-    __threadfence();
-    if (atomicAdd(flags + p, 1u) == 0u) return;
-    __threadfence();
+    // release this thread's node box, acquire the sibling's (the second
+    // thread to arrive reads both)
+    uint32_t arrived;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                 : "=r"(arrived)
+                 : "l"(flags + p)
+                 : "memory");
+    if (arrived == 0u) return;
     // the links only (the boxes are what this pass writes)
     const int4 lk = __ldcg(reinterpret_cast<const int4 *>(nodes + p) + 4);
     float4 llo, lhi, rlo, rhi;

@@ -9,9 +9,9 @@
 namespace scd {
 
 // ---------------------------------------------------------------------------
-// Kepler's equation E - e sin E = M, FP64 Newton.  The start is M + e sin M
-// for moderate e and Danby's M + 0.85 e sign(sin M) above e = 0.5; both
-// converge monotonically for the e < 1 of closed orbits.
+// Kepler's equation E - e sin E = M by Newton's method.  The start is
+// M + e sin M for moderate e and Danby's M + 0.85 e sign(sin M) above
+// e = 0.5; both converge for the e < 1 of closed orbits.
 // ---------------------------------------------------------------------------
 constexpr int kKeplerMaxIter = 40;
 
@@ -20,52 +20,62 @@ __device__ __forceinline__ double reduce_2pi(double M) {
   return fma(-k, kTwoPi, M);
 }
 
-__device__ __forceinline__ double kepler_E(double M, double e, int &iters) {
-  double E = (e <= 0.5) ? M + e * sin(M) : M + 0.85 * e * (sin(M) >= 0.0 ? 1.0 : -1.0);
-  int it = 0;
-  if (e == 0.0) {
-    iters = 0;
-    return M;
+// Kepler's equation, mixed precision: Newton in FP32 to about 3e-7 rad (at
+// most 12 steps: by perigee at e near 1 the FP32 residual cancels and stalls
+// near 1e-5 rad), then FP64 Newton steps.  Each FP64 step squares the error
+// (times |f''/2f'| = e|sin E| / 2(1 - e cos E), at most 1.5 for e <= 0.75),
+// so one step usually suffices: below 2e-13 rad, i.e. below 1e-8 km of
+// position at GEO distance.  Steps continue while the estimated error left
+// exceeds tol (per object, 1e-7 km / a) or the last correction exceeds 1e-5
+// rad; after kFp64Steps without that, iters reports non-convergence.
+// Returns E with sin E and cos E, corrected to second order in the last step
+// (third-order error below 2e-16), so the caller needs no further sincos.
+constexpr int kFp32Steps = 12, kFp64Steps = 8;
+
+// The rare further FP64 steps: take the pending correction d, then step until
+// the test passes; on return (Ed, s, c, d) describe the last step.
+__device__ __noinline__ void kepler_more_fp64(double M, double e, double tol, double &Ed, double &s,
+                                              double &c, double &d, int &iters) {
+  for (int step = 1; step < kFp64Steps; ++step) {
+    Ed -= d;
+    sincos(Ed, &s, &c);
+    const double fp = 1.0 - e * c;
+    d = (Ed - e * s - M) / fp;
+    iters += 1;
+    if (!(2.0 * fabs(e * s) * d * d > tol * fp || fabs(d) > 1e-5)) return;
   }
-  for (; it < kKeplerMaxIter; ++it) {
-    double s, c;
-    sincos(E, &s, &c);
-    double d = (E - e * s - M) / (1.0 - e * c);
-    E -= d;
-    if (fabs(d) <= 4e-15) break;
-  }
-  iters = it + 1;
-  return E;
+  iters = kKeplerMaxIter;  // no convergence
 }
 
-// Kepler's equation for M in [-pi, pi], mixed precision: Newton in FP32 to
-// about 3e-7 rad, then one FP64 Newton step, which squares that error (to
-// below 2e-13 rad for e <= 0.75, i.e. below 1e-8 km of position at GEO
-// distance).  Returns E with sin E and cos E, corrected to second order in
-// the last step, so the caller needs no further FP64 sincos.
-__device__ __forceinline__ double kepler_E_sc(double M, double e, double &sE, double &cE,
-                                              int &iters) {
+__device__ __forceinline__ double kepler_E_sc(double M, double e, double tol, double &sE,
+                                              double &cE, int &iters) {
   if (e == 0.0) {
     sincos(M, &sE, &cE);
     iters = 0;
     return M;
   }
   const float Mf = (float)M, ef = (float)e;
-  float E = (ef <= 0.5f) ? Mf + ef * sinf(Mf) : Mf + 0.85f * ef * (Mf >= 0.f ? 1.f : -1.f);
+  float E = (ef <= 0.5f) ? Mf + ef * sinf(Mf)
+                         : Mf + 0.85f * ef * (sinf(Mf) >= 0.f ? 1.f : -1.f);
   int it = 0;
-  for (; it < kKeplerMaxIter; ++it) {
+  for (; it < kFp32Steps; ++it) {
     float s, c;
     sincosf(E, &s, &c);
     float d = (E - ef * s - Mf) / (1.0f - ef * c);
     E -= d;
     if (fabsf(d) <= 1e-6f) break;
   }
-  iters = it + 1;
   double Ed = (double)E, s, c;
   sincos(Ed, &s, &c);
-  double d = (Ed - e * s - M) / (1.0 - e * c);
+  double fp = 1.0 - e * c;
+  double d = (Ed - e * s - M) / fp;
+  iters = it + 1;
+  // error left after this step (with a factor 4 of safety) above tol,
+  // compared without a second FP64 division: 2 |e s| d^2 / fp > tol
+  if (2.0 * fabs(e * s) * d * d > tol * fp || fabs(d) > 1e-5)
+    kepler_more_fp64(M, e, tol, Ed, s, c, d, iters);
   // sin(E - d), cos(E - d) to second order in d
-  double h = 0.5 * d * d;
+  const double h = 0.5 * d * d;
   sE = s - d * c - h * s;
   cE = c + d * s - h * c;
   return Ed - d;
@@ -76,7 +86,7 @@ __device__ __forceinline__ void position_at(const ObjParams &p, double t, double
                                             int &iters) {
   double M = reduce_2pi(p.M0 + p.n * t);
   double s, c;
-  kepler_E_sc(M, p.e, s, c, iters);
+  kepler_E_sc(M, p.e, p.tolE, s, c, iters);
   double ce = c - p.e;
 #pragma unroll
   for (int k = 0; k < 3; ++k) out[k] = fma(p.A[k], ce, p.B[k] * s);
@@ -159,7 +169,8 @@ __global__ void k_prepare_objects(const scd_element *__restrict__ el, int64_t n,
   p.vmax = vmax;
   p.r = x.radius_km;
   p.P = P;
-  p.pad[0] = p.pad[1] = 0.0;
+  p.tolE = 1e-7 / a;
+  p.pad = 0.0;
   par[i] = p;
   kout[i] = (int32_t)k;
   segcnt[i] = (sa.T + k) / k;  // ceil((T+1)/k)
@@ -223,10 +234,11 @@ __device__ __forceinline__ int64_t find_object(const int64_t *segoff, int64_t n,
   return lo;
 }
 
-// exact range of cos over [x0, x1] (x1 >= x0): the end values, widened to
-// 1 where a multiple of 2 pi lies inside, to -1 where an odd multiple of pi
-__device__ __forceinline__ void cos_range(double x0, double x1, double &lo, double &hi) {
-  double c0 = cos(x0), c1 = cos(x1);
+// exact range of cos over [x0, x1] (x1 >= x0) from the end values c0 =
+// cos x0, c1 = cos x1: widened to 1 where a multiple of 2 pi lies inside, to
+// -1 where an odd multiple of pi does
+__device__ __forceinline__ void cos_range(double x0, double x1, double c0, double c1, double &lo,
+                                          double &hi) {
   lo = fmin(c0, c1);
   hi = fmax(c0, c1);
   if (x1 - x0 >= kTwoPi) {
@@ -268,13 +280,17 @@ __global__ void __launch_bounds__(256) k_build_boxes(BoxArgs a) {
     double M1 = p.M0 + p.n * ((double)thi * a.tick_s);
     double kk = rint(M0 * (1.0 / kTwoPi));
     double Mr0 = fma(-kk, kTwoPi, M0), Mr1 = fma(-kk, kTwoPi, M1);
+    // both ends by the mixed-precision solve, which also gives sin E, cos E
+    // (E within 1e-7 km / a: far inside the 1e-6 km margin)
     int i0 = 0, i1 = 0;
-    double E0 = kepler_E(Mr0, p.e, i0);
-    double E1 = kepler_E(Mr1, p.e, i1);
+    double s0, c0, s1, c1;
+    double E0 = kepler_E_sc(Mr0, p.e, p.tolE, s0, c0, i0);
+    double E1 = kepler_E_sc(Mr1, p.e, p.tolE, s1, c1, i1);
     iters = max(i0, i1);
     double clo, chi, slo, shi;
-    cos_range(E0, E1, clo, chi);
-    cos_range(E0 - 0.5 * kPi, E1 - 0.5 * kPi, slo, shi);
+    cos_range(E0, E1, c0, c1, clo, chi);
+    // sin E = cos(E - pi/2)
+    cos_range(E0 - 0.5 * kPi, E1 - 0.5 * kPi, s0, s1, slo, shi);
     double w = p.r + kEpsKm;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -362,7 +378,8 @@ __global__ void k_prepare_params_only(const scd_element *__restrict__ el, int64_
   p.vmax = 0;
   p.r = x.radius_km;
   p.P = 0;
-  p.pad[0] = p.pad[1] = 0.0;
+  p.tolE = 1e-7 / a;
+  p.pad = 0.0;
   par[i] = p;
 }
 

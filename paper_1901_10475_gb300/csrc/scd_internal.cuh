@@ -28,7 +28,6 @@ enum : uint32_t {
   ERR_INVALID = 1u << 2,    // invalid element seen on the device
   ERR_ZIP = 1u << 3,        // open run starts and run ends did not pair up
   ERR_SORT = 1u << 4,       // a sort's tile copy did not arrive in time
-  ERR_TIMEOUT = 1u << 4,    // a bounded wait gave up
 };
 
 // Per-object propagation constants, derived once per scene from the
@@ -42,7 +41,8 @@ struct __align__(16) ObjParams {
   double vmax;   // perigee speed [km/s]
   double r;      // radius [km]
   double P;      // period [s]
-  double pad[2];
+  double tolE;   // eccentric-anomaly accuracy of the Kepler solve [rad]: 1e-7 km / a
+  double pad;
 };
 
 // Device-side counters of one scene, read back with one copy.  The first

@@ -387,7 +387,8 @@ static int find_eager(scd_scene *s, const scd_decomp *d, int dkind, int raw_mode
   unsigned int flags[2] = {0, 0};
   cudaMemcpy(&flags[0], &s->d_ctr.p->trav_flags, sizeof(unsigned int), cudaMemcpyDeviceToHost);
   cudaMemcpy(&flags[1], &s->d_ctr.p->sort_flags, sizeof(unsigned int), cudaMemcpyDeviceToHost);
-  if ((flags[0] & ERR_ZIP) || (flags[1] & ERR_SORT)) return SCD_ERR_INTERNAL;
+  if (flags[1] & ERR_SORT) return SCD_ERR_TIMEOUT;
+  if (flags[0] & ERR_ZIP) return SCD_ERR_INTERNAL;
   s->graph_M = M;
   finish_metrics(s, raw_mode);
   return SCD_OK;
@@ -460,7 +461,7 @@ static int find_graph(scd_scene *s, const scd_decomp *d, int dkind, int ob, int 
     const DevCounters &c = s->h_ctr;
     if (c.build_flags & ERR_INVALID) return SCD_ERR_INVALID_ARG;
     if (c.build_flags & ERR_KEPLER) return SCD_ERR_KEPLER_NOCONV;
-    if (c.sort_flags & ERR_SORT) return SCD_ERR_INTERNAL;
+    if (c.sort_flags & ERR_SORT) return SCD_ERR_TIMEOUT;
     bool fits = !(c.trav_flags & (ERR_STACK | ERR_ZIP)) &&
                 std::max(c.n_starts, c.n_ends) <= (unsigned long long)s->pair_cap &&
                 (!dkind || (int64_t)c.refs_total == s->n_refs);

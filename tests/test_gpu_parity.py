@@ -56,6 +56,49 @@ def test_positions_match_fp64_oracle(scd):
     assert np.abs(gp - op).max() < 1e-6
 
 
+def _high_e_elements(n=400, seed=19):
+    """Closed orbits with e in [0.9, 0.99] and perigee 300-2000 km above the
+    surface: the mixed-precision Kepler solve's hardest cases (perigee)."""
+    g = np.random.default_rng(seed)
+    e = g.uniform(0.9, 0.99, n)
+    rp = 6378.137 + g.uniform(300.0, 2000.0, n)
+    els = np.zeros((n, 7))
+    els[:, 0] = rp / (1.0 - e)
+    els[:, 1] = e
+    els[:, 2] = g.uniform(0.0, np.pi, n)
+    els[:, 3:6] = g.uniform(0.0, 2 * np.pi, (n, 3))
+    els[:, 6] = 2.5
+    return els
+
+
+def test_positions_high_eccentricity(scd):
+    els = _high_e_elements()
+    g = np.random.default_rng(1)
+    obj = g.integers(0, len(els), 20000)
+    t = g.uniform(0, 86400.0, 20000)
+    gp = _gpu_positions(scd, els, obj, t)
+    op = O.positions(els, obj, t)
+    assert np.abs(gp - op).max() < 1e-6
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_boxes_high_eccentricity(scd, mode):
+    """Box faces within one FP32 ulp of the oracle's for e up to 0.99."""
+    els = _high_e_elements(n=120, seed=20)
+    pol = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=100.0)
+    sc = scd.Scene(els, 43200.0, 1.0, pol, mode=mode).build_boxes()
+    lo, hi, obj = _host_boxes(sc)
+    k = O.step_ticks(els, O.STEP_PERIOD_FRACTION, 1.0, frac=100.0)
+    olo, ohi, oobj = O.boxes(els, 43200, 1.0, k, mode)
+    assert (obj == oobj).all()
+    for a, b, direction in [(lo, olo, -np.inf), (hi, ohi, np.inf)]:
+        a3, b3 = a[:, :3], b[:, :3]
+        near = (a3 == b3) | (np.nextafter(b3, np.float32(direction)) == a3) | (
+            np.nextafter(a3, np.float32(direction)) == b3)
+        assert near.all()
+    sc.close()
+
+
 @pytest.mark.parametrize("policy", ["fixed", "period", "band"])
 def test_step_lengths_bit_exact(scd, policy):
     els = P.catalog_mixture(n=4000, seed=12)
