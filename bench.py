@@ -285,6 +285,11 @@ def run_single(args, world, wl):
         sc.build_boxes()
         key = autotune.workload_key(els, args.horizon_s, TICK_S, wl, 1 << 24)
         tuning, _ = autotune.load_or_tune(sc, key, reps=1, decomp=decomp)
+    # the whole find sequence replayed as one captured CUDA graph
+    use_graph = args.graph if args.graph >= 0 else int(wl == "band_slab")
+    if use_graph:
+        tuning = dict(json.loads(args.tuning) if args.tuning else (tuning or {}), use_graph=1)
+        sc.set_tuning(tuning)
     d_el = torch.as_tensor(els, device="cuda")
 
     def step():
@@ -293,6 +298,17 @@ def run_single(args, world, wl):
         return scd.scd_find_pairs_device(sc.handle, decomp)[1]
 
     r = time_scene_steps(sc, step, args.steps, args.warmup, dev, world)
+    if use_graph:
+        # a replayed graph's kernels cannot be timed one by one: the phase
+        # split comes from the same screen launched eagerly, after the timed
+        # replays (CUDA events on the scene's stream around each phase)
+        sc.set_tuning(dict(tuning, use_graph=0))
+        step()
+        step()
+        m = sc.metrics()
+        r["phase_ms"] = {k: m[k] for k in r["phase_ms"]}
+        r["phase_ms_source"] = "one eager screen after the timed graph replays"
+        sc.set_tuning(tuning)
     t_total = sum(r["times"])
     if world > 1:
         t = torch.tensor([t_total], device="cuda", dtype=torch.float64)
@@ -376,13 +392,15 @@ def run_learned100k(args, world):
     import torch
 
     import paper_1901_10475_gb300 as scd
-    from oracle import stepnet as _unused  # noqa: F401  (features are computed on the GPU)
     from paper_1901_10475_gb300 import stepnet as sn
     dev = _device()
     # train on the method's own sweeps of a smaller population
     train_els = P.catalog_mixture(n=100000, seed=P.SEED_BASE + 6, dense_shells=True)
     t0 = time.perf_counter()
-    sw = sn.sweep(train_els, 7200.0, mode=args.mode)
+    # 20 step multipliers from P/50 to P/400 (geometric): 2M (elements, step,
+    # pair count) samples from 100k objects, with the screens' times
+    mults = tuple(float(50.0 * 8.0 ** (q / 19.0)) for q in range(20))
+    sw = sn.sweep(train_els, 7200.0, multipliers=mults, mode=args.mode)
     c_box, c_hit = sn.fit_cost_model(sw)
     Y = sn.targets(train_els, sw, c_box, c_hit).astype(np.float32)
     X = sn.features(train_els).cpu().numpy()
@@ -413,7 +431,9 @@ def run_learned100k(args, world):
     r["p100_ms"] = statistics.mean(out["p100"]["times"])
     r["p100_boxes"] = out["p100"]["metrics"]["boxes"]
     r["p100_pairs"] = out["p100"]["n_pairs"]
-    r["training"] = {"seconds": train_s, "samples": len(X), "final_loss": float(losses[-1]),
+    r["training"] = {"seconds": train_s, "objects": len(X),
+                     "sweep_samples": int(len(mults) * len(train_els)),
+                     "multipliers": [round(m, 1) for m in mults], "final_loss": float(losses[-1]),
                      "c_box_ms": c_box, "c_hit_ms": c_hit}
     net.close()
     return r
@@ -445,6 +465,9 @@ def main():
     ap.add_argument("--workload", default="catalog24h", choices=sorted(WORKLOADS))
     ap.add_argument("--tuning", default="", help="JSON tuning overrides")
     ap.add_argument("--autotune", action="store_true", help="search the tuning first")
+    ap.add_argument("--graph", type=int, default=-1,
+                    help="1: replay each screen's find sequence as one captured CUDA graph, "
+                         "0: launch eagerly (default: graph for band_slab, eager otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--box-mode", default="", choices=["", "speed", "interval"],
                     help="occ-int bound; default: speed, interval for batch64 and learned100k")
@@ -463,6 +486,10 @@ def main():
              if args.mode else "; SPEED boxes")
     if args.horizon_s != HORIZON_S:
         desc = desc.replace("24 h", f"{args.horizon_s:.0f} s")
+    if wl in ("catalog24h", "band_slab") and (
+            args.graph == 1 or (args.graph < 0 and wl == "band_slab")):
+        desc += "; the find sequence replayed as one captured CUDA graph"
+
 
     if args.impl == "reference":
         if rank != 0:
@@ -537,6 +564,8 @@ def main():
                             "traffic": traffic,
                             "peak_source": src, "phase_ms": ph,
                             "algorithmic_bytes": byt[name]}
+        if "phase_ms_source" in r:
+            line["roofline"]["phase_ms_source"] = r["phase_ms_source"]
         line["gpu_launches"] = r["launches"]
     if wl == "catalog24h":
         cpu = None

@@ -75,6 +75,7 @@ def lib():
                 "or_raw_cells_selected": (i64, [vp, vp, vp, i64, vp, vp, i64]),
                 "or_canonicalize": (i64, [vp, i64]),
                 "or_alg1_witnesses": (i64, [vp, i64, i64, d, vp, i64]),
+                "or_alg1_sweep": (i64, [vp, i64, i64, i64, d, vp, vp, i64]),
                 "or_alg3": (i32, [vp, i64, i64, d, i32, i64, vp, vp, vp, vp]),
                 "or_radial_range": (None, [vp, vp]),
                 "or_band_edges": (None, [vp, i64, i32, vp]),
@@ -286,6 +287,50 @@ def screen(els, T: int, tick_s: float, k, mode: int = BOX_SPEED):
 def alg1_witnesses(els, T: int, tick_s: float) -> np.ndarray:
     E = _els(els)
     return _cells_call_w(lib().or_alg1_witnesses, _p(E), len(E), int(T), float(tick_s))
+
+
+APPROACH_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("t", "<i4"), ("dist", "<f8")])
+
+
+def alg1_sweep(els, t0: int, t1: int, tick_s: float) -> np.ndarray:
+    """Alg 1 witnesses on ticks t0..t1 (pairs found by an x sweep, same
+    predicate), each with the Euclidean distance of the two centres."""
+    E = _els(els)
+    cap = 1 << 12
+    while True:
+        w = np.zeros(cap, WITNESS_DTYPE)
+        dist = np.zeros(cap)
+        n = lib().or_alg1_sweep(_p(E), len(E), int(t0), int(t1), float(tick_s), _p(w), _p(dist),
+                                cap)
+        if n <= cap:
+            out = np.zeros(n, APPROACH_DTYPE)
+            out["i"], out["j"], out["t"], out["dist"] = w["i"][:n], w["j"][:n], w["t"][:n], dist[:n]
+            return out
+        cap = int(n)
+
+
+def _alg1_chunk(args):
+    els, t0, t1, tick_s = args
+    return alg1_sweep(els, t0, t1, tick_s)
+
+
+def close_approaches(els, T: int, tick_s: float, d_km: float, processes: int = 0) -> np.ndarray:
+    """Every (i < j, tick) with the two centres closer than d_km (Euclidean)
+    at a tick of 0..T: the Alg 1 witnesses (cube contact, a superset when
+    d_km <= r_i + r_j) filtered by distance.  Tick ranges run in a pool of
+    processes started with spawn (safe after a GPU context exists)."""
+    import multiprocessing as mp
+    E = _els(els)
+    n_proc = processes or min(32, os.cpu_count() or 1)
+    edges = np.linspace(0, T + 1, 4 * n_proc + 1).astype(np.int64)
+    jobs = [(E, int(a), int(b) - 1, float(tick_s)) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+    if n_proc > 1 and len(jobs) > 1:
+        with mp.get_context("spawn").Pool(n_proc) as pool:
+            parts = pool.map(_alg1_chunk, jobs)
+    else:
+        parts = [_alg1_chunk(j) for j in jobs]
+    w = np.concatenate(parts) if parts else np.zeros(0, APPROACH_DTYPE)
+    return w[w["dist"] < d_km]
 
 
 def _cells_call_w(fn, *args):

@@ -478,6 +478,58 @@ int64_t or_alg1_witnesses(const double *els, int64_t n, int64_t T,
   return c;
 }
 
+/* Alg 1 over ticks t0..t1 (inclusive) with the pairs restricted by a sweep
+ * along x: two objects can only meet (Def 3) if their x centres are within
+ * r_i + r_j <= 2 max r, so after sorting by x only pairs inside that window
+ * are tested, with the same predicate.  Each witness also gets the
+ * Euclidean distance of the two centres (dist[k]).  Witnesses come in tick
+ * order; within a tick in sweep order (i < j in each). */
+typedef struct {
+  double x;
+  int64_t i;
+} or_xkey;
+
+static int cmp_xkey(const void *a, const void *b) {
+  double xa = ((const or_xkey *)a)->x, xb = ((const or_xkey *)b)->x;
+  return (xa > xb) - (xa < xb);
+}
+
+int64_t or_alg1_sweep(const double *els, int64_t n, int64_t t0, int64_t t1, double tick_s,
+                      or_witness *out, double *dist, int64_t cap) {
+  double *pos = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+  or_xkey *key = (or_xkey *)malloc(sizeof(or_xkey) * (size_t)(n > 0 ? n : 1));
+  double rmax = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    if (els[7 * i + 6] > rmax) rmax = els[7 * i + 6];
+  int64_t c = 0;
+  for (int64_t t = t0; t <= t1; ++t) {
+    for (int64_t i = 0; i < n; ++i) {
+      or_position(els + 7 * i, (double)t * tick_s, pos + 3 * i);
+      key[i].x = pos[3 * i];
+      key[i].i = i;
+    }
+    qsort(key, (size_t)n, sizeof(or_xkey), cmp_xkey);
+    for (int64_t a = 0; a < n; ++a)
+      for (int64_t b = a + 1; b < n && key[b].x - key[a].x <= 2.0 * rmax; ++b) {
+        int64_t i = key[a].i < key[b].i ? key[a].i : key[b].i;
+        int64_t j = key[a].i < key[b].i ? key[b].i : key[a].i;
+        if (!occ_collide(pos + 3 * i, els[7 * i + 6], pos + 3 * j, els[7 * j + 6])) continue;
+        if (c < cap) {
+          double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1],
+                 dz = pos[3 * i + 2] - pos[3 * j + 2];
+          out[c].i = (uint32_t)i;
+          out[c].j = (uint32_t)j;
+          out[c].t = (int32_t)t;
+          dist[c] = sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        ++c;
+      }
+  }
+  free(key);
+  free(pos);
+  return c;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Alg 3 with Alg 4 (initializeTree), getSmallestMaxTimeObject, Alg 5      */
 /* (advanceTime) and Alg 6 (resolveCollisions).  The AABB tree's job is to  */

@@ -104,6 +104,11 @@ int64_t or_canonicalize(or_cell *cells, int64_t n);
  * for t = 0..T, in (t, i, j) order. */
 int64_t or_alg1_witnesses(const double *els, int64_t n, int64_t T,
                           double tick_s, or_witness *out, int64_t cap);
+/* Alg 1 on ticks t0..t1 with pairs restricted by an x sweep (same witness
+ * set as or_alg1_witnesses on that range); dist[k] = Euclidean distance of
+ * witness k's centres.  Returns the witness count (only cap are written). */
+int64_t or_alg1_sweep(const double *els, int64_t n, int64_t t0, int64_t t1, double tick_s,
+                      or_witness *out, double *dist, int64_t cap);
 /* Alg 3 with Algs 4-6: the serial 4D search.  Returns 1 and the first
  * witness, 0 for None, or a negative code if a loop invariant (Sec. 7.2)
  * failed: -1 invariant 1, -2 invariant 2 (needs t_first, the earliest Alg 1

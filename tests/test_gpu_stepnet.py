@@ -124,3 +124,77 @@ def test_trained_steps_beat_the_period_rule_on_held_out_objects(mods):
     assert cost_learned <= cost_rule
     sc.close()
     net.close()
+
+
+def _covered(pairs, near):
+    """Is every approach (i, j, t) inside a reported interval of its pair?"""
+    key = pairs["i"].astype(np.int64) << 32 | pairs["j"].astype(np.int64)
+    order = np.argsort(key, kind="stable")
+    key, lo, hi = key[order], pairs["tlo"][order], pairs["thi"][order]
+    missed = []
+    for w in near:
+        k = (int(w["i"]) << 32) | int(w["j"])
+        a, b = np.searchsorted(key, k, "left"), np.searchsorted(key, k, "right")
+        if not np.any((lo[a:b] <= w["t"]) & (w["t"] <= hi[a:b])):
+            missed.append((int(w["i"]), int(w["j"]), int(w["t"])))
+    return missed
+
+
+def test_learned_and_rule_screens_miss_no_close_approach(mods):
+    """Soundness on a dense population: every approach closer than 5 km (two
+    objects of radius 2.5 km touching), found by Alg 1 at every 1 s tick of
+    6 h over 2000 objects, lies inside a reported interval of its pair, with
+    learned steps and with P/100."""
+    scd, sn = mods
+    els = P.catalog_mixture(n=2000, seed=91, dense_shells=True, crossing_frac=0.01,
+                            horizon_s=21600.0)
+    T = 21600
+    near = O.close_approaches(els, T, 1.0, 5.0)
+    assert len(near) >= 5  # the seeded crossings at least
+    net = sn.StepNet(seed=9)
+    net.params = (np.random.default_rng(4).standard_normal(OS.N_PARAMS) * 0.1).astype(np.float32)
+    rule = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=100.0)
+    for name, pol in (("learned", net.policy()), ("P/100", rule)):
+        sc = scd.Scene(els, float(T), 1.0, pol).build_boxes()
+        got = sc.find_pairs()
+        sc.close()
+        missed = _covered(got, near)
+        assert not missed, (name, missed[:5])
+    net.close()
+
+
+def test_learned100k_screen_misses_no_close_approach(mods):
+    """The n = 100000 dense-shell screen of 24 h with INTERVAL boxes, under
+    steps from a network trained on 20-multiplier sweeps of another 100000
+    objects and under P/100: on the 2000 objects nearest the 550 km shell,
+    every approach closer than 5 km at a 1 s tick (Alg 1 by brute force)
+    lies inside a reported interval of the full screen's output."""
+    scd, sn = mods
+    train = P.catalog_mixture(n=100000, seed=P.SEED_BASE + 6, dense_shells=True)
+    mults = tuple(50.0 * 8.0 ** (q / 19.0) for q in range(20))
+    sw = sn.sweep(train, 7200.0, multipliers=mults, mode=scd.SCD_BOX_INTERVAL)
+    c_box, c_hit = sn.fit_cost_model(sw)
+    Y = sn.targets(train, sw, c_box, c_hit).astype(np.float32)
+    X = sn.features(train).cpu().numpy()
+    net = sn.StepNet(seed=7)
+    sn.train(net, X, Y, epochs=60, batch=1024, lr=3e-3)
+
+    els = P.catalog_mixture(n=100000, seed=P.SEED_BASE + 5, dense_shells=True)
+    hp = els[:, 0] * (1.0 - els[:, 1]) - 6378.137
+    sub = np.sort(np.argsort(np.abs(hp - 550.0))[:2000])
+    near = O.close_approaches(els[sub], 86400, 1.0, 5.0)
+    assert len(near) > 100
+    near["i"], near["j"] = sub[near["i"]], sub[near["j"]]  # population indices (i < j kept)
+    in_sub = torch.zeros(len(els), dtype=torch.bool, device="cuda")
+    in_sub[torch.as_tensor(sub, device="cuda")] = True
+    rule = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=100.0)
+    for name, pol in (("learned", net.policy()), ("P/100", rule)):
+        sc = scd.Scene(els, 86400.0, 1.0, pol, mode=scd.SCD_BOX_INTERVAL).build_boxes()
+        pr = sc.find_pairs_device()
+        keep = in_sub[pr[:, 0].long()] & in_sub[pr[:, 1].long()]
+        pairs = scd.pairs_from_device(pr[keep])
+        del pr, keep
+        sc.close()
+        missed = _covered(pairs, near)
+        assert not missed, (name, len(missed), missed[:5])
+    net.close()

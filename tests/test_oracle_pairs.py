@@ -148,3 +148,30 @@ def test_one_tick_segments_equal_alg1_exactly():
     got = sorted((c[0], c[1], c[2]) for c in raw.tolist())
     assert all(c[2] == c[3] for c in raw.tolist())
     assert got == sorted(map(tuple, wit.tolist()))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_alg1_sweep_equals_alg1(seed):
+    """The x-swept Alg 1 finds exactly the all-pairs Alg 1 witnesses, and each
+    witness's distance is the Euclidean distance of the two positions."""
+    els = P.uniform_leo(60, seed=seed, radius_km=250.0)
+    a = O.alg1_witnesses(els, 300, 1.0)
+    b = O.alg1_sweep(els, 0, 300, 1.0)
+    key = lambda w: sorted(zip(w["i"].tolist(), w["j"].tolist(), w["t"].tolist()))
+    assert len(a) > 20 and key(a) == key(b)
+    for w in b[:10]:
+        pi = O.position(els[w["i"]], float(w["t"]))
+        pj = O.position(els[w["j"]], float(w["t"]))
+        assert w["dist"] == pytest.approx(np.linalg.norm(pi - pj), abs=1e-9)
+
+
+def test_close_approaches_find_the_seeded_crossings():
+    """Crossing pairs seeded at a known tick come within a few km then; the
+    pooled close-approach search returns them, and only distances < d."""
+    els = P.catalog_mixture(n=400, seed=9, crossing_frac=0.05)
+    got = O.close_approaches(els, 1200, 1.0, 5.0, processes=2)
+    assert len(got) > 0 and (got["dist"] < 5.0).all()
+    one = O.alg1_sweep(els, 0, 1200, 1.0)
+    want = one[one["dist"] < 5.0]
+    key = lambda w: sorted(zip(w["i"].tolist(), w["j"].tolist(), w["t"].tolist()))
+    assert key(got) == key(want)
