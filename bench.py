@@ -74,7 +74,7 @@ WORKLOADS = {
         "metric": "ms per 24h screen at n=100000, learned steps",
         "desc": ("100,000-object mixture with Gaussian LEO shells at 550 and 1150 km, 24 h; "
                  "per-object steps from the 8-64-64-1 step network trained in this run on "
-                 "sweeps of another 100,000-object population of the same shape (2 h, multipliers 50-400)")},
+                 "sweeps of another 100,000-object population of the same shape (24 h, 20 multipliers P/70-P/280)")},
 }
 
 
@@ -397,10 +397,12 @@ def run_learned100k(args, world):
     # train on the method's own sweeps of a smaller population
     train_els = P.catalog_mixture(n=100000, seed=P.SEED_BASE + 6, dense_shells=True)
     t0 = time.perf_counter()
-    # 20 step multipliers from P/50 to P/400 (geometric): 2M (elements, step,
-    # pair count) samples from 100k objects, with the screens' times
-    mults = tuple(float(50.0 * 8.0 ** (q / 19.0)) for q in range(20))
-    sw = sn.sweep(train_els, 7200.0, multipliers=mults, mode=args.mode)
+    # 20 step multipliers from P/70 to P/280 (geometric) at the screen's own
+    # horizon: 2M (elements, step, candidate-pair count) samples from 100k
+    # objects, with the screens' times (per-object costs do not carry over
+    # from short horizons: a box costs more in the larger tree of a long one)
+    mults = tuple(float(70.0 * 4.0 ** (q / 19.0)) for q in range(20))
+    sw = sn.sweep(train_els, HORIZON_S, multipliers=mults, mode=args.mode, count="runs")
     c_box, c_hit = sn.fit_cost_model(sw)
     Y = sn.targets(train_els, sw, c_box, c_hit).astype(np.float32)
     X = sn.features(train_els).cpu().numpy()
@@ -433,7 +435,11 @@ def run_learned100k(args, world):
     r["p100_pairs"] = out["p100"]["n_pairs"]
     r["training"] = {"seconds": train_s, "objects": len(X),
                      "sweep_samples": int(len(mults) * len(train_els)),
-                     "multipliers": [round(m, 1) for m in mults], "final_loss": float(losses[-1]),
+                     "multipliers": [round(m, 1) for m in mults],
+                     "sweep_ms": [round(float(x), 2) for x in sw["ms"]],
+                     "sweep_boxes": [int(x) for x in sw["total_boxes"]],
+                     "sweep_pairs": [int(x) for x in sw["total_pairs"]],
+                     "final_loss": float(losses[-1]),
                      "c_box_ms": c_box, "c_hit_ms": c_hit}
     net.close()
     return r

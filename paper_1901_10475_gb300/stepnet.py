@@ -89,9 +89,11 @@ def features(elements):
 
 
 def sweep(elements, horizon_s: float, tick_s: float = 1.0, multipliers=MULTIPLIERS,
-          mode: int = B.SCD_BOX_SPEED):
+          mode: int = B.SCD_BOX_SPEED, count: str = "cells"):
     """Screen the population once per multiplier.  Returns a dict of arrays:
-    boxes [F, n], pairs [F, n] (overlapping box pairs per object), ms [F],
+    boxes [F, n], pairs [F, n] (per object: its overlapping box pairs when
+    count == "cells", its merged candidate pairs when count == "runs"; the
+    latter stays within the record limits at long horizons), ms [F],
     total_boxes [F], total_pairs [F]."""
     import torch
 
@@ -117,7 +119,10 @@ def sweep(elements, horizon_s: float, tick_s: float = 1.0, multipliers=MULTIPLIE
         ms[q] = e0.elapsed_time(e1)
         k = sc.steps().cpu().numpy().astype(np.int64)
         boxes[q] = (T + k) // k
-        ptr, m = B.scd_find_raw_cells_device(sc.handle)
+        if count == "runs":
+            ptr, m = B.scd_find_pairs_device(sc.handle)
+        else:
+            ptr, m = B.scd_find_raw_cells_device(sc.handle)
         cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
         B.scd_count_pairs_per_object(ptr, m, n, cnt.data_ptr(), st.cuda_stream)
         pairs[q] = cnt.cpu().numpy()
