@@ -4,7 +4,9 @@ Times whole screens (boxes through the canonical list) with CUDA events on
 the scene's stream for candidate tunings, keeps the fastest, and caches the
 choice in a JSON file keyed by GPU name, a hash of the workload and log2 of
 the box count.  A staged search: leaf size x Morton bits x space warp
-first, then the time weight and block shape around the winner.
+first, then the time weight, the stack depth and the block shape (leaves of
+several boxes) or the nodes per traversal step (one box per leaf) around
+the winner.
 """
 from __future__ import annotations
 
@@ -79,6 +81,8 @@ def tune(scene, reps: int = 2, verbose: bool = False, decomp=None):
     stage2 += [dict(best, stack_depth=sd) for sd in (32, 128)]
     if best["leaf_size"] > 1:
         stage2 += [dict(best, block_threads=bt) for bt in (64, 256)]
+    else:
+        stage2 += [dict(best, nodes_per_step=1)]
     for cand in stage2:
         ms = run(cand)
         if ms < best_ms:

@@ -73,7 +73,7 @@ extern "C" SCD_API int scd_default_tuning(scd_tuning *t) {
   t->leaf_size = 1;  // one box per leaf: the persistent lock-step traversal
   t->stack_depth = 64;
   t->block_threads = 128;
-  t->morton_bits = 8;
+  t->morton_bits = 10;
   t->time_scale = 1.0f;
   t->use_graph = 0;
   t->space_warp = 0;
