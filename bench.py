@@ -78,9 +78,11 @@ WORKLOADS = {
 }
 
 
-TRAVERSAL_SOURCES = ("paper_1901_10475_gb300/csrc/traverse.cu",
-                     "paper_1901_10475_gb300/csrc/lbvh.cu",
-                     "paper_1901_10475_gb300/csrc/scd_internal.cuh")
+def library_sources():
+    """Every source file of the CUDA library, in name order (the traversal's
+    traffic depends on the tree, the boxes and the default tuning too)."""
+    d = os.path.join(ROOT, "paper_1901_10475_gb300", "csrc")
+    return [os.path.join(d, f) for f in sorted(os.listdir(d)) if f.endswith((".cu", ".cuh"))]
 
 
 def measured_traffic(workload: str):
@@ -97,8 +99,8 @@ def measured_traffic(workload: str):
             k, v = line.split(":", 1)
             fields[k] = v.strip()
     h = hashlib.sha256()
-    for f in TRAVERSAL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
+    for f in library_sources():
+        with open(f, "rb") as fh:
             h.update(fh.read())
     if fields.get("source_sha256") != h.hexdigest()[:16]:
         return None
