@@ -204,6 +204,17 @@ def _device():
     return dev
 
 
+def slowest_rank(t_ms: float, world: int, device: str = "cuda") -> float:
+    """The largest of the ranks' timed totals (every rank calls this; one
+    process per GPU, each a replica of the whole workload)."""
+    if world <= 1:
+        return t_ms
+    import torch
+    t = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_scene_steps(sc, step, steps, warmup, dev, world):
     """Warm up, then time `steps` screens with CUDA events on the scene's
     stream, flushing L2 between them (outside the timed events)."""
@@ -311,12 +322,8 @@ def run_single(args, world, wl):
         r["phase_ms"] = {k: m[k] for k in r["phase_ms"]}
         r["phase_ms_source"] = "one eager screen after the timed graph replays"
         sc.set_tuning(tuning)
-    t_total = sum(r["times"])
-    if world > 1:
-        t = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(t.item())
-    r["value"] = t_total / (args.steps * world)
+    # whole job: every rank's screens over the slowest rank's time
+    r["value"] = slowest_rank(sum(r["times"]), world) / (args.steps * world)
     r["unit"] = "ms"
     r["higher_is_better"] = False
     if decomp is None:
@@ -356,12 +363,13 @@ def run_batch64(args, world):
         t0 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         done = []
-        npairs = 0
+        npairs = launches = 0
         for g in groups:
             b = scd.BatchScene([scenes[s][0] for s in g], [scenes[s][1] for s in g], TICK_S, pol,
                                mode=args.mode)
             b.build_boxes()
             npairs += scd.scd_find_pairs_device(b.handle)[1]
+            launches += b.metrics()["launches"]
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(stream)
             done.append((g, ev))
@@ -371,23 +379,31 @@ def run_batch64(args, world):
         for g, ev in done:
             for s in g:
                 lat[s] = t0.elapsed_time(ev)
-        return t0, done, lat, npairs
+        return t0, done, lat, npairs, launches
 
     for _ in range(args.warmup):
         one_pass(False)
     totals, lats = [], []
+    launches = 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
         for _ in range(args.steps):
-            t0, done, lat, npairs = one_pass(True)
+            t0, done, lat, npairs, nl = one_pass(True)
             totals.append(t0.elapsed_time(done[-1][1]))
             lats.extend(lat.values())
+            launches += nl
     ms = statistics.mean(totals)
-    return {"value": len(scenes) * 1e3 / ms, "unit": "scenes/s", "higher_is_better": True,
+    # whole job: every rank's scenes over the slowest rank's time
+    t_all = slowest_rank(sum(totals), world)
+    return {"value": len(scenes) * world * args.steps * 1e3 / t_all, "unit": "scenes/s",
+            "higher_is_better": True,
             "times": totals, "clocks": clk.summary(), "n_pairs": npairs,
             "latency_ms": {"p50": float(np.percentile(lats, 50)),
                            "p99": float(np.percentile(lats, 99))},
             "batches": len(groups), "objects": int(sum(len(e) for e, _ in scenes)),
-            "boxes_est": float(sum(est)), "ms_per_pass": ms, "launches": None}
+            "boxes_est": float(sum(est)), "ms_per_pass": ms, "launches": launches}
 
 
 def run_learned100k(args, world):
@@ -428,7 +444,7 @@ def run_learned100k(args, world):
         out[name] = time_scene_steps(sc, step, args.steps, args.warmup, dev, world)
         sc.close()
     r = out["learned"]
-    r["value"] = statistics.mean(r["times"])
+    r["value"] = slowest_rank(sum(r["times"]), world) / (args.steps * world)
     r["unit"] = "ms"
     r["higher_is_better"] = False
     r["n"] = 100000
@@ -584,6 +600,8 @@ def main():
         line["cpu_baseline"] = cpu
     if "e2e" in r:
         line["e2e"] = r["e2e"]
+    if "gpu_launches" not in line and r.get("launches") is not None:
+        line["gpu_launches"] = r["launches"]
     for k in ("latency_ms", "batches", "objects", "boxes_est", "ms_per_pass", "p100_ms",
               "p100_boxes", "p100_pairs", "training", "tuning"):
         if k in r and r[k] is not None:
