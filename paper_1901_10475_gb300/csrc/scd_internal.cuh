@@ -83,13 +83,15 @@ static_assert(sizeof(TravNode) == 80 && offsetof(TravNode, left) == 64,
 constexpr int32_t kLeafBit = (int32_t)0x80000000u;
 
 // Compact node of the one-box-per-leaf traversal (40 bytes): both child
-// boxes quantised to 16 bits per face in the scene frame (lower faces
-// rounded down, upper faces up, so a quantised test never rejects a pair
-// that overlaps in FP32), the split gamma (left child gamma, right child
-// gamma + 1) with two leaf flags, and the rightmost leaf under the right
-// child (the left child's rightmost leaf is gamma itself).
+// boxes quantised in the scene frame (lower faces rounded down, upper faces
+// up, so a quantised test never rejects a pair that overlaps in FP32), the
+// split gamma (left child gamma, right child gamma + 1) with two leaf flags,
+// and the rightmost leaf under the right child (the left child's rightmost
+// leaf is gamma itself).  x and y take 16 bits, z 15 and the tick 17: one
+// quantum per tick up to 131071 ticks, so boxes of consecutive segments
+// (which touch, tick hi + 1 = tick lo, but do not overlap) stay apart.
 struct __align__(16) QBox {
-  uint32_t lo_xy, lo_zt, hi_xy, hi_zt;  // u16 pairs: x | y << 16, z | t << 16
+  uint32_t lo_xy, lo_zt, hi_xy, hi_zt;  // x | y << 16 and z | t << 15
 };
 constexpr uint32_t kQLeftLeaf = 0x80000000u, kQRightLeaf = 0x40000000u;
 constexpr uint32_t kQIndex = 0x3fffffffu;
@@ -116,7 +118,7 @@ __device__ __forceinline__ void ldg_qbox_pair(const QBox *p, uint4 &l, uint4 &r)
 
 // the scene frame of the quantisation: x, y, z in [-R, R] km, t in [0, T]
 struct QFrame {
-  float R, sx, st;  // sx = 65535 / (2R), st = 65535 / T
+  float R, sx, sz, st;  // sx = 65535 / 2R, sz = 32767 / 2R, st = min(1, 131071 / T)
 };
 
 // the frame of a scene, from the extent found by the box build; every kernel
@@ -125,29 +127,36 @@ __device__ inline QFrame scene_frame(const DevCounters *ctr, int64_t T) {
   QFrame f;
   f.R = (float)__longlong_as_double((long long)ctr->extent_bits);
   f.sx = 65535.0f / (2.0f * f.R);
-  f.st = 65535.0f / (float)(T > 0 ? T : 1);
+  f.sz = 32767.0f / (2.0f * f.R);
+  f.st = fminf(1.0f, 131071.0f / (float)(T > 0 ? T : 1));
   return f;
 }
 
-__host__ __device__ inline uint32_t q16_lo(float v) {
+// outward quantisation to [0, top]
+__host__ __device__ inline uint32_t q_lo(float v, float top) {
   float f = floorf(v);
-  f = f < 0.f ? 0.f : (f > 65535.f ? 65535.f : f);
+  f = f < 0.f ? 0.f : (f > top ? top : f);
   return (uint32_t)f;
 }
-__host__ __device__ inline uint32_t q16_hi(float v) {
+__host__ __device__ inline uint32_t q_hi(float v, float top) {
   float f = ceilf(v);
-  f = f < 0.f ? 0.f : (f > 65535.f ? 65535.f : f);
+  f = f < 0.f ? 0.f : (f > top ? top : f);
   return (uint32_t)f;
 }
 // quantise a box outward; the map x -> (x + R) * sx is monotone in FP32, so
 // box order relations survive it
 __host__ __device__ inline QBox quantize_box(const QFrame &f, float4 lo, float4 hi) {
   QBox q;
-  q.lo_xy = q16_lo((lo.x + f.R) * f.sx) | (q16_lo((lo.y + f.R) * f.sx) << 16);
-  q.lo_zt = q16_lo((lo.z + f.R) * f.sx) | (q16_lo(lo.w * f.st) << 16);
-  q.hi_xy = q16_hi((hi.x + f.R) * f.sx) | (q16_hi((hi.y + f.R) * f.sx) << 16);
-  q.hi_zt = q16_hi((hi.z + f.R) * f.sx) | (q16_hi(hi.w * f.st) << 16);
+  q.lo_xy = q_lo((lo.x + f.R) * f.sx, 65535.f) | (q_lo((lo.y + f.R) * f.sx, 65535.f) << 16);
+  q.lo_zt = q_lo((lo.z + f.R) * f.sz, 32767.f) | (q_lo(lo.w * f.st, 131071.f) << 15);
+  q.hi_xy = q_hi((hi.x + f.R) * f.sx, 65535.f) | (q_hi((hi.y + f.R) * f.sx, 65535.f) << 16);
+  q.hi_zt = q_hi((hi.z + f.R) * f.sz, 32767.f) | (q_hi(hi.w * f.st, 131071.f) << 15);
   return q;
+}
+
+// a <= b in both fields of a z | t << 15 word
+__device__ __forceinline__ bool zt_le(uint32_t a, uint32_t b) {
+  return (a & 0x7fffu) <= (b & 0x7fffu) && (a >> 15) <= (b >> 15);
 }
 
 __device__ inline uint32_t quantize(float u, int bits) {

@@ -370,14 +370,13 @@ __device__ __forceinline__ void test_children(const TravArgs &a, const QBox &q, 
   const uint2 lk = __ldg(a.qlink + node);
   const uint32_t g = lk.x & kQIndex;
   cl = (int32_t)g;
-  // per 16-bit lane: child lo <= query hi and query lo <= child hi
-  const uint32_t ml = __vcmpleu2(bl.x, q.hi_xy) & __vcmpleu2(q.lo_xy, bl.z) &
-                      __vcmpleu2(bl.y, q.hi_zt) & __vcmpleu2(q.lo_zt, bl.w);
-  const uint32_t mr = __vcmpleu2(br.x, q.hi_xy) & __vcmpleu2(q.lo_xy, br.z) &
-                      __vcmpleu2(br.y, q.hi_zt) & __vcmpleu2(q.lo_zt, br.w);
+  // child lo <= query hi and query lo <= child hi: x, y per 16-bit lane,
+  // then the z and tick fields
+  const uint32_t ml = __vcmpleu2(bl.x, q.hi_xy) & __vcmpleu2(q.lo_xy, bl.z);
+  const uint32_t mr = __vcmpleu2(br.x, q.hi_xy) & __vcmpleu2(q.lo_xy, br.z);
   // only subtrees whose rightmost leaf lies after the query's own leaf
-  gl = (int64_t)g > p && ml == 0xffffffffu;
-  gr = (int64_t)lk.y > p && mr == 0xffffffffu;
+  gl = (int64_t)g > p && ml == 0xffffffffu && zt_le(bl.y, q.hi_zt) && zt_le(q.lo_zt, bl.w);
+  gr = (int64_t)lk.y > p && mr == 0xffffffffu && zt_le(br.y, q.hi_zt) && zt_le(q.lo_zt, br.w);
   hl = gl && (lk.x & kQLeftLeaf);
   hr = gr && (lk.x & kQRightLeaf);
   gl &= !hl;
