@@ -136,9 +136,12 @@ typedef struct {
   int use_graph;      /* 1: replay find_pairs as one captured CUDA graph    */
   int space_warp;     /* 1: log-compress |x| before quantising (finer keys
                          near Earth, where most boxes are); 0: linear      */
-  int nodes_per_step; /* one box per leaf: tree nodes each lane visits per
-                         traversal step (two independent loads in flight),
-                         1 or 2                                            */
+  int nodes_per_step; /* one box per leaf, node width 2: tree nodes each
+                         lane visits per traversal step (two independent
+                         loads in flight), 1 or 2                          */
+  int node_width;     /* one box per leaf: 2 (binary nodes, 40 bytes) or 4
+                         (the grandchildren of a binary node in one 128-byte
+                         line: one traversal step descends two levels)     */
 } scd_tuning;
 
 typedef struct scd_scene scd_scene;

@@ -58,7 +58,8 @@ class scd_tuning(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("stack_depth", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("morton_bits", ctypes.c_int),
                 ("time_scale", ctypes.c_float), ("use_graph", ctypes.c_int),
-                ("space_warp", ctypes.c_int), ("nodes_per_step", ctypes.c_int)]
+                ("space_warp", ctypes.c_int), ("nodes_per_step", ctypes.c_int),
+                ("node_width", ctypes.c_int)]
 
 
 PAIR_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("tlo", "<i4"), ("thi", "<i4")])

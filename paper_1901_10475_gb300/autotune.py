@@ -5,8 +5,8 @@ the scene's stream for candidate tunings, keeps the fastest, and caches the
 choice in a JSON file keyed by GPU name, a hash of the workload and log2 of
 the box count.  A staged search: leaf size x Morton bits x space warp
 first, then the time weight, the stack depth and the block shape (leaves of
-several boxes) or the nodes per traversal step (one box per leaf) around
-the winner.
+several boxes) or the nodes per traversal step and the node width (one box
+per leaf) around the winner.
 """
 from __future__ import annotations
 
@@ -82,7 +82,7 @@ def tune(scene, reps: int = 2, verbose: bool = False, decomp=None):
     if best["leaf_size"] > 1:
         stage2 += [dict(best, block_threads=bt) for bt in (64, 256)]
     else:
-        stage2 += [dict(best, nodes_per_step=1)]
+        stage2 += [dict(best, nodes_per_step=1), dict(best, node_width=4)]
     for cand in stage2:
         ms = run(cand)
         if ms < best_ms:

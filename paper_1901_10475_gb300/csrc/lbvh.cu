@@ -99,7 +99,8 @@ __global__ void k_karras(const K *__restrict__ keys, int64_t M, TravNode *__rest
   lk.w = (int32_t)last;
   reinterpret_cast<int4 *>(nodes + i)[4] = lk;
   if (first == gamma) parent_leaf[gamma] = (int32_t)i; else parent_int[gamma] = (int32_t)i;
-  if (last == gamma + 1) parent_leaf[gamma + 1] = (int32_t)i; else parent_int[gamma + 1] = (int32_t)i;
+  if (last == gamma + 1) parent_leaf[gamma + 1] = (int32_t)i;
+  else parent_int[gamma + 1] = (int32_t)i | kRightChildBit;
   if (i == 0) parent_int[0] = -1;
   flags[i] = 0;
   if (first_out) first_out[i] = (int32_t)first;
@@ -121,7 +122,8 @@ __global__ void k_refit(const SBox *__restrict__ sbox, int64_t N, int L, int64_t
                         float4 *__restrict__ nhi, const int32_t *__restrict__ parent_int,
                         const int32_t *__restrict__ parent_leaf, uint32_t *__restrict__ flags,
                         QBox *__restrict__ qbox, uint2 *__restrict__ qlink,
-                        const DevCounters *__restrict__ ctr, int64_t T) {
+                        W4Node *__restrict__ w4, const DevCounters *__restrict__ ctr,
+                        int64_t T) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= M) return;
   const QFrame fr = scene_frame(ctr, T);
@@ -170,7 +172,37 @@ __global__ void k_refit(const SBox *__restrict__ sbox, int64_t N, int L, int64_t
       rlo = __ldcg(nlo + lk.y);
       rhi = __ldcg(nhi + lk.y);
     }
-    if (qbox) {
+    const int32_t up = parent_int[p];  // -1 at the root; bit 30: p is a right child
+    if (w4) {
+      // four-wide nodes: p's children go into its parent's node (slots 0-1
+      // or 2-3 by p's side), p's leaf children into p's own node
+      const QBox ql = quantize_box(fr, llo, lhi), qr = quantize_box(fr, rlo, rhi);
+      const uint32_t g = (uint32_t)lk.z;
+      const uint2 linkl = make_uint2(g | ((lk.x & kLeafBit) ? kW4Leaf : 0u), g);
+      const uint2 linkr = make_uint2((g + 1) | ((lk.y & kLeafBit) ? kW4Leaf : 0u), (uint32_t)lk.w);
+      if (up >= 0) {
+        W4Node &pn = w4[up & ~kRightChildBit];
+        const int s = (up & kRightChildBit) ? 2 : 0;
+        pn.box[s] = ql;
+        pn.box[s + 1] = qr;
+        pn.link[s] = linkl;
+        pn.link[s + 1] = linkr;
+      }
+      const QBox empty = {0xffffffffu, 0xffffffffu, 0u, 0u};
+      const uint2 none = make_uint2(kW4Empty, 0u);
+      if (lk.x & kLeafBit) {
+        w4[p].box[0] = ql;
+        w4[p].link[0] = linkl;
+        w4[p].box[1] = empty;
+        w4[p].link[1] = none;
+      }
+      if (lk.y & kLeafBit) {
+        w4[p].box[2] = qr;
+        w4[p].link[2] = make_uint2((g + 1) | kW4Leaf, g + 1);
+        w4[p].box[3] = empty;
+        w4[p].link[3] = none;
+      }
+    } else if (qbox) {
       qbox[2 * p] = quantize_box(fr, llo, lhi);
       qbox[2 * p + 1] = quantize_box(fr, rlo, rhi);
       uint32_t g = (uint32_t)lk.z;  // the split: left child gamma, right gamma + 1
@@ -185,7 +217,7 @@ __global__ void k_refit(const SBox *__restrict__ sbox, int64_t N, int L, int64_t
     }
     __stcg(nlo + p, f4min(llo, rlo));
     __stcg(nhi + p, f4max(lhi, rhi));
-    p = parent_int[p];
+    p = up >= 0 ? (up & ~kRightChildBit) : -1;
   }
 }
 
@@ -203,9 +235,11 @@ int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, i
     return SCD_ERR_OOM;
   const bool compact = L == 1;
   const bool cells = cell_shift >= 0;
-  if (compact && (!s->d_qbox.ensure(2 * (M > 1 ? M - 1 : 1), st) ||
-                  !s->d_qlink.ensure(M > 1 ? M - 1 : 1, st)))
+  const bool wide = compact && s->tune.node_width == 4;
+  if (compact && !wide && (!s->d_qbox.ensure(2 * (M > 1 ? M - 1 : 1), st) ||
+                           !s->d_qlink.ensure(M > 1 ? M - 1 : 1, st)))
     return SCD_ERR_OOM;
+  if (wide && !s->d_w4.ensure(M > 1 ? M - 1 : 1, st)) return SCD_ERR_OOM;
   if (compact && (!s->d_posof.ensure(s->N, st) || !s->s_nb.ensure(Nq, st))) return SCD_ERR_OOM;
   if (cells && (!s->s_cell.ensure(Nq, st) || !s->d_first.ensure(M > 1 ? M - 1 : 1, st)))
     return SCD_ERR_OOM;
@@ -229,7 +263,8 @@ int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, i
   k_refit<<<(unsigned)((M + bs - 1) / bs), bs, 0, st>>>(
       s->s_box.p, Nq, L, M, s->d_leaflo.p, s->d_leafhi.p, s->d_nodes.p, s->d_nlo.p,
       s->d_nhi.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p,
-      compact ? s->d_qbox.p : nullptr, compact ? s->d_qlink.p : nullptr, s->d_ctr.p, s->T);
+      compact && !wide ? s->d_qbox.p : nullptr, compact && !wide ? s->d_qlink.p : nullptr,
+      wide ? s->d_w4.p : nullptr, s->d_ctr.p, s->T);
   return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
 }
 

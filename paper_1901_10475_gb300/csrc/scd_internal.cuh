@@ -96,6 +96,24 @@ struct __align__(16) QBox {
 constexpr uint32_t kQLeftLeaf = 0x80000000u, kQRightLeaf = 0x40000000u;
 constexpr uint32_t kQIndex = 0x3fffffffu;
 
+// Four-wide node (one box per leaf, node width 4): the grandchildren of a
+// binary node in one 128-byte line.  Slots 0 and 1 hold the two children of
+// the left child (or the left child itself when it is a leaf, and an empty
+// slot), slots 2 and 3 those of the right child.  link.x = binary node or
+// leaf index with flags, link.y = the slot's rightmost leaf (0 when empty).
+// One traversal step reads the line with three 256-bit loads and descends
+// two binary levels.
+struct __align__(128) W4Node {
+  QBox box[4];
+  uint2 link[4];
+  uint32_t pad[8];
+};
+static_assert(sizeof(W4Node) == 128, "one cache line per four-wide node");
+constexpr uint32_t kW4Leaf = 0x80000000u, kW4Empty = 0x40000000u, kW4Index = 0x3fffffffu;
+// the right-child bit of a parent link (the Karras build marks which side
+// of its parent each internal node is)
+constexpr int32_t kRightChildBit = 0x40000000;
+
 // A sorted box: both corners in one 32-byte record (x, y, z in km, the tick
 // in w), read with one 256-bit load.
 struct __align__(32) SBox {
@@ -113,6 +131,12 @@ __device__ __forceinline__ void ldg_box(const SBox *p, float4 &lo, float4 &hi) {
 __device__ __forceinline__ void ldg_qbox_pair(const QBox *p, uint4 &l, uint4 &r) {
   asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
       : "=r"(l.x), "=r"(l.y), "=r"(l.z), "=r"(l.w), "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p));
+}
+// the four links of a four-wide node
+__device__ __forceinline__ void ldg_w4_links(const uint2 *p, uint4 &a, uint4 &b) {
+  asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
       : "l"(p));
 }
 
@@ -401,6 +425,7 @@ struct scd_scene {
   scd::DevBuf<unsigned long long> s_leafkey64;
   scd::DevBuf<scd::TravNode> d_nodes;
   scd::DevBuf<scd::QBox> d_qbox;     // 2 per internal node (one box per leaf)
+  scd::DevBuf<scd::W4Node> d_w4;     // four-wide nodes (node width 4)
   scd::DevBuf<uint2> d_qlink;        // per internal node: gamma | flags, last_r
   scd::DevBuf<float4> d_nlo, d_nhi;     // internal node boxes (refit)
   scd::DevBuf<float4> d_leaflo, d_leafhi;

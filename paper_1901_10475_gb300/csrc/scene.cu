@@ -78,6 +78,7 @@ extern "C" SCD_API int scd_default_tuning(scd_tuning *t) {
   t->use_graph = 0;
   t->space_warp = 0;
   t->nodes_per_step = 2;
+  t->node_width = 2;
   return SCD_OK;
 }
 
@@ -90,7 +91,8 @@ static bool tuning_ok(const scd_tuning *t) {
   bool ts = t->time_scale > 0.0f && t->time_scale <= 1.0f;
   bool sw = t->space_warp == 0 || t->space_warp == 1;
   bool ns = t->nodes_per_step == 1 || t->nodes_per_step == 2;
-  return leaf && st && bs && mb && ts && sw && ns;
+  bool nw = t->node_width == 2 || t->node_width == 4;
+  return leaf && st && bs && mb && ts && sw && ns && nw;
 }
 
 static bool element_ok(const scd_element &x) {
@@ -430,7 +432,8 @@ static void graph_key_of(const scd_scene *s, int64_t key[8]) {
   key[1] = s->n_slabs * 100000 + s->p_bands;
   key[2] = s->N;
   key[3] = s->pair_cap;
-  key[4] = s->tune.leaf_size * 1000 + s->tune.stack_depth;
+  key[4] = (s->tune.node_width * 10 + s->tune.nodes_per_step) * 100000 +
+           s->tune.leaf_size * 1000 + s->tune.stack_depth;
   key[5] = s->tune.morton_bits * 10 + s->tune.space_warp;
   key[6] = (int64_t)(s->tune.time_scale * 1e6f);
   key[7] = s->dkind ? s->n_refs : 0;
@@ -695,7 +698,7 @@ extern "C" SCD_API void scd_scene_destroy(scd_scene *s) {
   s->d_posof.release(st); s->s_nb.release(st);
   s->s_leafkey32.release(st); s->s_leafkey64.release(st);
   s->d_nodes.release(st); s->d_nlo.release(st); s->d_nhi.release(st);
-  s->d_qbox.release(st); s->d_qlink.release(st);
+  s->d_qbox.release(st); s->d_qlink.release(st); s->d_w4.release(st);
   s->d_leaflo.release(st); s->d_leafhi.release(st);
   s->d_parent_int.release(st); s->d_parent_leaf.release(st); s->d_flags.release(st);
   s->d_first_last.release(st);

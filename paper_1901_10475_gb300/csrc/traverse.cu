@@ -19,6 +19,7 @@
 // 2 (object bits + tick bits) <= 64 and an all-ones tick field cannot be a
 // tick (the open tag), else it travels as a 32-bit sort value.
 #include <algorithm>
+#include <type_traits>
 
 #include "scd_internal.cuh"
 
@@ -28,6 +29,7 @@ struct TravArgs {
   const TravNode *nodes;
   const QBox *qbox;           // compact nodes (one box per leaf)
   const uint2 *qlink;
+  const W4Node *w4;           // four-wide nodes (one box per leaf, node width 4)
   const SBox *sbox;           // sorted boxes
   const uint32_t *sobj, *sid; // object and unsorted id of each sorted box
   const int2 *nb;             // sorted positions of the previous / next segment
@@ -383,7 +385,16 @@ __device__ __forceinline__ void test_children(const TravArgs &a, const QBox &q, 
   gr &= !hr;
 }
 
-template <int kDepth, bool kTwo>
+// one slot of a four-wide node: it meets the quantised query and its
+// rightmost leaf lies after the query's own leaf (empty slots: leaf 0)
+__device__ __forceinline__ bool w4_slot(const QBox &q, int64_t p, const uint4 &b, uint32_t last) {
+  return (int64_t)last > p &&
+         (__vcmpleu2(b.x, q.hi_xy) & __vcmpleu2(q.lo_xy, b.z)) == 0xffffffffu &&
+         zt_le(b.y, q.hi_zt) && zt_le(q.lo_zt, b.w);
+}
+
+// kTwo: two binary nodes per lane and step; kW4: four-wide nodes
+template <int kDepth, bool kTwo, bool kW4>
 __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
   __shared__ uint2 hits[kT2Warps][kHitCap];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -478,36 +489,58 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
     const uint32_t pq = (uint32_t)p;  // this step's query, before p may end
     bool hl = false, hr = false, hl2 = false, hr2 = false;
     int32_t cl = 0, cl2 = 0;
-    if (active) {
-      if (kTwo && node2 < 0 && sp > sb) node2 = stack[--sp];
-      bool gl, gr, gl2 = false, gr2 = false;
-      test_children(a, q, p, node, gl, gr, hl, hr, cl);
-      if (kTwo && node2 >= 0) {
-        test_children(a, q, p, node2, gl2, gr2, hl2, hr2, cl2);
-        nt += 2;
+    // the subtrees to visit next: the first one (two) are this lane's next
+    // node(s), the rest go on the stack
+    int32_t first = -1, second = -1;
+    bool overflow = false;
+    auto take = [&](bool go, int32_t c) {
+      if (!go) return;
+      if (first < 0) {
+        first = c;
+      } else if (kTwo && second < 0) {
+        second = c;
+      } else if (sp < kDepth) {
+        stack[sp++] = c;
+      } else {
+        overflow = true;
       }
-      nt += 2;
-      // the subtrees to visit next: the first two are this lane's next
-      // nodes, the rest go on the stack
-      int32_t first = -1, second = -1;
-      bool overflow = false;
-      auto take = [&](bool go, int32_t c) {
-        if (!go) return;
-        if (first < 0) {
-          first = c;
-        } else if (kTwo && second < 0) {
-          second = c;
-        } else if (sp < kDepth) {
-          stack[sp++] = c;
-        } else {
-          overflow = true;
+    };
+    // four-wide: the leaf slots that pass, with their leaf indices
+    bool h4[4] = {false, false, false, false};
+    uint32_t c4[4] = {0u, 0u, 0u, 0u};
+    if (active) {
+      if constexpr (kW4) {
+        const W4Node *nd = a.w4 + node;
+        uint4 b0, b1, b2, b3, la, lb;
+        ldg_qbox_pair(nd->box, b0, b1);
+        ldg_qbox_pair(nd->box + 2, b2, b3);
+        ldg_w4_links(nd->link, la, lb);
+        nt += 4;
+        const uint32_t lx[4] = {la.x, la.z, lb.x, lb.z};
+        const bool ok[4] = {w4_slot(q, p, b0, la.y), w4_slot(q, p, b1, la.w),
+                            w4_slot(q, p, b2, lb.y), w4_slot(q, p, b3, lb.w)};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const bool leaf = (lx[k] & kW4Leaf) != 0u;
+          h4[k] = ok[k] && leaf;
+          c4[k] = lx[k] & kW4Index;
+          take(ok[k] && !leaf, (int32_t)c4[k]);
         }
-      };
-      take(gl, cl);
-      take(gr, cl + 1);
-      if (kTwo) {
-        take(gl2, cl2);
-        take(gr2, cl2 + 1);
+      } else {
+        if (kTwo && node2 < 0 && sp > sb) node2 = stack[--sp];
+        bool gl, gr, gl2 = false, gr2 = false;
+        test_children(a, q, p, node, gl, gr, hl, hr, cl);
+        if (kTwo && node2 >= 0) {
+          test_children(a, q, p, node2, gl2, gr2, hl2, hr2, cl2);
+          nt += 2;
+        }
+        nt += 2;
+        take(gl, cl);
+        take(gr, cl + 1);
+        if (kTwo) {
+          take(gl2, cl2);
+          take(gr2, cl2 + 1);
+        }
       }
       if (overflow) {
         atomicOr(&a.ctr->trav_flags, ERR_STACK);
@@ -528,14 +561,19 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
       if (h) buf[nhit + __popc(v & lt)] = make_uint2(pq, (uint32_t)c);
       nhit += __popc(v);
     };
-    append(hl, cl);
-    append(hr, cl + 1);
-    if (kTwo) {
-      append(hl2, cl2);
-      append(hr2, cl2 + 1);
+    if constexpr (kW4) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) append(h4[k], (int32_t)c4[k]);
+    } else {
+      append(hl, cl);
+      append(hr, cl + 1);
+      if (kTwo) {
+        append(hl2, cl2);
+        append(hr2, cl2 + 1);
+      }
     }
     __syncwarp();
-    if (nhit > kHitCap - (kTwo ? 128 : 64)) {
+    if (nhit > kHitCap - (kTwo || kW4 ? 128 : 64)) {
       drain_hits(a, buf, nhit, we);
       __syncwarp();
       ntests += nhit;  // exact box tests, counted once per warp
@@ -562,12 +600,14 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
 }
 
 // persistent: as many blocks as fit on the GPU at once
-template <int kDepth, bool kTwo>
+template <int kDepth, bool kTwo, bool kW4>
 static void launch_t2(const TravArgs &a, int sms, cudaStream_t st) {
   static int per_sm = 0;
-  if (!per_sm) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse2<kDepth, kTwo>,
-                                                             kT2Threads, 0);
-  k_traverse2<kDepth, kTwo><<<(unsigned)(sms * std::max(per_sm, 1)), kT2Threads, 0, st>>>(a);
+  if (!per_sm)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_traverse2<kDepth, kTwo, kW4>,
+                                                  kT2Threads, 0);
+  k_traverse2<kDepth, kTwo, kW4><<<(unsigned)(sms * std::max(per_sm, 1)), kT2Threads, 0, st>>>(
+      a);
 }
 
 int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_bits) {
@@ -575,6 +615,7 @@ int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_b
   a.nodes = s->d_nodes.p;
   a.qbox = s->d_qbox.p;
   a.qlink = s->d_qlink.p;
+  a.w4 = s->d_w4.p;
   a.sbox = s->s_box.p;
   a.sobj = s->s_obj.p;
   a.nb = s->s_nb.p;
@@ -611,17 +652,18 @@ int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_b
     // persistent: as many blocks as fit on the GPU at once
     static int sms = 0;
     if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
-    const bool two = s->tune.nodes_per_step == 2;
+    const bool two = s->tune.nodes_per_step == 2, w4 = s->tune.node_width == 4;
+    if (w4 && (reinterpret_cast<uintptr_t>(a.w4) & 127)) return SCD_ERR_INTERNAL;
+    auto go = [&](auto depth) {
+      constexpr int D = decltype(depth)::value;
+      if (w4) launch_t2<D, false, true>(a, sms, s->stream);
+      else if (two) launch_t2<D, true, false>(a, sms, s->stream);
+      else launch_t2<D, false, false>(a, sms, s->stream);
+    };
     switch (s->tune.stack_depth) {
-      case 32:
-        two ? launch_t2<32, true>(a, sms, s->stream) : launch_t2<32, false>(a, sms, s->stream);
-        break;
-      case 128:
-        two ? launch_t2<128, true>(a, sms, s->stream) : launch_t2<128, false>(a, sms, s->stream);
-        break;
-      default:
-        two ? launch_t2<64, true>(a, sms, s->stream) : launch_t2<64, false>(a, sms, s->stream);
-        break;
+      case 32: go(std::integral_constant<int, 32>()); break;
+      case 128: go(std::integral_constant<int, 128>()); break;
+      default: go(std::integral_constant<int, 64>()); break;
     }
     note_launch();
     return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;

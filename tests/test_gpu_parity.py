@@ -168,7 +168,8 @@ def test_tunings_give_identical_sets(scd, leaf, bits):
     pol = scd.make_step_policy(scd.SCD_STEP_FIXED, fixed_ticks=7)
     tuning = dict(leaf_size=leaf, morton_bits=bits, stack_depth=32, block_threads=64,
                   space_warp=int(bits == 10), time_scale=0.5 if bits == 16 else 1.0,
-                  nodes_per_step=1 if bits == 10 else 2)
+                  nodes_per_step=1 if bits == 10 else 2,
+                  node_width=4 if leaf == 1 and bits != 10 else 2)
     _screen_parity(scd, els, 1500, pol, tuning=tuning, raw_too=(leaf == 4))
 
 
