@@ -116,6 +116,7 @@ __device__ __forceinline__ float4 f4max(float4 a, float4 b) {
 // Bottom-up union.  The second thread to reach a node (atomic arrival count)
 // reads both children and goes on; the first one stops.  Nobody waits.
 // With one box per leaf the sorted boxes are the leaf boxes.
+template <bool kWide>
 __global__ void k_refit(const SBox *__restrict__ sbox, int64_t N, int L, int64_t M,
                         float4 *__restrict__ leaflo, float4 *__restrict__ leafhi,
                         TravNode *__restrict__ nodes, float4 *__restrict__ nlo,
@@ -173,7 +174,7 @@ __global__ void k_refit(const SBox *__restrict__ sbox, int64_t N, int L, int64_t
       rhi = __ldcg(nhi + lk.y);
     }
     const int32_t up = parent_int[p];  // -1 at the root; bit 30: p is a right child
-    if (w4) {
+    if constexpr (kWide) {
       // four-wide nodes: p's children go into its parent's node (slots 0-1
       // or 2-3 by p's side), p's leaf children into p's own node
       const QBox ql = quantize_box(fr, llo, lhi), qr = quantize_box(fr, rlo, rhi);
@@ -260,7 +261,7 @@ int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, i
         cells ? s->d_first.p : nullptr);
     note_launch();
   }
-  k_refit<<<(unsigned)((M + bs - 1) / bs), bs, 0, st>>>(
+  (wide ? k_refit<true> : k_refit<false>)<<<(unsigned)((M + bs - 1) / bs), bs, 0, st>>>(
       s->s_box.p, Nq, L, M, s->d_leaflo.p, s->d_leafhi.p, s->d_nodes.p, s->d_nlo.p,
       s->d_nhi.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p,
       compact && !wide ? s->d_qbox.p : nullptr, compact && !wide ? s->d_qlink.p : nullptr,
