@@ -76,6 +76,7 @@ def lib():
                 "or_canonicalize": (i64, [vp, i64]),
                 "or_alg1_witnesses": (i64, [vp, i64, i64, d, vp, i64]),
                 "or_alg1_sweep": (i64, [vp, i64, i64, i64, d, vp, vp, i64]),
+                "or_raw_cells_tree": (i64, [vp, vp, vp, i64, vp, i64]),
                 "or_alg3": (i32, [vp, i64, i64, d, i32, i64, vp, vp, vp, vp]),
                 "or_radial_range": (None, [vp, vp]),
                 "or_band_edges": (None, [vp, i64, i32, vp]),
@@ -252,6 +253,15 @@ def raw_cells_bruteforce(lo4, hi4, obj):
     hi4 = np.ascontiguousarray(hi4, np.float32)
     obj = np.ascontiguousarray(obj, np.uint32)
     return _cells_call(lib().or_raw_cells_bruteforce, _p(lo4), _p(hi4), _p(obj), len(obj))
+
+
+def raw_cells_tree(lo4, hi4, obj):
+    """Every overlapping box pair of different objects, through the paper's
+    incrementally built AABB tree (Sec. 3.2)."""
+    lo4 = np.ascontiguousarray(lo4, np.float32)
+    hi4 = np.ascontiguousarray(hi4, np.float32)
+    obj = np.ascontiguousarray(obj, np.uint32)
+    return _cells_call(lib().or_raw_cells_tree, _p(lo4), _p(hi4), _p(obj), len(obj))
 
 
 def raw_cells_sweep(lo4, hi4, obj):

@@ -349,6 +349,139 @@ int64_t or_raw_cells_bruteforce(const float *lo4, const float *hi4,
   return c;
 }
 
+/* ------------------------------------------------------------------------ */
+/* The paper's data structure (Sec. 3.2): an AABB tree built by incremental  */
+/* insert under a surface-area heuristic, answering "which boxes meet this  */
+/* box" by descending from the root.  Nodes link by index (parent, two      */
+/* children); leaves carry a box index.  In 4D the "surface area" of a box  */
+/* with extents a, b, c, d is the 3-volume of its boundary,                 */
+/* 2 (abc + abd + acd + bcd).  Insertion descends to the sibling that the   */
+/* heuristic prefers and refits the ancestors; no rotations (optional in    */
+/* the paper), which changes the tree's shape, never its answers.           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double lo[4], hi[4];
+  int64_t parent, c0, c1; /* -1: none; a leaf has no children */
+  int64_t box;            /* leaf: the box index */
+} or_tnode;
+
+typedef struct {
+  or_tnode *n;
+  int64_t count, root;
+} or_tree;
+
+static double tsurface(const double *lo, const double *hi) {
+  double a = hi[0] - lo[0], b = hi[1] - lo[1], c = hi[2] - lo[2], d = hi[3] - lo[3];
+  return 2.0 * (a * b * c + a * b * d + a * c * d + b * c * d);
+}
+
+static double tsurface_union(const or_tnode *x, const double *lo, const double *hi) {
+  double ul[4], uh[4];
+  for (int k = 0; k < 4; ++k) {
+    ul[k] = x->lo[k] < lo[k] ? x->lo[k] : lo[k];
+    uh[k] = x->hi[k] > hi[k] ? x->hi[k] : hi[k];
+  }
+  return tsurface(ul, uh);
+}
+
+static void tunion_into(or_tnode *dst, const or_tnode *a, const or_tnode *b) {
+  for (int k = 0; k < 4; ++k) {
+    dst->lo[k] = a->lo[k] < b->lo[k] ? a->lo[k] : b->lo[k];
+    dst->hi[k] = a->hi[k] > b->hi[k] ? a->hi[k] : b->hi[k];
+  }
+}
+
+static void tree_insert(or_tree *t, const float *lo4, const float *hi4, int64_t box) {
+  int64_t leaf = t->count++;
+  or_tnode *L = t->n + leaf;
+  for (int k = 0; k < 4; ++k) {
+    L->lo[k] = lo4[4 * box + k];
+    L->hi[k] = hi4[4 * box + k];
+  }
+  L->parent = L->c0 = L->c1 = -1;
+  L->box = box;
+  if (t->root < 0) {
+    t->root = leaf;
+    return;
+  }
+  /* descend: pairing with node x costs its union's surface; going below x
+   * adds the growth of x to whatever the child costs */
+  int64_t x = t->root;
+  while (t->n[x].c0 >= 0) {
+    or_tnode *X = t->n + x;
+    double here = tsurface_union(X, L->lo, L->hi);
+    double grow = here - tsurface(X->lo, X->hi);
+    double cost[2];
+    for (int c = 0; c < 2; ++c) {
+      const or_tnode *C = t->n + (c ? X->c1 : X->c0);
+      double u = tsurface_union(C, L->lo, L->hi);
+      cost[c] = grow + (C->c0 >= 0 ? u - tsurface(C->lo, C->hi) : u);
+    }
+    if (here <= cost[0] && here <= cost[1]) break;
+    x = cost[0] <= cost[1] ? X->c0 : X->c1;
+  }
+  /* a new parent for x and the leaf */
+  int64_t np = t->count++;
+  or_tnode *P = t->n + np;
+  int64_t old = t->n[x].parent;
+  P->parent = old;
+  P->c0 = x;
+  P->c1 = leaf;
+  P->box = -1;
+  tunion_into(P, t->n + x, L);
+  t->n[x].parent = np;
+  L->parent = np;
+  if (old < 0) {
+    t->root = np;
+  } else if (t->n[old].c0 == x) {
+    t->n[old].c0 = np;
+  } else {
+    t->n[old].c1 = np;
+  }
+  /* refit the ancestors */
+  for (int64_t a = old; a >= 0; a = t->n[a].parent)
+    tunion_into(t->n + a, t->n + t->n[a].c0, t->n + t->n[a].c1);
+}
+
+static int tnode_meets(const or_tnode *x, const float *lo, const float *hi) {
+  for (int k = 0; k < 4; ++k)
+    if (x->lo[k] > (double)hi[k] || (double)lo[k] > x->hi[k]) return 0;
+  return 1;
+}
+
+int64_t or_raw_cells_tree(const float *lo4, const float *hi4, const uint32_t *obj, int64_t N,
+                          or_cell *out, int64_t cap) {
+  or_tree t;
+  t.n = (or_tnode *)malloc(sizeof(or_tnode) * (size_t)(2 * N + 1));
+  t.count = 0;
+  t.root = -1;
+  for (int64_t b = 0; b < N; ++b) tree_insert(&t, lo4, hi4, b);
+  int64_t *stack = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * N + 1));
+  int64_t c = 0;
+  for (int64_t a = 0; a < N && t.root >= 0; ++a) {
+    const float *ql = lo4 + 4 * a, *qh = hi4 + 4 * a;
+    int64_t sp = 0;
+    stack[sp++] = t.root;
+    while (sp > 0) {
+      const or_tnode *x = t.n + stack[--sp];
+      if (!tnode_meets(x, ql, qh)) continue;
+      if (x->c0 >= 0) {
+        stack[sp++] = x->c0;
+        stack[sp++] = x->c1;
+        continue;
+      }
+      int64_t b = x->box; /* each pair once, from its lower box index */
+      if (b <= a || obj[a] == obj[b]) continue;
+      if (c < cap) make_cell(lo4, hi4, obj, a, b, out + c);
+      ++c;
+    }
+  }
+  free(stack);
+  free(t.n);
+  return c;
+}
+
 static const float *g_sort_lo;
 static int cmp_by_tlo(const void *x, const void *y) {
   int64_t a = *(const int64_t *)x, b = *(const int64_t *)y;

@@ -97,6 +97,11 @@ int64_t or_raw_cells_selected(const float *lo4, const float *hi4,
                               const uint8_t *sel, or_cell *out, int64_t cap);
 /* sort by (i,j,tlo,thi) and merge intervals of one (i,j) that overlap or
  * touch (next.tlo <= cur.thi + 1).  In place; returns the new length. */
+/* The same cell set as or_raw_cells_bruteforce, found through an AABB tree
+ * built by incremental insertion under a surface-area heuristic (Sec. 3.2);
+ * cells come in query order. */
+int64_t or_raw_cells_tree(const float *lo4, const float *hi4, const uint32_t *obj, int64_t N,
+                          or_cell *out, int64_t cap);
 int64_t or_canonicalize(or_cell *cells, int64_t n);
 
 /* --- the paper's algorithms ---------------------------------------------- */

@@ -159,6 +159,11 @@ def test_config1_uniform_leo_pair_set_bit_exact(scd):
     pol = scd.make_step_policy(scd.SCD_STEP_FIXED, fixed_ticks=10)
     got, m = _screen_parity(scd, els, 6000, pol)
     assert m["boxes"] == 512 * 601
+    # the second oracle: the paper's incrementally built AABB tree
+    sc = scd.Scene(els, 6000.0, 1.0, pol).build_boxes()
+    lo, hi, obj = _host_boxes(sc)
+    sc.close()
+    assert _same(got, O.canonicalize(O.raw_cells_tree(lo, hi, obj)))
 
 
 @pytest.mark.parametrize("leaf", [1, 2, 4, 8])

@@ -175,3 +175,27 @@ def test_close_approaches_find_the_seeded_crossings():
     want = one[one["dist"] < 5.0]
     key = lambda w: sorted(zip(w["i"].tolist(), w["j"].tolist(), w["t"].tolist()))
     assert key(got) == key(want)
+
+
+def _keys(c):
+    return sorted(zip(c["i"].tolist(), c["j"].tolist(), c["tlo"].tolist(), c["thi"].tolist()))
+
+
+@pytest.mark.parametrize("seed,radius", [(4, 60.0), (5, 250.0), (6, 10.0)])
+def test_aabb_tree_equals_bruteforce(seed, radius):
+    """The paper's incrementally built AABB tree (Sec. 3.2) finds exactly the
+    brute-force set of overlapping box pairs, from sparse to crowded."""
+    els = P.uniform_leo(120, seed=seed, radius_km=radius)
+    k = O.step_ticks(els, O.STEP_FIXED, 1.0, fixed_ticks=10)
+    lo, hi, obj = O.boxes(els, 1200, 1.0, k)
+    a = O.raw_cells_bruteforce(lo, hi, obj)
+    b = O.raw_cells_tree(lo, hi, obj)
+    assert len(a) > 0 and _keys(a) == _keys(b)
+
+
+def test_aabb_tree_equals_sweep_on_the_small_workload():
+    """n = 512, 6000 s, fixed 10 s steps: 307,712 boxes."""
+    els = P.uniform_leo(512)
+    k = O.step_ticks(els, O.STEP_FIXED, 1.0, fixed_ticks=10)
+    lo, hi, obj = O.boxes(els, 6000, 1.0, k)
+    assert _keys(O.raw_cells_tree(lo, hi, obj)) == _keys(O.raw_cells_sweep(lo, hi, obj))
