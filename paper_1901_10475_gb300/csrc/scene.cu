@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "scd_internal.cuh"
 
@@ -330,6 +331,24 @@ static int find_pairs_impl(scd_scene *s, const scd_decomp *d, int raw_mode) {
 
 // The find sequence run op by op, with host reads of the counters between
 // phases (buffer growth, stack depth, checks).
+// Records per box seen so far, per kind of screen (SPEED runs, INTERVAL
+// runs, raw cells), starting from catalog-shaped measurements (9.4, 1.5, 22)
+// and raised by every screen that needed more; bounded so that one
+// pathological scene cannot make every later scene reserve huge buffers.
+static std::mutex g_slots_mu;
+static double g_slots_per_box[3] = {12.0, 2.0, 24.0};
+
+static double slots_per_box(int kind) {
+  std::lock_guard<std::mutex> lk(g_slots_mu);
+  return g_slots_per_box[kind];
+}
+
+static void note_slots_per_box(int kind, double ratio) {
+  std::lock_guard<std::mutex> lk(g_slots_mu);
+  const double r = std::min(64.0, ratio * 1.125);
+  if (r > g_slots_per_box[kind]) g_slots_per_box[kind] = r;
+}
+
 static int find_eager(scd_scene *s, const scd_decomp *d, int dkind, int raw_mode, int ob, int tb) {
   cudaStream_t st = s->stream;
   int64_t N = s->N;
@@ -354,7 +373,11 @@ static int find_eager(scd_scene *s, const scd_decomp *d, int dkind, int raw_mode
   }
   if (s->events_ready) cudaEventRecord(s->ev[4], st);
   // A8: traversal, retried with more room when the buffers overflow
-  if (s->pair_cap == 0) s->pair_cap = std::max<int64_t>(1 << 16, N / 4);
+  // first guess of the record slots of a new scene: the largest records per
+  // box seen so far in this process for the kind of screen (a scene that
+  // needs more traverses again with the exact count, and raises the guess)
+  const int rkind = raw_mode ? 2 : (s->box_mode == SCD_BOX_INTERVAL ? 1 : 0);
+  if (s->pair_cap == 0) s->pair_cap = std::max<int64_t>(1 << 16, (int64_t)(N * slots_per_box(rkind)));
   bool done = false;
   for (int attempt = 0; attempt < 6 && !done; ++attempt) {
     if (!s->d_starts.ensure(s->pair_cap, st) || (!raw_mode && !s->d_ends.ensure(s->pair_cap, st)) ||
@@ -377,6 +400,7 @@ static int find_eager(scd_scene *s, const scd_decomp *d, int dkind, int raw_mode
     if (need >= (1ull << 32) - 1) return SCD_ERR_CAPACITY;
     if (need <= (unsigned long long)s->pair_cap) done = true;
     else s->pair_cap = (int64_t)(need + need / 8 + 1024);
+    if (N > 0) note_slots_per_box(rkind, (double)need / (double)N);
   }
   if (!done) return SCD_ERR_INTERNAL;
   if (s->h_ctr.build_flags & ERR_INVALID) return SCD_ERR_INVALID_ARG;
