@@ -333,19 +333,25 @@ static int find_pairs_impl(scd_scene *s, const scd_decomp *d, int raw_mode) {
 // phases (buffer growth, stack depth, checks).
 // Records per box seen so far, per kind of screen (SPEED runs, INTERVAL
 // runs, raw cells), starting from catalog-shaped measurements (9.4, 1.5, 22)
-// and raised by every screen that needed more; bounded so that one
-// pathological scene cannot make every later scene reserve huge buffers.
+// and raised by every large screen (2^20 boxes or more, where a second
+// traversal is costly) that needed more; small screens neither learn nor
+// use it, and it stays at most 16, so that small crowded scenes cannot make
+// a later large one reserve huge buffers.
 static std::mutex g_slots_mu;
 static double g_slots_per_box[3] = {12.0, 2.0, 24.0};
+constexpr int64_t kSlotsLearnBoxes = 1 << 20;
 
-static double slots_per_box(int kind) {
+static double slots_per_box(int kind, int64_t N) {
+  static const double base[3] = {12.0, 2.0, 24.0};
+  if (N < kSlotsLearnBoxes) return base[kind];
   std::lock_guard<std::mutex> lk(g_slots_mu);
   return g_slots_per_box[kind];
 }
 
-static void note_slots_per_box(int kind, double ratio) {
+static void note_slots_per_box(int kind, int64_t N, double ratio) {
+  if (N < kSlotsLearnBoxes) return;
   std::lock_guard<std::mutex> lk(g_slots_mu);
-  const double r = std::min(64.0, ratio * 1.125);
+  const double r = std::min(16.0, ratio * 1.125);
   if (r > g_slots_per_box[kind]) g_slots_per_box[kind] = r;
 }
 
@@ -377,7 +383,8 @@ static int find_eager(scd_scene *s, const scd_decomp *d, int dkind, int raw_mode
   // box seen so far in this process for the kind of screen (a scene that
   // needs more traverses again with the exact count, and raises the guess)
   const int rkind = raw_mode ? 2 : (s->box_mode == SCD_BOX_INTERVAL ? 1 : 0);
-  if (s->pair_cap == 0) s->pair_cap = std::max<int64_t>(1 << 16, (int64_t)(N * slots_per_box(rkind)));
+  if (s->pair_cap == 0)
+    s->pair_cap = std::max<int64_t>(1 << 16, (int64_t)(N * slots_per_box(rkind, N)));
   bool done = false;
   for (int attempt = 0; attempt < 6 && !done; ++attempt) {
     if (!s->d_starts.ensure(s->pair_cap, st) || (!raw_mode && !s->d_ends.ensure(s->pair_cap, st)) ||
@@ -400,7 +407,7 @@ static int find_eager(scd_scene *s, const scd_decomp *d, int dkind, int raw_mode
     if (need >= (1ull << 32) - 1) return SCD_ERR_CAPACITY;
     if (need <= (unsigned long long)s->pair_cap) done = true;
     else s->pair_cap = (int64_t)(need + need / 8 + 1024);
-    if (N > 0) note_slots_per_box(rkind, (double)need / (double)N);
+    if (N > 0) note_slots_per_box(rkind, N, (double)need / (double)N);
   }
   if (!done) return SCD_ERR_INTERNAL;
   if (s->h_ctr.build_flags & ERR_INVALID) return SCD_ERR_INVALID_ARG;
