@@ -77,3 +77,24 @@ def test_decomposition_argument_checks(scd):
             sc.find_pairs(bad)
         assert e.value.status == scd._binding.SCD_ERR_INVALID_ARG
     sc.close()
+
+
+@pytest.mark.parametrize("decomp", [None, "slab", "bands"])
+def test_four_wide_nodes_give_the_same_lists(scd, decomp):
+    """Node width 4 (grandchildren in one line, cell subtrees rooted at
+    binary nodes) gives the same lists as binary nodes, plain and
+    decomposed, eagerly and replayed as a CUDA graph."""
+    els = P.catalog_mixture(n=700, seed=44, radius_km=25.0)
+    pol = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=100.0)
+    d = {None: None, "slab": (scd.SCD_DECOMP_SLAB_OCT, 0, 16),
+         "bands": (scd.SCD_DECOMP_ALT_BANDS, 8, 0)}[decomp]
+    ref = scd.Scene(els, 20000.0, 1.0, pol).build_boxes()
+    want = ref.find_pairs(d)
+    ref.close()
+    assert len(want) > 100
+    for graph in (0, 1):
+        sc = scd.Scene(els, 20000.0, 1.0, pol, tuning=dict(node_width=4, use_graph=graph))
+        for _ in range(3):  # a graph is captured on the first call and replayed after
+            sc.build_boxes()
+            assert _same(sc.find_pairs(d), want)
+        sc.close()
