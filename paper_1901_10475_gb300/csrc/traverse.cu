@@ -318,6 +318,9 @@ constexpr int kHitCap = 256;  // per warp; drained when fewer than 64 slots rema
 // queries claimed per warp atomic; small, so that the queries in flight stay
 // a narrow window of the Morton order and their nodes stay in L2
 constexpr unsigned kQueryChunk = 32;
+// a refill can hand out up to 32 queries at once, from the pool's rest and
+// one new chunk: a chunk smaller than a warp would leave lanes without one
+static_assert(kQueryChunk >= 32, "a query chunk covers at least one warp's refill");
 
 struct WarpEmit {
   ChunkCursor s, e;  // start and end record chunks (raw cells use s)
