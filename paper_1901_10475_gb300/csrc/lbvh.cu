@@ -115,14 +115,15 @@ __device__ __forceinline__ float4 f4max(float4 a, float4 b) {
 
 // Bottom-up union.  The second thread to reach a node (atomic arrival count)
 // reads both children and goes on; the first one stops.  Nobody waits.
-// With one box per leaf the sorted boxes are the leaf boxes.
+// With one box per leaf the sorted boxes are the leaf boxes.  This pass
+// serves the float nodes (several boxes per leaf) and the four-wide ones;
+// binary compact nodes take k_refit_q below.
 template <bool kWide>
 __global__ void k_refit(const SBox *__restrict__ sbox, int64_t N, int L, int64_t M,
                         float4 *__restrict__ leaflo, float4 *__restrict__ leafhi,
                         TravNode *__restrict__ nodes, float4 *__restrict__ nlo,
                         float4 *__restrict__ nhi, const int32_t *__restrict__ parent_int,
                         const int32_t *__restrict__ parent_leaf, uint32_t *__restrict__ flags,
-                        QBox *__restrict__ qbox, uint2 *__restrict__ qlink,
                         W4Node *__restrict__ w4, const DevCounters *__restrict__ ctr,
                         int64_t T) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -203,12 +204,6 @@ __global__ void k_refit(const SBox *__restrict__ sbox, int64_t N, int L, int64_t
         w4[p].box[3] = empty;
         w4[p].link[3] = none;
       }
-    } else if (qbox) {
-      qbox[2 * p] = quantize_box(fr, llo, lhi);
-      qbox[2 * p + 1] = quantize_box(fr, rlo, rhi);
-      uint32_t g = (uint32_t)lk.z;  // the split: left child gamma, right gamma + 1
-      uint32_t fl = ((lk.x & kLeafBit) ? kQLeftLeaf : 0u) | ((lk.y & kLeafBit) ? kQRightLeaf : 0u);
-      qlink[p] = make_uint2(g | fl, (uint32_t)lk.w);
     } else {
       float4 *np = reinterpret_cast<float4 *>(nodes + p);
       np[0] = llo;
@@ -218,6 +213,64 @@ __global__ void k_refit(const SBox *__restrict__ sbox, int64_t N, int L, int64_t
     }
     __stcg(nlo + p, f4min(llo, rlo));
     __stcg(nhi + p, f4max(lhi, rhi));
+    p = up >= 0 ? (up & ~kRightChildBit) : -1;
+  }
+}
+
+// the union of two quantised boxes: per field, the lower corner's minimum
+// and the upper corner's maximum (x, y in 16-bit lanes, then z | t << 15)
+__device__ __forceinline__ QBox qbox_union(const QBox &a, const QBox &b) {
+  QBox u;
+  u.lo_xy = __vminu2(a.lo_xy, b.lo_xy);
+  u.hi_xy = __vmaxu2(a.hi_xy, b.hi_xy);
+  u.lo_zt = min(a.lo_zt & 0x7fffu, b.lo_zt & 0x7fffu) | (min(a.lo_zt >> 15, b.lo_zt >> 15) << 15);
+  u.hi_zt = max(a.hi_zt & 0x7fffu, b.hi_zt & 0x7fffu) | (max(a.hi_zt >> 15, b.hi_zt >> 15) << 15);
+  return u;
+}
+
+// The refit of binary compact nodes (one box per leaf) in the quantised
+// frame: a node's quantised box is the union of its children's.  Outward
+// quantisation is monotone per coordinate, so that union equals the
+// quantised union of the exact boxes, bit for bit, at half the bytes per
+// node (16 instead of 32).
+__global__ void k_refit_q(const SBox *__restrict__ sbox, int64_t M,
+                          const TravNode *__restrict__ nodes, QBox *__restrict__ nq,
+                          const int32_t *__restrict__ parent_int,
+                          const int32_t *__restrict__ parent_leaf, uint32_t *__restrict__ flags,
+                          QBox *__restrict__ qbox, uint2 *__restrict__ qlink,
+                          const DevCounters *__restrict__ ctr, int64_t T) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= M || M == 1) return;
+  const QFrame fr = scene_frame(ctr, T);
+  auto child = [&](int32_t link) {
+    if (link & kLeafBit) {
+      const int32_t q = link & ~kLeafBit;
+      return quantize_box(fr, __ldcg(&sbox[q].lo), __ldcg(&sbox[q].hi));
+    }
+    const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(nq + link));
+    return QBox{v.x, v.y, v.z, v.w};
+  };
+  int32_t p = parent_leaf[c];
+  while (p >= 0) {
+    // release this thread's node box, acquire the sibling's (the second
+    // thread to arrive reads both)
+    uint32_t arrived;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                 : "=r"(arrived)
+                 : "l"(flags + p)
+                 : "memory");
+    if (arrived == 0u) return;
+    const int4 lk = __ldcg(reinterpret_cast<const int4 *>(nodes + p) + 4);
+    const QBox ql = child(lk.x), qr = child(lk.y);
+    qbox[2 * p] = ql;
+    qbox[2 * p + 1] = qr;
+    const uint32_t g = (uint32_t)lk.z;  // the split: left child gamma, right gamma + 1
+    const uint32_t fl =
+        ((lk.x & kLeafBit) ? kQLeftLeaf : 0u) | ((lk.y & kLeafBit) ? kQRightLeaf : 0u);
+    qlink[p] = make_uint2(g | fl, (uint32_t)lk.w);
+    const QBox u = qbox_union(ql, qr);
+    __stcg(reinterpret_cast<uint4 *>(nq + p), make_uint4(u.lo_xy, u.lo_zt, u.hi_xy, u.hi_zt));
+    const int32_t up = parent_int[p];
     p = up >= 0 ? (up & ~kRightChildBit) : -1;
   }
 }
@@ -261,11 +314,17 @@ int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, i
         cells ? s->d_first.p : nullptr);
     note_launch();
   }
-  (wide ? k_refit<true> : k_refit<false>)<<<(unsigned)((M + bs - 1) / bs), bs, 0, st>>>(
-      s->s_box.p, Nq, L, M, s->d_leaflo.p, s->d_leafhi.p, s->d_nodes.p, s->d_nlo.p,
-      s->d_nhi.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p,
-      compact && !wide ? s->d_qbox.p : nullptr, compact && !wide ? s->d_qlink.p : nullptr,
-      wide ? s->d_w4.p : nullptr, s->d_ctr.p, s->T);
+  static_assert(sizeof(QBox) == sizeof(float4), "the quantised node boxes use the float ones' buffer");
+  if (compact && !wide) {
+    k_refit_q<<<(unsigned)((M + bs - 1) / bs), bs, 0, st>>>(
+        s->s_box.p, M, s->d_nodes.p, reinterpret_cast<QBox *>(s->d_nlo.p), s->d_parent_int.p,
+        s->d_parent_leaf.p, s->d_flags.p, s->d_qbox.p, s->d_qlink.p, s->d_ctr.p, s->T);
+  } else {
+    (wide ? k_refit<true> : k_refit<false>)<<<(unsigned)((M + bs - 1) / bs), bs, 0, st>>>(
+        s->s_box.p, Nq, L, M, s->d_leaflo.p, s->d_leafhi.p, s->d_nodes.p, s->d_nlo.p,
+        s->d_nhi.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p,
+        wide ? s->d_w4.p : nullptr, s->d_ctr.p, s->T);
+  }
   return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
 }
 
