@@ -182,9 +182,9 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_downsweep(
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t wcnt[kRsWarps][256];  // per warp, per digit
   __shared__ uint32_t scanbuf[256];
-  __shared__ uint32_t gdig[256];    // first global position of each digit
-  __shared__ uint32_t dstart[256];  // first tile position of each digit
-  __shared__ uint32_t gbase[256];   // global position of the tile's first item of each digit
+  __shared__ uint32_t gdig[256];   // first global position of each digit
+  __shared__ uint32_t gbase[256];  // global position of the tile's first item of each digit,
+                                   // less the digit's first tile position (mod 2^32)
 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -263,16 +263,21 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_downsweep(
     }
     __syncthreads();  // every warp's counts are in; the tile buffer is free
 
-    // (c) per digit: exclusive prefix over the warps, then over the digits
+    // (c) per digit: the digit's first tile position (a scan over the
+    // digits), then each warp's first position within it; afterwards
+    // wcnt[w][dg] is warp w's first tile position for digit dg
     {
       uint32_t run = 0;
 #pragma unroll
+      for (int q = 0; q < kRsWarps; ++q) run += wcnt[q][d];
+      uint32_t at = digit_scan_excl(run, scanbuf);
+      gbase[d] -= at;
+#pragma unroll
       for (int q = 0; q < kRsWarps; ++q) {
-        uint32_t c = wcnt[q][d];
-        wcnt[q][d] = run;
-        run += c;
+        const uint32_t c = wcnt[q][d];
+        wcnt[q][d] = at;
+        at += c;
       }
-      dstart[d] = digit_scan_excl(run, scanbuf);
     }
     __syncthreads();
 
@@ -281,7 +286,7 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_downsweep(
     for (int k = 0; k < kRsItems; ++k) {
       if (base + seg + k * 32 + lane < n) {
         uint32_t dg = digit_of(key[k], shift);
-        uint32_t r = dstart[dg] + wcnt[w][dg] + rnk[k];
+        uint32_t r = wcnt[w][dg] + rnk[k];
         kb[r] = key[k];
         if (kVals) vb[r] = val[k];
       }
@@ -293,7 +298,7 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_downsweep(
     for (int r = threadIdx.x; r < cnt; r += kRsThreads) {
       K kk = kb[r];
       uint32_t dg = digit_of(kk, shift);
-      uint32_t pos = gbase[dg] + (uint32_t)r - dstart[dg];
+      uint32_t pos = gbase[dg] + (uint32_t)r;
       kout[pos] = kk;
       if (kVals) vout[pos] = vb[r];
     }
