@@ -62,23 +62,36 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const K *__restrict__
   }
 }
 
-// exclusive scan over one digit's block counts; totals[d] = the digit's count
+// exclusive scan over one digit's block counts; totals[d] = the digit's count.
+// A chunk is 1024 x kScanItems counts: warp w holds a segment of 32 x
+// kScanItems, item k of lane l at k * 32 + l (coalesced), scanned within
+// the warp in registers; one block-wide scan of the warp totals per chunk.
+constexpr int kScanItems = 8;
 __global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *__restrict__ counts, int64_t nblk,
                                                   uint32_t *__restrict__ totals) {
   __shared__ uint32_t ws[32];
   uint32_t *c = counts + (int64_t)blockIdx.x * nblk;
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t carry = 0;
-  for (int64_t b0 = 0; b0 < nblk; b0 += 1024) {
-    int64_t idx = b0 + threadIdx.x;
-    uint32_t v = idx < nblk ? c[idx] : 0u;
-    uint32_t x = v;
+  for (int64_t b0 = 0; b0 < nblk; b0 += 1024 * kScanItems) {
+    const int64_t seg = b0 + (int64_t)w * 32 * kScanItems + lane;
+    uint32_t v[kScanItems];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+    for (int k = 0; k < kScanItems; ++k) v[k] = seg + k * 32 < nblk ? c[seg + k * 32] : 0u;
+    uint32_t wrun = 0;  // the warp segment's items before item k
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      uint32_t x = v[k];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      const uint32_t item = v[k];
+      v[k] = wrun + x - item;  // exclusive, within the warp's segment
+      wrun += __shfl_sync(0xffffffffu, x, 31);
     }
-    if (lane == 31) ws[w] = x;
+    if (lane == 0) ws[w] = wrun;
     __syncthreads();
     if (w == 0) {
       uint32_t s = ws[lane];
@@ -90,8 +103,10 @@ __global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *__restrict__ counts,
       ws[lane] = s;
     }
     __syncthreads();
-    uint32_t before = (w > 0 ? ws[w - 1] : 0u) + carry;
-    if (idx < nblk) c[idx] = before + x - v;
+    const uint32_t before = (w > 0 ? ws[w - 1] : 0u) + carry;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+      if (seg + k * 32 < nblk) c[seg + k * 32] = before + v[k];
     carry += ws[31];
     __syncthreads();
   }
