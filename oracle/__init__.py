@@ -78,6 +78,7 @@ def lib():
                 "or_alg1_sweep": (i64, [vp, i64, i64, i64, d, vp, vp, i64]),
                 "or_raw_cells_tree": (i64, [vp, vp, vp, i64, vp, i64]),
                 "or_alg3": (i32, [vp, i64, i64, d, i32, i64, vp, vp, vp, vp]),
+                "or_narrow_phase": (i64, [vp, i64, vp, i64, d, vp, vp, vp, vp, i64]),
                 "or_radial_range": (None, [vp, vp]),
                 "or_band_edges": (None, [vp, i64, i32, vp]),
                 "or_band_counts": (None, [vp, i64, i32, vp]),
@@ -362,6 +363,40 @@ def alg3(els, T: int, tick_s: float, mode: int = BOX_SPEED, t_first: int = -1):
                        ctypes.byref(wj), ctypes.byref(wt), ctypes.byref(it))
     w = (wi.value, wj.value, wt.value) if rc == 1 else None
     return rc, w, it.value
+
+
+def narrow_phase(els, cands, tick_s: float, witnesses: bool = True):
+    """Narrow phase over a candidate list (CELL_DTYPE rows i < j, [tlo, thi]):
+    every tick of every candidate interval tested with Alg 1's predicate
+    (Defs 2-4).  Returns (first, count, margin, witness list): per candidate
+    the first witness tick (-1: none), the number of witness ticks and the
+    smallest |d_inf - (r_i + r_j)| over its ticks; the witnesses in
+    candidate order (empty if witnesses is False)."""
+    E = _els(els)
+    C = np.ascontiguousarray(np.asarray(cands, dtype=CELL_DTYPE))
+    m = len(C)
+    first = np.zeros(m, np.int32)
+    count = np.zeros(m, np.uint32)
+    margin = np.zeros(m, np.float64)
+    cap = 1 << 12 if witnesses else 0
+    while True:
+        out = np.zeros(max(cap, 1), WITNESS_DTYPE)
+        k = lib().or_narrow_phase(_p(E), len(E), _p(C), m, float(tick_s), _p(first), _p(count),
+                                  _p(margin), _p(out) if witnesses else None, cap)
+        if k < 0:
+            raise ValueError("candidate with an object index >= n or an empty tick interval")
+        if not witnesses or k <= cap:
+            return first, count, margin, out[:min(k, cap)].copy()
+        cap = int(k)
+
+
+def earliest_witness(wit):
+    """The first witness in Alg 1's order (tick, then i, then j) of a witness
+    list, or None."""
+    if len(wit) == 0:
+        return None
+    o = np.lexsort((wit["j"], wit["i"], wit["t"]))[0]
+    return int(wit["i"][o]), int(wit["j"][o]), int(wit["t"][o])
 
 
 # --- decomposition (Sec. 5, Sec. 6.1) ----------------------------------------

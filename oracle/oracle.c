@@ -611,6 +611,54 @@ int64_t or_alg1_witnesses(const double *els, int64_t n, int64_t T,
   return c;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Narrow phase: the collision witnesses (Def 4) inside a candidate list.  */
+/* For each candidate (i, j, [tlo, thi]) every tick t of the interval is   */
+/* tested with the same predicate as Alg 1 (Defs 2-3: centres within       */
+/* r_i + r_j in the infinity norm, positions by the Sec. 6.1 propagation). */
+/* Per candidate: the first witness tick (-1: none), the witness count and */
+/* the smallest |d_inf - (r_i + r_j)| over its ticks (how close the        */
+/* decisions came to the boundary).  Witnesses are listed in candidate     */
+/* order, ticks ascending.  Returns the witness count, or -1 if a          */
+/* candidate names an object >= n or has tlo > thi or tlo < 0.             */
+/* ------------------------------------------------------------------------ */
+int64_t or_narrow_phase(const double *els, int64_t n, const or_cell *cand, int64_t m,
+                        double tick_s, int32_t *first, uint32_t *count, double *margin,
+                        or_witness *out, int64_t cap) {
+  int64_t c = 0;
+  for (int64_t q = 0; q < m; ++q) {
+    const or_cell x = cand[q];
+    if ((int64_t)x.i >= n || (int64_t)x.j >= n || x.tlo < 0 || x.tlo > x.thi) return -1;
+    const double *ei = els + 7 * (int64_t)x.i, *ej = els + 7 * (int64_t)x.j;
+    const double R = ei[6] + ej[6];
+    int32_t f = -1;
+    uint32_t k = 0;
+    double mg = INFINITY;
+    for (int64_t t = x.tlo; t <= x.thi; ++t) {
+      double pi[3], pj[3];
+      or_position(ei, (double)t * tick_s, pi);
+      or_position(ej, (double)t * tick_s, pj);
+      double d = 0.0;
+      for (int a = 0; a < 3; ++a)
+        if (fabs(pi[a] - pj[a]) > d) d = fabs(pi[a] - pj[a]);
+      if (fabs(d - R) < mg) mg = fabs(d - R);
+      if (!occ_collide(pi, ei[6], pj, ej[6])) continue;
+      if (f < 0) f = (int32_t)t;
+      ++k;
+      if (out && c < cap) {
+        out[c].i = x.i;
+        out[c].j = x.j;
+        out[c].t = (int32_t)t;
+      }
+      ++c;
+    }
+    if (first) first[q] = f;
+    if (count) count[q] = k;
+    if (margin) margin[q] = mg;
+  }
+  return c;
+}
+
 /* Alg 1 over ticks t0..t1 (inclusive) with the pairs restricted by a sweep
  * along x: two objects can only meet (Def 3) if their x centres are within
  * r_i + r_j <= 2 max r, so after sorting by x only pairs inside that window

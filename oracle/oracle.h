@@ -114,6 +114,15 @@ int64_t or_alg1_witnesses(const double *els, int64_t n, int64_t T,
  * witness k's centres.  Returns the witness count (only cap are written). */
 int64_t or_alg1_sweep(const double *els, int64_t n, int64_t t0, int64_t t1, double tick_s,
                       or_witness *out, double *dist, int64_t cap);
+/* Narrow phase over m candidates (i < j < n, 0 <= tlo <= thi): every tick
+ * of each interval tested as in Alg 1.  first[q] = first witness tick or -1,
+ * count[q] = witness ticks, margin[q] = min |d_inf - (r_i + r_j)| over the
+ * ticks; witnesses (candidate order, ticks ascending) go to out (cap
+ * entries, out may be NULL).  Returns the witness count, -1 on a bad
+ * candidate. */
+int64_t or_narrow_phase(const double *els, int64_t n, const or_cell *cand, int64_t m,
+                        double tick_s, int32_t *first, uint32_t *count, double *margin,
+                        or_witness *out, int64_t cap);
 /* Alg 3 with Algs 4-6: the serial 4D search.  Returns 1 and the first
  * witness, 0 for None, or a negative code if a loop invariant (Sec. 7.2)
  * failed: -1 invariant 1, -2 invariant 2 (needs t_first, the earliest Alg 1
