@@ -10,6 +10,9 @@ over the max-rank time); ``e2e`` is the same through the C ABI with host
 buffers (elements copied in, pairs copied out inside the timed region).
 
 Other workloads (--workload):
+  narrow24h   the default screen followed by the narrow phase over its
+              candidates: the first collision witness of the 24 h problem
+              (Def 5) from device-resident elements
   band_slab   the same population with band-table steps (P/200 .. P/400 by
               perigee altitude) and the 16 slab x 8 octant decomposition, with
               the tuning picked by the autotuner
@@ -51,6 +54,9 @@ TICK_S = 1.0
 FRACTION = 100.0
 L2_BYTES = 129 * 1024 * 1024
 MU = 398600.4418
+# nominal FP64 rate of a GB300 [GFLOP/s]: 152 SMs x 2.07 GHz x ~4 FP64 flops
+# per SM and clock (two FMA lanes)
+FP64_PEAK_GFLOPS = 1250.0
 
 WORKLOADS = {
     "catalog24h": {
@@ -64,6 +70,13 @@ WORKLOADS = {
                  "(1000-2000 km), P/50 (2000-30000 km), P/400 (above); 16 tick slabs x 8 ECI "
                  "octants as 128 cell subtrees of one sort in one persistent traversal; tuning "
                  "from the autotuner")},
+    "narrow24h": {
+        "metric": "ms per 24h first-witness solve at n=16848 (screen + narrow phase)",
+        "desc": ("the n=16848 mixture, 24 h, 1 s ticks, per-object step P/100: the screen's "
+                 "canonical candidate list, then the narrow phase (Alg 1's infinity-norm test "
+                 "at the candidates' ticks, FP64 positions, ticks skipped by the "
+                 "relative-motion bound): per-candidate first witness and witness count and "
+                 "the earliest witness (Def 5)")},
     "batch64": {
         "metric": "scenes per second, 64 scenes, ~1.2M objects, horizons 6-72 h",
         "desc": ("64 independent catalog-shaped scenes, sizes log-uniform 1e3-6e4 (total "
@@ -336,6 +349,105 @@ def run_single(args, world, wl):
     return r
 
 
+def narrow_flops_per_eval():
+    """FP64 operations per narrow-phase tick evaluation from the committed
+    ncu summary, while the library's sources still hash to the ones it was
+    measured on; else None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_narrow_catalog16848.md")
+    if not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.split(":", 1)[0] in ("fp64_flops_per_eval", "source_sha256"):
+            k, v = line.split(":", 1)
+            fields[k] = v.strip()
+    h = hashlib.sha256()
+    for f in library_sources():
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    if fields.get("source_sha256") != h.hexdigest()[:16]:
+        return None
+    return float(fields["fp64_flops_per_eval"])
+
+
+def run_narrow(args, world):
+    """The 24 h screen, then the narrow phase over its candidate list."""
+    import torch
+
+    import paper_1901_10475_gb300 as scd
+    dev = _device()
+    els = P.catalog_mixture(n=N_OBJ, seed=P.SEED_BASE + 2)
+    pol = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=FRACTION)
+    sc = scd.Scene(els, args.horizon_s, TICK_S, pol, mode=args.mode)
+    d_el = torch.as_tensor(els, device="cuda")
+    stream = torch.cuda.current_stream()
+    buf = {}
+    np_ms, np_evals = [], []
+
+    def step():
+        scd.scd_scene_set_elements_device(sc.handle, d_el.data_ptr(), N_OBJ)
+        scd.scd_build_boxes(sc.handle)
+        ptr, m = scd.scd_find_pairs_device(sc.handle)
+        buf["ptr"] = ptr
+        if buf.get("m") != m:
+            buf["m"] = m
+            buf["first"] = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+            buf["count"] = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        buf["w"] = scd.scd_narrow_phase(sc.handle, ptr, m, buf["first"].data_ptr(),
+                                        buf["count"].data_ptr())
+        e1.record(stream)
+        e1.synchronize()
+        np_ms.append(e0.elapsed_time(e1))
+        np_evals.append(sc.metrics()["narrow_evals"])
+        return m
+
+    r = time_scene_steps(sc, step, args.steps, args.warmup, dev, world)
+    r["launches"] += 2 * args.steps  # the narrow phase's init and persistent kernels
+    k = args.steps
+    r["phase_ms"]["ms_narrow"] = statistics.mean(np_ms[-k:])
+    r["narrow"] = {"ms": statistics.mean(np_ms[-k:]), "tick_evals": int(np_evals[-1]),
+                   "tick_evals_per_s": np_evals[-1] / (statistics.mean(np_ms[-k:]) * 1e-3),
+                   "candidates": buf["m"],
+                   "candidate_ticks": _candidate_ticks(buf["ptr"], buf["m"]),
+                   "candidates_with_witness": int((buf["first"][:buf["m"]] >= 0).sum()),
+                   "witness_ticks": int(buf["count"][:buf["m"]].long().sum()),
+                   "earliest_witness": list(buf["w"]) if buf["w"] else None}
+    r["value"] = slowest_rank(sum(r["times"]), world) / (args.steps * world)
+    r["unit"] = "ms"
+    r["higher_is_better"] = False
+    # end to end through the C ABI: host elements in, earliest witness out
+    host_in = torch.as_tensor(np.ascontiguousarray(els)).pin_memory()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    ts = []
+    for q in range(max(1, min(args.steps, 5))):
+        flush.fill_(float(q))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        scd._binding.lib().scd_scene_set_elements(sc.handle, ctypes.c_void_p(host_in.data_ptr()),
+                                                  N_OBJ)
+        scd.scd_build_boxes(sc.handle)
+        ptr, m = scd.scd_find_pairs_device(sc.handle)
+        scd.scd_narrow_phase(sc.handle, ptr, m, buf["first"].data_ptr(), buf["count"].data_ptr())
+        ts.append((time.perf_counter() - t0) * 1e3)
+    r["e2e"] = {"value": statistics.median(ts), "unit": "ms", "h2d_bytes_per_step": 56 * N_OBJ,
+                "d2h_bytes_per_step": 12}
+    r["n"] = N_OBJ
+    sc.close()
+    return r
+
+
+def _candidate_ticks(ptr, m):
+    """Sum of thi - tlo + 1 over a device candidate list."""
+    import paper_1901_10475_gb300 as scd
+    if m == 0:
+        return 0
+    p = scd.device_view(ptr, (m, 4), "<i4")
+    return int((p[:, 3].long() - p[:, 2].long() + 1).sum())
+
+
 def run_batch64(args, world):
     import torch
 
@@ -543,6 +655,8 @@ def main():
         torch.distributed.init_process_group("nccl")
     if wl in ("catalog24h", "band_slab"):
         r = run_single(args, world, wl)
+    elif wl == "narrow24h":
+        r = run_narrow(args, world)
     elif wl == "batch64":
         r = run_batch64(args, world)
     else:
@@ -578,16 +692,30 @@ def main():
         dom = max(ph, key=ph.get)
         name = dom[3:]
         hbm = pk.get("hbm_gbs", 6800.0)
-        achieved = byt[name] / (ph[dom] * 1e-3) / 1e9
         # the committed capture is of the default configuration only
         default_cfg = (args.horizon_s == HORIZON_S and not args.mode and not args.tuning
                        and not args.autotune)
-        traffic = measured_traffic(wl) if name == "traverse" and default_cfg else None
-        line["roofline"] = {"kernel_phase": name, "bound": "hbm", "achieved": achieved,
-                            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                            "traffic": traffic,
-                            "peak_source": src, "phase_ms": ph,
-                            "algorithmic_bytes": byt[name]}
+        if name == "narrow":
+            # FP64 arithmetic bound: FP64 operations per tick evaluation (ncu
+            # instruction counts, committed) x evaluations / kernel time,
+            # against the nominal FP64 rate (no measured FP64 peak exists)
+            fpe = narrow_flops_per_eval()
+            ev = r["narrow"]["tick_evals"]
+            achieved = fpe * ev / (ph[dom] * 1e-3) / 1e9 if fpe else None
+            line["roofline"] = {"kernel_phase": name, "bound": "alu",
+                                "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
+                                "unit": "GFLOP/s (FP64)",
+                                "frac": achieved / FP64_PEAK_GFLOPS if achieved else None,
+                                "traffic": None, "peak_source": "nominal",
+                                "phase_ms": ph, "fp64_flops_per_eval": fpe}
+        else:
+            achieved = byt[name] / (ph[dom] * 1e-3) / 1e9
+            traffic = measured_traffic(wl) if name == "traverse" and default_cfg else None
+            line["roofline"] = {"kernel_phase": name, "bound": "hbm", "achieved": achieved,
+                                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                                "traffic": traffic,
+                                "peak_source": src, "phase_ms": ph,
+                                "algorithmic_bytes": byt[name]}
         if "phase_ms_source" in r:
             line["roofline"]["phase_ms_source"] = r["phase_ms_source"]
         line["gpu_launches"] = r["launches"]
@@ -603,7 +731,7 @@ def main():
     if "gpu_launches" not in line and r.get("launches") is not None:
         line["gpu_launches"] = r["launches"]
     for k in ("latency_ms", "batches", "objects", "boxes_est", "ms_per_pass", "p100_ms",
-              "p100_boxes", "p100_pairs", "training", "tuning"):
+              "p100_boxes", "p100_pairs", "training", "tuning", "narrow"):
         if k in r and r[k] is not None:
             line[k] = r[k]
     line["clocks"] = r["clocks"]

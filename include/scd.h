@@ -213,6 +213,38 @@ SCD_API int scd_find_pairs_device(scd_scene *s, const scd_decomp *d,
 SCD_API int scd_find_raw_cells_device(scd_scene *s, const scd_pair **dev_out,
                                       int64_t *n_out);
 
+/* One collision witness (Def 4): objects i < j collide at tick t. */
+typedef struct {
+  uint32_t i, j;
+  int32_t t;
+} scd_witness;
+
+/* Narrow phase (Def 4, Def 5): the collision witnesses inside a candidate
+ * list of the scene.  For each candidate q (i, j, [tlo, thi]) every tick t
+ * of the interval is decided by the test of Alg 1: objects i and j collide
+ * at t iff their centres, propagated in FP64 (Sec. 6.1), are within
+ * r_i + r_j in the infinity norm (Defs 2-3).  Ticks where a bound on the
+ * relative motion (perigee speeds, relative velocity and perigee gravity)
+ * proves the distance above r_i + r_j are not evaluated; the results are
+ * those of testing every tick.
+ *   d_pairs   device array of n_pairs candidates with i, j < n and
+ *             0 <= tlo <= thi <= T (for example the list of
+ *             scd_find_pairs_device); read only.
+ *   d_first   device array of n_pairs (or NULL): the first witness tick of
+ *             each candidate, -1 if it has none.
+ *   d_count   device array of n_pairs (or NULL): the number of witness
+ *             ticks of each candidate.
+ *   earliest  host pointer (or NULL): the first witness in Alg 1's order
+ *             (smallest t, then i, then j) over all candidates, t = -1 if
+ *             there is none.  Over the scene's full candidate list this is
+ *             the answer of the discrete-time n-to-n problem (Def 5-6).
+ * Needs scd_build_boxes (the per-object propagation constants): else
+ * SCD_ERR_STATE.  A candidate outside those ranges: SCD_ERR_INVALID_ARG
+ * (its outputs are -1 and 0, the others are valid).  n_pairs >= 2^32:
+ * SCD_ERR_CAPACITY.  Synchronous on the scene's stream. */
+SCD_API int scd_narrow_phase(scd_scene *s, const scd_pair *d_pairs, int64_t n_pairs,
+                             int32_t *d_first, uint32_t *d_count, scd_witness *earliest);
+
 /* The scene's boxes in object-major, segment order (device pointers owned
  * by the scene): lo4/hi4 are nbox x 4 floats (x, y, z [km], tick), obj the
  * object of each box. */
@@ -308,7 +340,8 @@ SCD_API int scd_count_pairs_per_object(const scd_pair *d_pairs, int64_t n_pairs,
                                        uint32_t *d_counts, void *cuda_stream);
 
 /* Metrics of the scene's last find_pairs as one JSON object (box count,
- * node and leaf tests, pair counts, kernel times).  Writes at most cap bytes
+ * node and leaf tests, pair counts, kernel times; narrow_evals: the ticks the
+ * last scd_narrow_phase evaluated).  Writes at most cap bytes
  * including the terminating NUL. */
 SCD_API int scd_last_metrics(const scd_scene *s, char *json, size_t cap);
 

@@ -19,7 +19,8 @@ from ._binding import (PAIR_DTYPE, SCD_BOX_INTERVAL, SCD_BOX_SPEED, SCD_DECOMP_A
                        scd_batch_find_pairs, scd_build_boxes, scd_default_tuning,
                        scd_find_pairs, scd_find_pairs_device, scd_find_pairs_into,
                        scd_find_raw_cells_device,
-                       scd_get_boxes, scd_get_steps, scd_last_metrics, scd_propagate,
+                       scd_get_boxes, scd_get_steps, scd_last_metrics, scd_narrow_phase,
+                       scd_propagate,
                        scd_propagate_noalloc,
                        scd_scene_create, scd_scene_destroy, scd_scene_set_elements,
                        scd_scene_set_elements_device, scd_scene_set_tuning,
@@ -93,6 +94,20 @@ class Scene:
     def find_raw_cells_device(self):
         ptr, n = scd_find_raw_cells_device(self.handle)
         return device_view(ptr, (n, 4), "<i4")
+
+    def narrow_phase(self, pairs):
+        """Collision witnesses inside a device candidate list (an (m, 4) int32
+        tensor of scd_pair records, e.g. find_pairs_device()): per candidate
+        the first witness tick (-1: none) and the witness count, as device
+        tensors, and the earliest witness (i, j, t) in Alg 1's order, or
+        None."""
+        import torch
+        m = int(pairs.shape[0])
+        first = torch.empty(m, dtype=torch.int32, device=pairs.device)
+        count = torch.empty(m, dtype=torch.int32, device=pairs.device)
+        w = scd_narrow_phase(self.handle, pairs.data_ptr() if m else 0, m,
+                             first.data_ptr() if m else 0, count.data_ptr() if m else 0)
+        return first, count, w
 
     def boxes(self):
         lo, hi, obj, n = scd_get_boxes(self.handle)

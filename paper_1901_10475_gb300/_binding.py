@@ -62,6 +62,10 @@ class scd_tuning(ctypes.Structure):
                 ("node_width", ctypes.c_int)]
 
 
+class scd_witness(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_uint32), ("j", ctypes.c_uint32), ("t", ctypes.c_int32)]
+
+
 PAIR_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("tlo", "<i4"), ("thi", "<i4")])
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -99,6 +103,7 @@ def lib() -> ctypes.CDLL:
             "scd_find_pairs_device": (i32, [vp, P(scd_decomp), P(vp), P(i64)]),
             "scd_find_raw_cells_device": (i32, [vp, P(vp), P(i64)]),
             "scd_get_boxes": (i32, [vp, P(vp), P(vp), P(vp), P(i64)]),
+            "scd_narrow_phase": (i32, [vp, vp, i64, vp, vp, P(scd_witness)]),
             "scd_get_steps": (i32, [vp, P(vp)]),
             "scd_propagate": (i32, [vp, i64, vp, vp, i64, vp, vp]),
             "scd_propagate_noalloc": (i32, [vp, i64, vp, vp, i64, vp, vp]),
@@ -275,6 +280,17 @@ def scd_find_raw_cells_device(scene: int):
     check(lib().scd_find_raw_cells_device(scene, ctypes.byref(p), ctypes.byref(n)),
           "scd_find_raw_cells_device")
     return p.value, int(n.value)
+
+
+def scd_narrow_phase(scene: int, d_pairs: int, n_pairs: int, d_first: int = 0,
+                     d_count: int = 0):
+    """Narrow phase over n_pairs device candidates: fills the device arrays
+    d_first (int32) and d_count (uint32) when given; returns the earliest
+    witness (i, j, t) in Alg 1's order, or None."""
+    w = scd_witness()
+    check(lib().scd_narrow_phase(scene, d_pairs or None, int(n_pairs), d_first or None,
+                                 d_count or None, ctypes.byref(w)), "scd_narrow_phase")
+    return None if w.t < 0 else (int(w.i), int(w.j), int(w.t))
 
 
 def scd_get_boxes(scene: int):

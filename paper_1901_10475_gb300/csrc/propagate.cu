@@ -4,93 +4,10 @@
 // and the 4D Morton key of every box.
 #include <math.h>
 
+#include "kepler.cuh"
 #include "scd_internal.cuh"
 
 namespace scd {
-
-// ---------------------------------------------------------------------------
-// Kepler's equation E - e sin E = M by Newton's method.  The start is
-// M + e sin M for moderate e and Danby's M + 0.85 e sign(sin M) above
-// e = 0.5; both converge for the e < 1 of closed orbits.
-// ---------------------------------------------------------------------------
-constexpr int kKeplerMaxIter = 40;
-
-__device__ __forceinline__ double reduce_2pi(double M) {
-  double k = rint(M * (1.0 / kTwoPi));
-  return fma(-k, kTwoPi, M);
-}
-
-// Kepler's equation, mixed precision: Newton in FP32 to about 3e-7 rad (at
-// most 12 steps: by perigee at e near 1 the FP32 residual cancels and stalls
-// near 1e-5 rad), then FP64 Newton steps.  Each FP64 step squares the error
-// (times |f''/2f'| = e|sin E| / 2(1 - e cos E), at most 1.5 for e <= 0.75),
-// so one step usually suffices: below 2e-13 rad, i.e. below 1e-8 km of
-// position at GEO distance.  Steps continue while the estimated error left
-// exceeds tol (per object, 1e-7 km / a) or the last correction exceeds 1e-5
-// rad; after kFp64Steps without that, iters reports non-convergence.
-// Returns E with sin E and cos E, corrected to second order in the last step
-// (third-order error below 2e-16), so the caller needs no further sincos.
-constexpr int kFp32Steps = 12, kFp64Steps = 8;
-
-// The rare further FP64 steps: take the pending correction d, then step until
-// the test passes; on return (Ed, s, c, d) describe the last step.
-__device__ __noinline__ void kepler_more_fp64(double M, double e, double tol, double &Ed, double &s,
-                                              double &c, double &d, int &iters) {
-  for (int step = 1; step < kFp64Steps; ++step) {
-    Ed -= d;
-    sincos(Ed, &s, &c);
-    const double fp = 1.0 - e * c;
-    d = (Ed - e * s - M) / fp;
-    iters += 1;
-    if (!(2.0 * fabs(e * s) * d * d > tol * fp || fabs(d) > 1e-5)) return;
-  }
-  iters = kKeplerMaxIter;  // no convergence
-}
-
-__device__ __forceinline__ double kepler_E_sc(double M, double e, double tol, double &sE,
-                                              double &cE, int &iters) {
-  if (e == 0.0) {
-    sincos(M, &sE, &cE);
-    iters = 0;
-    return M;
-  }
-  const float Mf = (float)M, ef = (float)e;
-  float E = (ef <= 0.5f) ? Mf + ef * sinf(Mf)
-                         : Mf + 0.85f * ef * (sinf(Mf) >= 0.f ? 1.f : -1.f);
-  int it = 0;
-  for (; it < kFp32Steps; ++it) {
-    float s, c;
-    sincosf(E, &s, &c);
-    float d = (E - ef * s - Mf) / (1.0f - ef * c);
-    E -= d;
-    if (fabsf(d) <= 1e-6f) break;
-  }
-  double Ed = (double)E, s, c;
-  sincos(Ed, &s, &c);
-  double fp = 1.0 - e * c;
-  double d = (Ed - e * s - M) / fp;
-  iters = it + 1;
-  // error left after this step (with a factor 4 of safety) above tol,
-  // compared without a second FP64 division: 2 |e s| d^2 / fp > tol
-  if (2.0 * fabs(e * s) * d * d > tol * fp || fabs(d) > 1e-5)
-    kepler_more_fp64(M, e, tol, Ed, s, c, d, iters);
-  // sin(E - d), cos(E - d) to second order in d
-  const double h = 0.5 * d * d;
-  sE = s - d * c - h * s;
-  cE = c + d * s - h * c;
-  return Ed - d;
-}
-
-// position at time t [s] from the per-object constants
-__device__ __forceinline__ void position_at(const ObjParams &p, double t, double out[3],
-                                            int &iters) {
-  double M = reduce_2pi(p.M0 + p.n * t);
-  double s, c;
-  kepler_E_sc(M, p.e, p.tolE, s, c, iters);
-  double ce = c - p.e;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) out[k] = fma(p.A[k], ce, p.B[k] * s);
-}
 
 // ---------------------------------------------------------------------------
 // A1: per-object constants and step length.  The period and the step are

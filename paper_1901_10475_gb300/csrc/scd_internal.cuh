@@ -442,6 +442,10 @@ struct scd_scene {
   int64_t n_out = 0;
   scd::SortScratch sort_sc;
 
+  // narrow phase: device state words, tick evaluations of the last call
+  scd::DevBuf<unsigned long long> d_narrow;
+  unsigned long long last_np_evals = 0;
+
   // metrics of the last find_pairs
   double ms_sort = 0, ms_build = 0, ms_traverse = 0, ms_canon = 0, ms_boxes = 0;
   unsigned long long last_node_tests = 0, last_leaf_tests = 0, last_runs = 0, last_open = 0;
