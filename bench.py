@@ -54,9 +54,6 @@ TICK_S = 1.0
 FRACTION = 100.0
 L2_BYTES = 129 * 1024 * 1024
 MU = 398600.4418
-# nominal FP64 rate of a GB300 [GFLOP/s]: 152 SMs x 2.07 GHz x ~4 FP64 flops
-# per SM and clock (two FMA lanes)
-FP64_PEAK_GFLOPS = 1250.0
 
 WORKLOADS = {
     "catalog24h": {
@@ -104,7 +101,7 @@ def measured_traffic(workload: str):
     measured on; else None."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_traverse2_catalog16848_24h.md")
-    if workload != "catalog24h" or not os.path.exists(path):
+    if workload not in ("catalog24h", "narrow24h") or not os.path.exists(path):
         return None
     fields = {}
     for line in open(path):
@@ -349,28 +346,6 @@ def run_single(args, world, wl):
     return r
 
 
-def narrow_flops_per_eval():
-    """FP64 operations per narrow-phase tick evaluation from the committed
-    ncu summary, while the library's sources still hash to the ones it was
-    measured on; else None."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "k_narrow_catalog16848.md")
-    if not os.path.exists(path):
-        return None
-    fields = {}
-    for line in open(path):
-        if ":" in line and line.split(":", 1)[0] in ("fp64_flops_per_eval", "source_sha256"):
-            k, v = line.split(":", 1)
-            fields[k] = v.strip()
-    h = hashlib.sha256()
-    for f in library_sources():
-        with open(f, "rb") as fh:
-            h.update(fh.read())
-    if fields.get("source_sha256") != h.hexdigest()[:16]:
-        return None
-    return float(fields["fp64_flops_per_eval"])
-
-
 def run_narrow(args, world):
     """The 24 h screen, then the narrow phase over its candidate list."""
     import torch
@@ -383,7 +358,7 @@ def run_narrow(args, world):
     d_el = torch.as_tensor(els, device="cuda")
     stream = torch.cuda.current_stream()
     buf = {}
-    np_ms, np_evals = [], []
+    np_ms, np_evals, np_evals64 = [], [], []
 
     def step():
         scd.scd_scene_set_elements_device(sc.handle, d_el.data_ptr(), N_OBJ)
@@ -401,7 +376,9 @@ def run_narrow(args, world):
         e1.record(stream)
         e1.synchronize()
         np_ms.append(e0.elapsed_time(e1))
-        np_evals.append(sc.metrics()["narrow_evals"])
+        mm = sc.metrics()
+        np_evals.append(mm["narrow_evals"])
+        np_evals64.append(mm["narrow_evals_fp64"])
         return m
 
     r = time_scene_steps(sc, step, args.steps, args.warmup, dev, world)
@@ -409,6 +386,7 @@ def run_narrow(args, world):
     k = args.steps
     r["phase_ms"]["ms_narrow"] = statistics.mean(np_ms[-k:])
     r["narrow"] = {"ms": statistics.mean(np_ms[-k:]), "tick_evals": int(np_evals[-1]),
+                   "tick_evals_fp64": int(np_evals64[-1]),
                    "tick_evals_per_s": np_evals[-1] / (statistics.mean(np_ms[-k:]) * 1e-3),
                    "candidates": buf["m"],
                    "candidate_ticks": _candidate_ticks(buf["ptr"], buf["m"]),
@@ -689,33 +667,21 @@ def main():
         line["leaf_tests"] = m["leaf_tests"]
         ph = r["phase_ms"]
         byt = algorithmic_bytes(m, r["n"])
-        dom = max(ph, key=ph.get)
+        # the dominant phase of the screen (the narrow phase of narrow24h is
+        # reported on its own, under "narrow")
+        dom = max((k for k in ph if k != "ms_narrow"), key=ph.get)
         name = dom[3:]
         hbm = pk.get("hbm_gbs", 6800.0)
+        achieved = byt[name] / (ph[dom] * 1e-3) / 1e9
         # the committed capture is of the default configuration only
         default_cfg = (args.horizon_s == HORIZON_S and not args.mode and not args.tuning
                        and not args.autotune)
-        if name == "narrow":
-            # FP64 arithmetic bound: FP64 operations per tick evaluation (ncu
-            # instruction counts, committed) x evaluations / kernel time,
-            # against the nominal FP64 rate (no measured FP64 peak exists)
-            fpe = narrow_flops_per_eval()
-            ev = r["narrow"]["tick_evals"]
-            achieved = fpe * ev / (ph[dom] * 1e-3) / 1e9 if fpe else None
-            line["roofline"] = {"kernel_phase": name, "bound": "alu",
-                                "achieved": achieved, "peak": FP64_PEAK_GFLOPS,
-                                "unit": "GFLOP/s (FP64)",
-                                "frac": achieved / FP64_PEAK_GFLOPS if achieved else None,
-                                "traffic": None, "peak_source": "nominal",
-                                "phase_ms": ph, "fp64_flops_per_eval": fpe}
-        else:
-            achieved = byt[name] / (ph[dom] * 1e-3) / 1e9
-            traffic = measured_traffic(wl) if name == "traverse" and default_cfg else None
-            line["roofline"] = {"kernel_phase": name, "bound": "hbm", "achieved": achieved,
-                                "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                                "traffic": traffic,
-                                "peak_source": src, "phase_ms": ph,
-                                "algorithmic_bytes": byt[name]}
+        traffic = measured_traffic(wl) if name == "traverse" and default_cfg else None
+        line["roofline"] = {"kernel_phase": name, "bound": "hbm", "achieved": achieved,
+                            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                            "traffic": traffic,
+                            "peak_source": src, "phase_ms": ph,
+                            "algorithmic_bytes": byt[name]}
         if "phase_ms_source" in r:
             line["roofline"]["phase_ms_source"] = r["phase_ms_source"]
         line["gpu_launches"] = r["launches"]

@@ -340,8 +340,9 @@ SCD_API int scd_count_pairs_per_object(const scd_pair *d_pairs, int64_t n_pairs,
                                        uint32_t *d_counts, void *cuda_stream);
 
 /* Metrics of the scene's last find_pairs as one JSON object (box count,
- * node and leaf tests, pair counts, kernel times; narrow_evals: the ticks the
- * last scd_narrow_phase evaluated).  Writes at most cap bytes
+ * node and leaf tests, pair counts, kernel times; narrow_evals and
+ * narrow_evals_fp64: the ticks the last scd_narrow_phase evaluated, and
+ * those of them it had to decide in FP64).  Writes at most cap bytes
  * including the terminating NUL. */
 SCD_API int scd_last_metrics(const scd_scene *s, char *json, size_t cap);
 

@@ -444,7 +444,8 @@ struct scd_scene {
 
   // narrow phase: device state words, tick evaluations of the last call
   scd::DevBuf<unsigned long long> d_narrow;
-  unsigned long long last_np_evals = 0;
+  scd::DevBuf<unsigned char> d_npobj;  // per-object FP32 constants (64 B each)
+  unsigned long long last_np_evals = 0, last_np_evals64 = 0;
 
   // metrics of the last find_pairs
   double ms_sort = 0, ms_build = 0, ms_traverse = 0, ms_canon = 0, ms_boxes = 0;

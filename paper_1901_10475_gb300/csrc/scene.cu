@@ -706,13 +706,14 @@ extern "C" SCD_API int scd_last_metrics(const scd_scene *s, char *json, size_t c
                    "\"ms_traverse\": %.4f, \"ms_canon\": %.4f, \"leaf_size\": %d, "
                    "\"stack_depth\": %d, \"block_threads\": %d, \"morton_bits\": %d, "
                    "\"launches\": %llu, \"refs\": %lld, \"cells\": %d, \"graph\": %d, "
-                   "\"narrow_evals\": %llu}",
+                   "\"narrow_evals\": %llu, \"narrow_evals_fp64\": %llu}",
                    (long long)s->n, (long long)s->T, (long long)s->N, s->last_node_tests,
                    s->last_leaf_tests, s->last_runs, s->last_open, (long long)s->n_out, s->ms_boxes, s->ms_sort,
                    s->ms_build, s->ms_traverse, s->ms_canon, s->tune.leaf_size,
                    s->tune.stack_depth, s->tune.block_threads, s->tune.morton_bits,
                    s->last_launches, (long long)(s->dkind ? s->n_refs : s->N),
-                   s->dkind ? s->n_cells : 1, s->last_graph, s->last_np_evals);
+                   s->dkind ? s->n_cells : 1, s->last_graph, s->last_np_evals,
+                   s->last_np_evals64);
   if (w < 0 || (size_t)w >= cap) return SCD_ERR_BUFFER_TOO_SMALL;
   return SCD_OK;
 }
@@ -738,6 +739,7 @@ extern "C" SCD_API void scd_scene_destroy(scd_scene *s) {
   s->d_tilecnt.release(st);
   s->d_out.release(st);
   s->d_narrow.release(st);
+  s->d_npobj.release(st);
   s->sort_sc.release(st);
   s->s_cell.release(st); s->d_first.release(st);
   s->d_refcnt.release(st); s->d_refoff.release(st); s->d_refkey.release(st);

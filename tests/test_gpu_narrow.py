@@ -136,9 +136,11 @@ def test_full_24h_catalog_sampled(scd):
     at_t0 = hit[first[hit] == t0]
     ij = sorted((int(pairs[q, 0]), int(pairs[q, 1])) for q in _host(at_t0))
     assert w == (ij[0][0], ij[0][1], t0)
-    ev = sc.metrics()["narrow_evals"]
+    mt = sc.metrics()
+    ev, ev64 = mt["narrow_evals"], mt["narrow_evals_fp64"]
     ticks = int((pairs[:, 3].long() - pairs[:, 2].long() + 1).sum())
     assert 0 < ev < ticks  # the skip bound does skip (parity above: soundly)
+    assert 0 < ev64 < ev  # most ticks are decided by the FP32 tier's bounds
     sc.close()
 
 
