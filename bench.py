@@ -382,7 +382,7 @@ def run_narrow(args, world):
         return m
 
     r = time_scene_steps(sc, step, args.steps, args.warmup, dev, world)
-    r["launches"] += 2 * args.steps  # the narrow phase's init and persistent kernels
+    r["launches"] += 3 * args.steps  # the narrow phase: state init, object constants, k_narrow
     k = args.steps
     r["phase_ms"]["ms_narrow"] = statistics.mean(np_ms[-k:])
     r["narrow"] = {"ms": statistics.mean(np_ms[-k:]), "tick_evals": int(np_evals[-1]),

@@ -263,8 +263,11 @@ __device__ __forceinline__ void np_tick(const NarrowArgs &a, NpLane &L,
 }
 
 // Persistent: every lane holds one candidate and walks its ticks; lanes that
-// finish claim the next candidates in list order (one atomic per warp and
-// refill), so consecutive lanes share object i and its constants stay in L1.
+// finish claim the next candidates (one atomic per warp and refill), so
+// consecutive lanes share object i and its constants stay in L1.  Claims run
+// from the end of the list: candidates of the highest object indices, which
+// in catalog order are the eccentric and geosynchronous orbits with the
+// longest intervals, start first instead of forming a tail.
 __global__ void __launch_bounds__(kNpThreads, kNpBlocksPerSm) k_narrow(NarrowArgs a) {
   constexpr unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -283,14 +286,15 @@ __global__ void __launch_bounds__(kNpThreads, kNpBlocksPerSm) k_narrow(NarrowArg
         const unsigned long long mine =
             base + (unsigned long long)__popc(idle & ((1u << lane) - 1u));
         if (mine < (unsigned long long)a.m) {
-          const scd_pair c = a.pairs[mine];
+          const int64_t qq = a.m - 1 - (int64_t)mine;
+          const scd_pair c = a.pairs[qq];
           if ((int64_t)c.i >= a.n || (int64_t)c.j >= a.n || c.tlo < 0 || c.tlo > c.thi ||
               (int64_t)c.thi > a.T) {
             err |= NP_ERR_PAIR;
-            if (a.first) a.first[mine] = -1;
-            if (a.count) a.count[mine] = 0;
+            if (a.first) a.first[qq] = -1;
+            if (a.count) a.count[qq] = 0;
           } else {
-            L.q = (int64_t)mine;
+            L.q = qq;
             L.oi = c.i;
             L.oj = c.j;
             L.t = c.tlo;
