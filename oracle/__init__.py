@@ -79,6 +79,8 @@ def lib():
                 "or_raw_cells_tree": (i64, [vp, vp, vp, i64, vp, i64]),
                 "or_alg3": (i32, [vp, i64, i64, d, i32, i64, vp, vp, vp, vp]),
                 "or_narrow_phase": (i64, [vp, i64, vp, i64, d, vp, vp, vp, vp, i64]),
+                "or_refine_discrete": (i64, [vp, i64, i64, d, i32, vp, i64, vp, vp, vp]),
+                "or_refine_continuous": (i64, [vp, i64, d, d, i32, vp, i64, vp, vp]),
                 "or_radial_range": (None, [vp, vp]),
                 "or_band_edges": (None, [vp, i64, i32, vp]),
                 "or_band_counts": (None, [vp, i64, i32, vp]),
@@ -397,6 +399,43 @@ def earliest_witness(wit):
         return None
     o = np.lexsort((wit["j"], wit["i"], wit["t"]))[0]
     return int(wit["i"][o]), int(wit["j"][o]), int(wit["t"][o])
+
+
+SPAN_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("t0", "<f8"), ("t1", "<f8")])
+
+
+def refine_discrete(els, T: int, tick_s: float, mode: int = BOX_SPEED):
+    """Adaptive refinement in bulk-synchronous rounds (Alg 5-6 taken top-down
+    over all objects): returns (witnesses in Alg 1's order, active intervals
+    per round, distinct tick candidates)."""
+    E = _els(els)
+    rb = np.zeros(64, np.int64)
+    rounds = ctypes.c_int(0)
+    ntc = ctypes.c_int64(0)
+    cap = 1 << 12
+    while True:
+        out = np.zeros(cap, WITNESS_DTYPE)
+        k = lib().or_refine_discrete(_p(E), len(E), int(T), float(tick_s), int(mode), _p(out), cap,
+                                     _p(rb), ctypes.byref(rounds), ctypes.byref(ntc))
+        if k <= cap:
+            return out[:k].copy(), rb[:rounds.value].copy(), int(ntc.value)
+        cap = int(k)
+
+
+def refine_continuous(els, T_s: float, eps_s: float, mode: int = BOX_SPEED):
+    """The continuous-time variant (Sec. 4.6): returns (spans (i, j, t0, t1)
+    at resolution eps_s, active intervals per round)."""
+    E = _els(els)
+    rb = np.zeros(64, np.int64)
+    rounds = ctypes.c_int(0)
+    cap = 1 << 12
+    while True:
+        out = np.zeros(cap, SPAN_DTYPE)
+        k = lib().or_refine_continuous(_p(E), len(E), float(T_s), float(eps_s), int(mode),
+                                       _p(out), cap, _p(rb), ctypes.byref(rounds))
+        if k <= cap:
+            return out[:k].copy(), rb[:rounds.value].copy()
+        cap = int(k)
 
 
 # --- decomposition (Sec. 5, Sec. 6.1) ----------------------------------------

@@ -826,6 +826,219 @@ done:
 }
 
 /* ------------------------------------------------------------------------ */
+/* Adaptive refinement in bulk-synchronous rounds: the interval doubling    */
+/* and halving of Alg 5 and Alg 6 taken top-down over all objects at once. */
+/* Every object starts with one interval, the whole horizon.  In a round   */
+/* every active interval gets its 4D box (Def 8); a box that meets no box  */
+/* of another object proves its object collision-free over the interval    */
+/* (every other object's position at those times lies in one of this       */
+/* round's boxes, or was proven free of collisions in an earlier round),   */
+/* so the interval is done; an interval whose box meets another is halved, */
+/* as Alg 6 halves the longer of two overlapping intervals.  Property 2    */
+/* keeps the halves inside the parent box.                                 */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int64_t obj, t0, t1;
+} or_seg;
+
+static void *grow(void *p, int64_t *cap, int64_t need, size_t elem) {
+  if (need <= *cap) return p;
+  int64_t c = *cap > 0 ? *cap : 64;
+  while (c < need) c *= 2;
+  *cap = c;
+  return realloc(p, (size_t)c * elem);
+}
+
+static int cmp_witness_alg1(const void *x, const void *y) {
+  const or_witness *a = (const or_witness *)x, *b = (const or_witness *)y;
+  if (a->t != b->t) return a->t < b->t ? -1 : 1;
+  if (a->i != b->i) return a->i < b->i ? -1 : 1;
+  if (a->j != b->j) return a->j < b->j ? -1 : 1;
+  return 0;
+}
+
+int64_t or_refine_discrete(const double *els, int64_t n, int64_t T, double tick_s, int mode,
+                           or_witness *out, int64_t cap, int64_t *round_boxes, int *rounds,
+                           int64_t *n_tick_candidates) {
+  int64_t m = n, scap = 0, ncap = 0, ccap = 0, nc = 0;
+  or_seg *S = (or_seg *)grow(NULL, &scap, n > 0 ? n : 1, sizeof(or_seg));
+  or_seg *next = NULL;
+  or_witness *cand = NULL;
+  for (int64_t i = 0; i < n; ++i) {
+    S[i].obj = i;
+    S[i].t0 = 0;
+    S[i].t1 = T;
+  }
+  int r = 0;
+  while (m > 0 && r < 64) {
+    if (round_boxes) round_boxes[r] = m;
+    float *lo = (float *)malloc(sizeof(float) * 4 * (size_t)m);
+    float *hi = (float *)malloc(sizeof(float) * 4 * (size_t)m);
+    char *hit = (char *)calloc((size_t)m, 1), *hit_long = (char *)calloc((size_t)m, 1);
+    for (int64_t a = 0; a < m; ++a)
+      or_box(els + 7 * S[a].obj, mode, S[a].t0, S[a].t1, tick_s, lo + 4 * a, hi + 4 * a, NULL,
+             NULL);
+    for (int64_t a = 0; a < m; ++a)
+      for (int64_t b = a + 1; b < m; ++b) {
+        if (S[a].obj == S[b].obj) continue;
+        if (!boxes_overlap(lo + 4 * a, hi + 4 * a, lo + 4 * b, hi + 4 * b)) continue;
+        hit[a] = hit[b] = 1;
+        const int la = S[a].t1 > S[a].t0, lb = S[b].t1 > S[b].t0;
+        if (lb) hit_long[a] = 1;
+        if (la) hit_long[b] = 1;
+        if (!la && !lb) { /* two single ticks (the same tick: the boxes meet in time) */
+          cand = (or_witness *)grow(cand, &ccap, nc + 1, sizeof(or_witness));
+          cand[nc].i = (uint32_t)(S[a].obj < S[b].obj ? S[a].obj : S[b].obj);
+          cand[nc].j = (uint32_t)(S[a].obj < S[b].obj ? S[b].obj : S[a].obj);
+          cand[nc].t = (int32_t)S[a].t0;
+          ++nc;
+        }
+      }
+    int64_t mn = 0;
+    for (int64_t a = 0; a < m; ++a) {
+      if (!hit[a]) continue; /* proven free of collisions over [t0, t1] */
+      if (S[a].t1 > S[a].t0) {
+        const int64_t mid = S[a].t0 + (S[a].t1 - S[a].t0) / 2;
+        next = (or_seg *)grow(next, &ncap, mn + 2, sizeof(or_seg));
+        next[mn].obj = S[a].obj;
+        next[mn].t0 = S[a].t0;
+        next[mn].t1 = mid;
+        next[mn + 1].obj = S[a].obj;
+        next[mn + 1].t0 = mid + 1;
+        next[mn + 1].t1 = S[a].t1;
+        mn += 2;
+      } else if (hit_long[a]) { /* wait for the longer intervals it meets to halve */
+        next = (or_seg *)grow(next, &ncap, mn + 1, sizeof(or_seg));
+        next[mn++] = S[a];
+      }
+    }
+    free(lo);
+    free(hi);
+    free(hit);
+    free(hit_long);
+    or_seg *tmp = S;
+    int64_t tcap = scap;
+    S = next;
+    scap = ncap;
+    next = tmp;
+    ncap = tcap;
+    m = mn;
+    ++r;
+  }
+  if (rounds) *rounds = r;
+  /* tick candidates, once each, then Alg 1's test at the tick */
+  if (nc > 0) qsort(cand, (size_t)nc, sizeof(or_witness), cmp_witness_alg1);
+  int64_t u = 0;
+  for (int64_t q = 0; q < nc; ++q)
+    if (u == 0 || cmp_witness_alg1(&cand[u - 1], &cand[q]) != 0) cand[u++] = cand[q];
+  if (n_tick_candidates) *n_tick_candidates = u;
+  int64_t c = 0;
+  for (int64_t q = 0; q < u; ++q) {
+    const double *ei = els + 7 * (int64_t)cand[q].i, *ej = els + 7 * (int64_t)cand[q].j;
+    double pi[3], pj[3];
+    or_position(ei, (double)cand[q].t * tick_s, pi);
+    or_position(ej, (double)cand[q].t * tick_s, pj);
+    if (!occ_collide(pi, ei[6], pj, ej[6])) continue;
+    if (c < cap) out[c] = cand[q];
+    ++c;
+  }
+  free(S);
+  free(next);
+  free(cand);
+  return c;
+}
+
+/* The continuous-time variant (Sec. 4.6): the same rounds over closed real
+ * intervals, halved down to length eps_s; consecutive halves share their
+ * endpoint (t_min of the second = t_max of the first).  At the finest
+ * level every pair of meeting boxes is reported with the intersection of
+ * the two intervals: any collision at any real time lies in a reported
+ * span (sound without a time step), and with interval boxes the spans'
+ * boxes shrink to the occupancy regions as eps_s goes to 0. */
+static int cmp_span(const void *x, const void *y) {
+  const or_span *a = (const or_span *)x, *b = (const or_span *)y;
+  if (a->i != b->i) return a->i < b->i ? -1 : 1;
+  if (a->j != b->j) return a->j < b->j ? -1 : 1;
+  if (a->t0 != b->t0) return a->t0 < b->t0 ? -1 : 1;
+  if (a->t1 != b->t1) return a->t1 < b->t1 ? -1 : 1;
+  return 0;
+}
+
+int64_t or_refine_continuous(const double *els, int64_t n, double T_s, double eps_s, int mode,
+                             or_span *out, int64_t cap, int64_t *round_boxes, int *rounds) {
+  int L = 0;
+  while (L < 40 && ldexp(T_s, -L) > eps_s) ++L;
+  int64_t m = n, scap = 0, ncap = 0, ocap = 0, no = 0;
+  or_seg *S = (or_seg *)grow(NULL, &scap, n > 0 ? n : 1, sizeof(or_seg));
+  or_seg *next = NULL;
+  or_span *o = NULL;
+  for (int64_t i = 0; i < n; ++i) {
+    S[i].obj = i;
+    S[i].t0 = 0; /* interval [t0, t0 + 1] in units of T_s / 2^level */
+    S[i].t1 = 1;
+  }
+  int r = 0;
+  for (int level = 0; level <= L && m > 0; ++level) {
+    if (round_boxes) round_boxes[r] = m;
+    ++r;
+    const double unit = ldexp(T_s, -level);
+    float *lo = (float *)malloc(sizeof(float) * 4 * (size_t)m);
+    float *hi = (float *)malloc(sizeof(float) * 4 * (size_t)m);
+    char *hit = (char *)calloc((size_t)m, 1);
+    for (int64_t a = 0; a < m; ++a)
+      or_box(els + 7 * S[a].obj, mode, S[a].t0, S[a].t1, unit, lo + 4 * a, hi + 4 * a, NULL,
+             NULL);
+    for (int64_t a = 0; a < m; ++a)
+      for (int64_t b = a + 1; b < m; ++b) {
+        if (S[a].obj == S[b].obj) continue;
+        if (!boxes_overlap(lo + 4 * a, hi + 4 * a, lo + 4 * b, hi + 4 * b)) continue;
+        hit[a] = hit[b] = 1;
+        if (level == L) {
+          o = (or_span *)grow(o, &ocap, no + 1, sizeof(or_span));
+          o[no].i = (uint32_t)(S[a].obj < S[b].obj ? S[a].obj : S[b].obj);
+          o[no].j = (uint32_t)(S[a].obj < S[b].obj ? S[b].obj : S[a].obj);
+          o[no].t0 = (double)(S[a].t0 > S[b].t0 ? S[a].t0 : S[b].t0) * unit;
+          o[no].t1 = (double)(S[a].t1 < S[b].t1 ? S[a].t1 : S[b].t1) * unit;
+          ++no;
+        }
+      }
+    int64_t mn = 0;
+    if (level < L)
+      for (int64_t a = 0; a < m; ++a) {
+        if (!hit[a]) continue;
+        next = (or_seg *)grow(next, &ncap, mn + 2, sizeof(or_seg));
+        next[mn].obj = next[mn + 1].obj = S[a].obj;
+        next[mn].t0 = 2 * S[a].t0;
+        next[mn].t1 = 2 * S[a].t0 + 1;
+        next[mn + 1].t0 = 2 * S[a].t0 + 1;
+        next[mn + 1].t1 = 2 * S[a].t0 + 2;
+        mn += 2;
+      }
+    free(lo);
+    free(hi);
+    free(hit);
+    or_seg *tmp = S;
+    int64_t tcap = scap;
+    S = next;
+    scap = ncap;
+    next = tmp;
+    ncap = tcap;
+    m = mn;
+  }
+  if (rounds) *rounds = r;
+  if (no > 0) qsort(o, (size_t)no, sizeof(or_span), cmp_span);
+  int64_t u = 0;
+  for (int64_t q = 0; q < no; ++q)
+    if (u == 0 || cmp_span(&o[u - 1], &o[q]) != 0) o[u++] = o[q];
+  for (int64_t q = 0; q < u && q < cap; ++q) out[q] = o[q];
+  free(S);
+  free(next);
+  free(o);
+  return u;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Static decomposition: potential-collision graph from perigee/apogee      */
 /* (Sec. 6.1) and altitude bands from every (n/p)-th sorted semi-major axis.*/
 /* ------------------------------------------------------------------------ */

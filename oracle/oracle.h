@@ -131,6 +131,27 @@ int or_alg3(const double *els, int64_t n, int64_t T, double tick_s, int mode,
             int64_t t_first, uint32_t *wi, uint32_t *wj, int64_t *wt,
             int64_t *iterations);
 
+/* --- adaptive refinement (Alg 5-6 in rounds; Sec. 4.6) ------------------- */
+/* one span of the continuous-time variant: objects i < j may meet at some
+ * real time in [t0, t1] seconds */
+typedef struct { uint32_t i, j; double t0, t1; } or_span;
+/* Rounds over all objects' intervals, starting from [0, T] each: a box that
+ * meets no other object's box is done, one that meets another is halved
+ * (ticks [t0, mid], [mid+1, t1]); two single-tick boxes that meet are a
+ * tick candidate.  Returns the witnesses among the tick candidates (Alg 1's
+ * test at the tick), in Alg 1's order (t, i, j); round_boxes[r] = active
+ * intervals of round r (up to 64 rounds), *rounds the rounds taken,
+ * *n_tick_candidates the distinct tick candidates. */
+int64_t or_refine_discrete(const double *els, int64_t n, int64_t T, double tick_s, int mode,
+                           or_witness *out, int64_t cap, int64_t *round_boxes, int *rounds,
+                           int64_t *n_tick_candidates);
+/* The continuous-time variant (Sec. 4.6): closed real intervals halved
+ * down to length <= eps_s, halves sharing their endpoint; every meeting
+ * pair of boxes at that level as (i < j, intersection of the intervals),
+ * sorted, each once.  Returns the span count (only cap written). */
+int64_t or_refine_continuous(const double *els, int64_t n, double T_s, double eps_s, int mode,
+                             or_span *out, int64_t cap, int64_t *round_boxes, int *rounds);
+
 /* --- static decomposition (Sec. 5, Sec. 6.1) ----------------------------- */
 /* padded radial range [a(1-e) - sqrt(3) r, a(1+e) + sqrt(3) r] */
 void or_radial_range(const double *el, double out[2]);

@@ -1,0 +1,126 @@
+"""Pins of the oracle's adaptive refinement: the interval doubling and
+halving of Alg 5 and Alg 6 taken top-down in bulk-synchronous rounds, and
+its continuous-time variant (Sec. 4.6).
+
+The discrete form must find exactly Alg 1's witnesses (soundness of the
+interval occupancy regions, Property 1 at single ticks), its earliest must
+be Alg 3's first witness, far-apart objects must need a number of boxes that
+does not depend on the time step (the paper's case for growing intervals),
+and the rounds are bounded by the halvings of [0, T].  The continuous form
+must cover every discrete witness, find a crossing that falls between two
+ticks (the tunnelling Alg 1 misses), and nest as eps shrinks."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import population as P
+
+
+def _key(w):
+    return sorted(map(tuple, np.asarray(w).tolist()))
+
+
+@pytest.mark.parametrize("mode", [O.BOX_SPEED, O.BOX_INTERVAL])
+@pytest.mark.parametrize("seed", [300, 302, 310, 311])
+def test_discrete_refinement_equals_alg1(mode, seed):
+    els = P.uniform_leo(10, seed=seed, radius_km=400.0)
+    T = 300
+    w, rb, ntc = O.refine_discrete(els, T, 1.0, mode)
+    ref = O.alg1_witnesses(els, T, 1.0)
+    assert _key(w) == _key(ref)
+    assert ntc >= len(w)
+    # Alg 1's order, and the earliest is Alg 1's return value
+    assert w.tolist() == ref.tolist()
+    # every round halves the long intervals: at most ceil(log2(T+1)) + 2 rounds
+    assert len(rb) <= math.ceil(math.log2(T + 1)) + 2
+    if len(ref):
+        rc, w3, _ = O.alg3(els, T, 1.0, mode, int(ref["t"][0]))
+        assert rc == 1 and w3[2] == int(w["t"][0])
+
+
+@pytest.mark.parametrize("mode", [O.BOX_SPEED, O.BOX_INTERVAL])
+def test_far_apart_objects_cost_the_same_at_any_time_step(mode):
+    # a LEO and a GEO orbit never meet; their boxes separate once the
+    # intervals are a fraction of an orbit long, so the rounds and boxes do
+    # not depend on the time step: 100x finer ticks, the same work (where a
+    # fixed-step method does 100x more)
+    els = np.array([[7000.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0],
+                    [42164.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0]])
+    runs = [O.refine_discrete(els, T, tick, mode) for tick, T in ((1.0, 86400), (0.01, 8640000))]
+    for w, rb, ntc in runs:
+        assert len(w) == 0 and ntc == 0
+        assert rb.sum() <= 100
+    assert runs[0][1].tolist() == runs[1][1].tolist()
+
+
+def test_refinement_uses_far_fewer_boxes_than_single_ticks():
+    # a sparse population: most objects are proven free over long intervals
+    els = P.uniform_leo(40, seed=5, radius_km=2.5)
+    T = 3000
+    w, rb, _ = O.refine_discrete(els, T, 1.0, O.BOX_INTERVAL)
+    assert _key(w) == _key(O.alg1_witnesses(els, T, 1.0))
+    assert rb.sum() < 0.1 * len(els) * (T + 1)
+
+
+def test_identical_elements_witness_every_tick():
+    els = P.uniform_leo(4, seed=5)
+    els[2] = els[0]
+    T = 120
+    w, rb, _ = O.refine_discrete(els, T, 1.0, O.BOX_SPEED)
+    mine = w[(w["i"] == 0) & (w["j"] == 2)]
+    assert mine["t"].tolist() == list(range(T + 1))
+
+
+def _crossing_between_ticks(tc=100.5, a=7000.0, r=1.0):
+    """Two circular orbits of radius a in perpendicular planes through the x
+    axis, both at (a, 0, 0) at time tc: distance 0 there, but at the ticks
+    either side (0.5 s away) the infinity-norm distance is a sin(n / 2),
+    about 3.8 km, above r_i + r_j = 2 km."""
+    n = math.sqrt(O.MU / a ** 3)
+    M0 = -n * tc
+    return np.array([[a, 0.0, 0.0, 0.0, 0.0, M0, r],
+                     [a, 0.0, math.pi / 2, 0.0, 0.0, M0, r]])
+
+
+@pytest.mark.parametrize("mode", [O.BOX_SPEED, O.BOX_INTERVAL])
+def test_continuous_finds_the_crossing_alg1_tunnels_through(mode):
+    els = _crossing_between_ticks()
+    T = 200
+    assert len(O.alg1_witnesses(els, T, 1.0)) == 0  # tunnelling at 1 s ticks
+    assert len(O.refine_discrete(els, T, 1.0, mode)[0]) == 0
+    spans, rb = O.refine_continuous(els, float(T), 0.1, mode)
+    assert len(spans) > 0
+    assert np.all(spans["t1"] - spans["t0"] <= 0.1 + 1e-12)
+    assert np.any((spans["t0"] <= 100.5) & (100.5 <= spans["t1"]))
+    # every span lies near the crossing: the boxes shrink with the interval
+    assert spans["t0"].min() > 95.0 and spans["t1"].max() < 106.0
+
+
+@pytest.mark.parametrize("mode", [O.BOX_SPEED, O.BOX_INTERVAL])
+@pytest.mark.parametrize("seed", [300, 310])
+def test_continuous_covers_every_discrete_witness(mode, seed):
+    els = P.uniform_leo(10, seed=seed, radius_km=400.0)
+    T = 300
+    spans, _ = O.refine_continuous(els, float(T), 0.5, mode)
+    for i, j, t in O.alg1_witnesses(els, T, 1.0).tolist():
+        m = spans[(spans["i"] == i) & (spans["j"] == j)]
+        assert np.any((m["t0"] <= t) & (t <= m["t1"])), (i, j, t)
+
+
+def test_continuous_spans_nest_as_eps_shrinks():
+    els = P.uniform_leo(10, seed=300, radius_km=400.0)
+    coarse, _ = O.refine_continuous(els, 300.0, 2.0, O.BOX_INTERVAL)
+    fine, _ = O.refine_continuous(els, 300.0, 0.5, O.BOX_INTERVAL)
+    assert 0 < len(coarse) <= len(fine)
+    for i, j, t0, t1 in fine.tolist():
+        m = coarse[(coarse["i"] == i) & (coarse["j"] == j)]
+        assert np.any((m["t0"] <= t0) & (t1 <= m["t1"]))
+
+
+def test_continuous_robustly_safe_system_is_proven_safe():
+    els = np.array([[7000.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0],
+                    [42164.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0]])
+    spans, rb = O.refine_continuous(els, 86400.0, 0.01, O.BOX_INTERVAL)
+    assert len(spans) == 0 and rb.sum() <= 100
