@@ -88,11 +88,18 @@ WORKLOADS = {
 }
 
 
+# the library sources a screen runs (boxes, sort, hierarchy, traversal,
+# canonical list, scene control): the traversal's DRAM traffic depends on
+# these alone; the narrow phase, the step network and the refinement rounds
+# live in other files and do not run in a screen
+SCREEN_SOURCES = ("decomp.cu", "kepler.cuh", "lbvh.cu", "propagate.cu", "radix_sort.cu",
+                  "scd_internal.cuh", "scene.cu", "traverse.cu")
+
+
 def library_sources():
-    """Every source file of the CUDA library, in name order (the traversal's
-    traffic depends on the tree, the boxes and the default tuning too)."""
+    """The screen's CUDA sources, in name order."""
     d = os.path.join(ROOT, "paper_1901_10475_gb300", "csrc")
-    return [os.path.join(d, f) for f in sorted(os.listdir(d)) if f.endswith((".cu", ".cuh"))]
+    return [os.path.join(d, f) for f in sorted(SCREEN_SOURCES)]
 
 
 def measured_traffic(workload: str):
