@@ -10,6 +10,9 @@ over the max-rank time); ``e2e`` is the same through the C ABI with host
 buffers (elements copied in, pairs copied out inside the timed region).
 
 Other workloads (--workload):
+  refine512   the 512-object, 6000 s population of the parity tests solved by
+              adaptive refinement (Alg 5-6 in rounds), beside the fixed-step
+              screen plus narrow phase
   narrow24h   the default screen followed by the narrow phase over its
               candidates: the first collision witness of the 24 h problem
               (Def 5) from device-resident elements
@@ -74,6 +77,12 @@ WORKLOADS = {
                  "at the candidates' ticks, FP64 positions, ticks skipped by the "
                  "relative-motion bound): per-candidate first witness and witness count and "
                  "the earliest witness (Def 5)")},
+    "refine512": {
+        "metric": "ms per adaptive-refinement solve at n=512, 6000 s (every collision witness)",
+        "desc": ("n=512 uniform LEO (a 6678-8378 km, e < 0.01, i 0-100 deg), r = 2.5 km, 6000 s "
+                 "at 1 s ticks: Alg 5-6 as data-parallel rounds from [0, T] (SPEED boxes, sort "
+                 "and sweep per round), tick candidates decided by the narrow phase; against the "
+                 "fixed 10-tick screen plus the narrow phase on the same population")},
     "batch64": {
         "metric": "scenes per second, 64 scenes, ~1.2M objects, horizons 6-72 h",
         "desc": ("64 independent catalog-shaped scenes, sizes log-uniform 1e3-6e4 (total "
@@ -424,6 +433,92 @@ def run_narrow(args, world):
     return r
 
 
+def run_refine(args, world):
+    """Adaptive refinement on the small workload, and the fixed-step screen
+    plus narrow phase on the same population for comparison."""
+    import torch
+
+    import paper_1901_10475_gb300 as scd
+    dev = _device()
+    els = P.uniform_leo(512)
+    T_S = 6000.0
+    pol = scd.make_step_policy(scd.SCD_STEP_FIXED, fixed_ticks=10)
+    sc = scd.Scene(els, T_S, TICK_S, pol)
+    sc.build_boxes()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return ts, out
+
+    if world > 1:
+        torch.distributed.barrier()
+    with ClockSampler(dev) as clk:
+        times, (w, rb) = timed(lambda: scd.scd_refine_witnesses(sc.handle), args.steps,
+                               args.warmup)
+
+        def fixed():
+            scd.scd_build_boxes(sc.handle)
+            ptr, m = scd.scd_find_pairs_device(sc.handle)
+            return scd.scd_narrow_phase(sc.handle, ptr, m)
+
+        ftimes, earliest = timed(fixed, args.steps, args.warmup)
+    # algorithmic bytes of the rounds: per interval its box (32 B) and sort
+    # key and index (8 B) written, 4 radix passes over key and index (24 B
+    # each), the sweep's read of the box (32 B), the flags (4 B) and the
+    # split's reads and writes (12 + 24 B)
+    per_box = 32 + 8 + 4 * 24 + 32 + 4 + 36
+    byt = int(rb.sum()) * per_box
+    ms = statistics.mean(times)
+    pk, src = _peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    # kernels per timed solve: per round the boxes, 4 radix passes of 3
+    # kernels, the sweep and the split; then the start, two 64-bit sorts (8
+    # passes of 3), the distinct candidates, the narrow phase (3), the
+    # witness keys and their decoding
+    launches = args.steps * (15 * len(rb) + 1 + 48 + 1 + 3 + 1 + 1)
+    r = {"times": times, "clocks": clk.summary(), "unit": "ms", "higher_is_better": False,
+         "value": slowest_rank(sum(times), world) / (args.steps * world),
+         "launches": launches, "n": len(els)}
+    r["refine"] = {"rounds": int(len(rb)), "intervals_per_round": [int(x) for x in rb],
+                   "boxes": int(rb.sum()), "witnesses": int(len(w)),
+                   "earliest_witness": [int(x) for x in w[0]] if len(w) else None,
+                   "fixed_step_ms": statistics.mean(ftimes),
+                   "fixed_step_boxes": 512 * 601,
+                   "fixed_step_earliest": list(earliest) if earliest else None}
+    r["roofline_refine"] = {"kernel_phase": "refinement rounds", "bound": "hbm",
+                            "achieved": byt / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                            "frac": byt / (ms * 1e-3) / 1e9 / hbm, "traffic": None,
+                            "peak_source": src, "algorithmic_bytes": byt}
+    # end to end through the ABI: host elements in, witnesses out
+    host_in = torch.as_tensor(np.ascontiguousarray(els)).pin_memory()
+    ts = []
+    for q in range(max(1, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        scd._binding.lib().scd_scene_set_elements(sc.handle, ctypes.c_void_p(host_in.data_ptr()),
+                                                  len(els))
+        scd.scd_build_boxes(sc.handle)
+        w2, _ = scd.scd_refine_witnesses(sc.handle)
+        ts.append((time.perf_counter() - t0) * 1e3)
+    r["e2e"] = {"value": statistics.median(ts), "unit": "ms", "h2d_bytes_per_step": 56 * len(els),
+                "d2h_bytes_per_step": 12 * len(w2)}
+    sc.close()
+    return r
+
+
 def _candidate_ticks(ptr, m):
     """Sum of thi - tlo + 1 over a device candidate list."""
     import paper_1901_10475_gb300 as scd
@@ -642,6 +737,8 @@ def main():
         r = run_single(args, world, wl)
     elif wl == "narrow24h":
         r = run_narrow(args, world)
+    elif wl == "refine512":
+        r = run_refine(args, world)
     elif wl == "batch64":
         r = run_batch64(args, world)
     else:
@@ -659,7 +756,8 @@ def main():
         "ms_per_step": statistics.mean(r["times"]), "higher_is_better": r["higher_is_better"],
         "scaling": "weak", "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
         "config": {"workload": desc,
-                   "l2": "flushed between steps (writes 2x L2); working set > 1 GB"},
+                   "l2": ("flushed between steps (writes 2x L2)" if wl == "refine512" else
+                          "flushed between steps (writes 2x L2); working set > 1 GB")},
     }
     pk, src = _peaks()
     if "metrics" in r:
@@ -703,8 +801,10 @@ def main():
         line["e2e"] = r["e2e"]
     if "gpu_launches" not in line and r.get("launches") is not None:
         line["gpu_launches"] = r["launches"]
+    if "roofline_refine" in r:
+        line["roofline"] = r["roofline_refine"]
     for k in ("latency_ms", "batches", "objects", "boxes_est", "ms_per_pass", "p100_ms",
-              "p100_boxes", "p100_pairs", "training", "tuning", "narrow"):
+              "p100_boxes", "p100_pairs", "training", "tuning", "narrow", "refine"):
         if k in r and r[k] is not None:
             line[k] = r[k]
     line["clocks"] = r["clocks"]

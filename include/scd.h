@@ -245,6 +245,30 @@ typedef struct {
 SCD_API int scd_narrow_phase(scd_scene *s, const scd_pair *d_pairs, int64_t n_pairs,
                              int32_t *d_first, uint32_t *d_count, scd_witness *earliest);
 
+/* Adaptive refinement: the interval growing and halving of Alg 5 and Alg 6
+ * as data-parallel rounds over all of the scene's objects.  Every object
+ * starts with [0, T]; each round builds the 4D box (Def 8; SPEED boxes,
+ * whatever the scene's box mode) of every active interval; an interval
+ * whose box meets no other object's box is proven collision-free and
+ * dropped, one that meets another is halved (ticks [t0, mid], [mid+1, t1]),
+ * a single tick that still meets a longer interval waits; two single-tick
+ * boxes that meet are a tick candidate, decided by Alg 1's test through
+ * scd_narrow_phase.  The result is every collision witness (Def 4) of
+ * ticks 0..T, sorted in Alg 1's order (t, then i, then j): the first is the
+ * answer of Def 5.  The per-object step policy of the scene plays no part.
+ *   host_out     host array of cap witnesses (may be NULL if cap == 0).
+ *   n_out        the witness count; cap too small: SCD_ERR_BUFFER_TOO_SMALL
+ *                with *n_out set and nothing written.
+ *   round_boxes  host array of 64 (or NULL): active intervals per round.
+ *   rounds       (or NULL): the rounds taken, at most ceil(log2(T+1)) + 2.
+ * Needs scd_build_boxes (the per-object constants): else SCD_ERR_STATE.
+ * Batches of scenes: SCD_ERR_INVALID_ARG.  n > 2^20: SCD_ERR_CAPACITY.
+ * Meeting boxes are found by a sort on the lower x face and a sweep, work
+ * that grows with the boxes each box's x range covers: meant for
+ * populations up to some thousands of objects.  Synchronous. */
+SCD_API int scd_refine_witnesses(scd_scene *s, scd_witness *host_out, int64_t cap,
+                                 int64_t *n_out, int64_t *round_boxes, int *rounds);
+
 /* The scene's boxes in object-major, segment order (device pointers owned
  * by the scene): lo4/hi4 are nbox x 4 floats (x, y, z [km], tick), obj the
  * object of each box. */

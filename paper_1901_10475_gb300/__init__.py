@@ -19,7 +19,8 @@ from ._binding import (PAIR_DTYPE, SCD_BOX_INTERVAL, SCD_BOX_SPEED, SCD_DECOMP_A
                        scd_batch_find_pairs, scd_build_boxes, scd_default_tuning,
                        scd_find_pairs, scd_find_pairs_device, scd_find_pairs_into,
                        scd_find_raw_cells_device,
-                       scd_get_boxes, scd_get_steps, scd_last_metrics, scd_narrow_phase,
+                       WITNESS_DTYPE, scd_get_boxes, scd_get_steps, scd_last_metrics,
+                       scd_narrow_phase, scd_refine_witnesses,
                        scd_propagate,
                        scd_propagate_noalloc,
                        scd_scene_create, scd_scene_destroy, scd_scene_set_elements,
@@ -31,7 +32,7 @@ for _n in dir(B):  # every entry point and constant under its C name
         globals()[_n] = getattr(B, _n)
 
 __all__ = [n for n in dir(B) if n.startswith("scd_") or n.startswith("SCD_")] + [
-    "Scene", "device_view", "PAIR_DTYPE", "ScdError", "make_step_policy"]
+    "Scene", "device_view", "PAIR_DTYPE", "WITNESS_DTYPE", "ScdError", "make_step_policy"]
 
 
 class _CudaArray:
@@ -108,6 +109,12 @@ class Scene:
         w = scd_narrow_phase(self.handle, pairs.data_ptr() if m else 0, m,
                              first.data_ptr() if m else 0, count.data_ptr() if m else 0)
         return first, count, w
+
+    def refine_witnesses(self):
+        """Every collision witness (i, j, t) by adaptive refinement, in Alg
+        1's order, and the active intervals of each round (needs
+        build_boxes)."""
+        return scd_refine_witnesses(self.handle)
 
     def boxes(self):
         lo, hi, obj, n = scd_get_boxes(self.handle)

@@ -104,6 +104,7 @@ def lib() -> ctypes.CDLL:
             "scd_find_raw_cells_device": (i32, [vp, P(vp), P(i64)]),
             "scd_get_boxes": (i32, [vp, P(vp), P(vp), P(vp), P(i64)]),
             "scd_narrow_phase": (i32, [vp, vp, i64, vp, vp, P(scd_witness)]),
+            "scd_refine_witnesses": (i32, [vp, vp, i64, P(i64), vp, P(i32)]),
             "scd_get_steps": (i32, [vp, P(vp)]),
             "scd_propagate": (i32, [vp, i64, vp, vp, i64, vp, vp]),
             "scd_propagate_noalloc": (i32, [vp, i64, vp, vp, i64, vp, vp]),
@@ -291,6 +292,27 @@ def scd_narrow_phase(scene: int, d_pairs: int, n_pairs: int, d_first: int = 0,
     check(lib().scd_narrow_phase(scene, d_pairs or None, int(n_pairs), d_first or None,
                                  d_count or None, ctypes.byref(w)), "scd_narrow_phase")
     return None if w.t < 0 else (int(w.i), int(w.j), int(w.t))
+
+
+WITNESS_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("t", "<i4")])
+
+
+def scd_refine_witnesses(scene: int, cap: int = 1 << 16):
+    """Every collision witness of the scene by adaptive refinement, in Alg
+    1's order (a numpy WITNESS_DTYPE array), and the active intervals of
+    each round."""
+    n = ctypes.c_int64(0)
+    rounds = ctypes.c_int(0)
+    rb = np.zeros(64, np.int64)
+    while True:
+        out = np.zeros(max(cap, 1), WITNESS_DTYPE)
+        rc = lib().scd_refine_witnesses(scene, out.ctypes.data, cap, ctypes.byref(n),
+                                        rb.ctypes.data, ctypes.byref(rounds))
+        if rc == SCD_ERR_BUFFER_TOO_SMALL:
+            cap = int(n.value)
+            continue
+        check(rc, "scd_refine_witnesses")
+        return out[:n.value].copy(), rb[:rounds.value].copy()
 
 
 def scd_get_boxes(scene: int):

@@ -1,0 +1,116 @@
+"""Parity of the CUDA adaptive refinement (scd_refine_witnesses, through the
+C ABI) with the oracle: the witness list is exact (Alg 1's test decides every
+tick candidate), so it must equal the oracle's refinement and Alg 1 witness
+for witness, in Alg 1's order.  The rounds' interval counts come from
+overlap tests of FP32 boxes whose centres agree with the oracle's to 1e-7 km,
+so they may differ where two boxes touch; they must agree within 2%."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import population as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def scd():
+    import paper_1901_10475_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+def _scene(scd, els, horizon_s, mode=0):
+    step = scd.make_step_policy(scd.SCD_STEP_FIXED, fixed_ticks=10)
+    return scd.Scene(els, horizon_s, 1.0, step=step, mode=mode).build_boxes()
+
+
+def _tuples(w):
+    return [(int(a), int(b), int(c)) for a, b, c in w.tolist()]
+
+
+@pytest.mark.parametrize("seed", [300, 302, 310, 311])
+def test_small_large_radii_equal_alg1_and_oracle(scd, seed):
+    els = P.uniform_leo(10, seed=seed, radius_km=400.0)
+    T = 300
+    sc = _scene(scd, els, float(T))
+    w, rb = sc.refine_witnesses()
+    ref = O.alg1_witnesses(els, T, 1.0)
+    assert _tuples(w) == _tuples(ref)
+    ow, orb, _ = O.refine_discrete(els, T, 1.0, O.BOX_SPEED)
+    assert len(rb) <= math.ceil(math.log2(T + 1)) + 2
+    assert abs(int(rb.sum()) - int(orb.sum())) <= 0.02 * orb.sum()
+    sc.close()
+
+
+def test_uniform_512_six_thousand_seconds(scd):
+    # the small workload's population (n = 512, 6000 s), with one pair of
+    # identical elements that collide at every tick
+    els = P.uniform_leo(512)
+    els[511] = els[7]
+    sc = _scene(scd, els, 6000.0)
+    w, rb = sc.refine_witnesses()
+    ow, orb, _ = O.refine_discrete(els, 6000, 1.0, O.BOX_SPEED)
+    assert _tuples(w) == _tuples(ow)
+    mine = w[(w["i"] == 7) & (w["j"] == 511)]
+    assert mine["t"].tolist() == list(range(6001))
+    assert len(rb) == len(orb)
+    assert abs(int(rb.sum()) - int(orb.sum())) <= 0.02 * orb.sum()
+    # an INTERVAL-mode scene refines with the same SPEED boxes
+    sc2 = _scene(scd, els, 6000.0, mode=1)
+    w2, rb2 = sc2.refine_witnesses()
+    assert _tuples(w2) == _tuples(w) and rb2.tolist() == rb.tolist()
+    sc.close()
+    sc2.close()
+
+
+def test_catalog_mixture_crossings(scd):
+    els, cr = P.catalog_mixture(n=2000, seed=21, crossing_frac=0.004, horizon_s=1800.0,
+                                return_crossings=True)
+    T = 1800
+    sc = _scene(scd, els, float(T))
+    w, rb = sc.refine_witnesses()
+    ref = O.alg1_sweep(els, 0, T, 1.0)
+    assert sorted(_tuples(w)) == sorted((int(a), int(b), int(c)) for a, b, c, _ in ref.tolist())
+    got = set(_tuples(w))
+    for (b, c, tc) in cr:
+        assert (b, c, tc) in got
+    # the same witnesses as the narrow phase over the fixed-step screen's
+    # candidates (P/100 steps): both are exact
+    step = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=100.0)
+    sc2 = scd.Scene(els, float(T), 1.0, step=step).build_boxes()
+    first, count, earliest = sc2.narrow_phase(sc2.find_pairs_device())
+    assert int(count.cpu().numpy().astype(np.int64).sum()) == len(w)
+    assert earliest == (tuple(_tuples(w[:1])[0]) if len(w) else None)
+    sc.close()
+    sc2.close()
+
+
+def test_far_apart_orbits_and_errors(scd):
+    els = np.array([[7000.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0],
+                    [42164.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0]])
+    step = scd.make_step_policy(scd.SCD_STEP_FIXED, fixed_ticks=10)
+    sc = scd.Scene(els, 86400.0, 1.0, step=step)
+    with pytest.raises(scd.ScdError) as e:
+        sc.refine_witnesses()  # boxes not built yet
+    assert e.value.status == scd.SCD_ERR_STATE
+    sc.build_boxes()
+    w, rb = sc.refine_witnesses()
+    _, orb, _ = O.refine_discrete(els, 86400, 1.0, O.BOX_SPEED)
+    assert len(w) == 0 and rb.tolist() == orb.tolist()
+    sc.close()
+    # a buffer too small reports the count needed and writes nothing
+    els = P.uniform_leo(4, seed=5)
+    els[2] = els[0]
+    sc = _scene(scd, els, 50.0)
+    import ctypes
+    n = ctypes.c_int64(0)
+    out = np.zeros(4, scd.WITNESS_DTYPE)
+    rc = scd._binding.lib().scd_refine_witnesses(sc.handle, out.ctypes.data, 4, ctypes.byref(n),
+                                                 None, None)
+    assert rc == scd.SCD_ERR_BUFFER_TOO_SMALL and n.value == 51
+    assert not out.view(np.int32).any()
+    sc.close()
