@@ -269,6 +269,26 @@ SCD_API int scd_narrow_phase(scd_scene *s, const scd_pair *d_pairs, int64_t n_pa
 SCD_API int scd_refine_witnesses(scd_scene *s, scd_witness *host_out, int64_t cap,
                                  int64_t *n_out, int64_t *round_boxes, int *rounds);
 
+/* One span of the continuous-time variant: objects i < j may meet at some
+ * real time in [t0, t1] seconds. */
+typedef struct {
+  uint32_t i, j;
+  double t0, t1;
+} scd_span;
+
+/* The continuous-time variant of the refinement (Sec. 4.6): the same rounds
+ * over closed real intervals, starting from [0, T tick_s] seconds, halved
+ * into [t0, mid] and [mid, t1] (the halves share their endpoint), down to
+ * the first length <= eps_s; every pair of meeting boxes at that level is
+ * one span, the intersection of the two intervals (an instant where two
+ * consecutive intervals meet).  No time step: a collision at any real time
+ * lies in a span.  SPEED boxes.  Spans sorted by (i, j, t0, t1), each once.
+ *   host_out, cap, n_out, round_boxes, rounds: as scd_refine_witnesses.
+ * eps_s <= 0: SCD_ERR_INVALID_ARG; eps_s below T tick_s / 2^22:
+ * SCD_ERR_CAPACITY.  Needs scd_build_boxes.  Synchronous. */
+SCD_API int scd_refine_continuous(scd_scene *s, double eps_s, scd_span *host_out, int64_t cap,
+                                  int64_t *n_out, int64_t *round_boxes, int *rounds);
+
 /* The scene's boxes in object-major, segment order (device pointers owned
  * by the scene): lo4/hi4 are nbox x 4 floats (x, y, z [km], tick), obj the
  * object of each box. */

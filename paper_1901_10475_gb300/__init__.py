@@ -20,7 +20,8 @@ from ._binding import (PAIR_DTYPE, SCD_BOX_INTERVAL, SCD_BOX_SPEED, SCD_DECOMP_A
                        scd_find_pairs, scd_find_pairs_device, scd_find_pairs_into,
                        scd_find_raw_cells_device,
                        WITNESS_DTYPE, scd_get_boxes, scd_get_steps, scd_last_metrics,
-                       scd_narrow_phase, scd_refine_witnesses,
+                       scd_narrow_phase, scd_refine_continuous, scd_refine_witnesses,
+                       SPAN_DTYPE,
                        scd_propagate,
                        scd_propagate_noalloc,
                        scd_scene_create, scd_scene_destroy, scd_scene_set_elements,
@@ -32,7 +33,8 @@ for _n in dir(B):  # every entry point and constant under its C name
         globals()[_n] = getattr(B, _n)
 
 __all__ = [n for n in dir(B) if n.startswith("scd_") or n.startswith("SCD_")] + [
-    "Scene", "device_view", "PAIR_DTYPE", "WITNESS_DTYPE", "ScdError", "make_step_policy"]
+    "Scene", "device_view", "PAIR_DTYPE", "WITNESS_DTYPE", "SPAN_DTYPE", "ScdError",
+    "make_step_policy"]
 
 
 class _CudaArray:
@@ -115,6 +117,11 @@ class Scene:
         1's order, and the active intervals of each round (needs
         build_boxes)."""
         return scd_refine_witnesses(self.handle)
+
+    def refine_continuous(self, eps_s: float):
+        """Spans (i, j, t0, t1) of the continuous-time refinement down to
+        intervals of eps_s seconds, and the active intervals per round."""
+        return scd_refine_continuous(self.handle, eps_s)
 
     def boxes(self):
         lo, hi, obj, n = scd_get_boxes(self.handle)

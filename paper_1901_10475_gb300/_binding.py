@@ -105,6 +105,7 @@ def lib() -> ctypes.CDLL:
             "scd_get_boxes": (i32, [vp, P(vp), P(vp), P(vp), P(i64)]),
             "scd_narrow_phase": (i32, [vp, vp, i64, vp, vp, P(scd_witness)]),
             "scd_refine_witnesses": (i32, [vp, vp, i64, P(i64), vp, P(i32)]),
+            "scd_refine_continuous": (i32, [vp, d, vp, i64, P(i64), vp, P(i32)]),
             "scd_get_steps": (i32, [vp, P(vp)]),
             "scd_propagate": (i32, [vp, i64, vp, vp, i64, vp, vp]),
             "scd_propagate_noalloc": (i32, [vp, i64, vp, vp, i64, vp, vp]),
@@ -312,6 +313,26 @@ def scd_refine_witnesses(scene: int, cap: int = 1 << 16):
             cap = int(n.value)
             continue
         check(rc, "scd_refine_witnesses")
+        return out[:n.value].copy(), rb[:rounds.value].copy()
+
+
+SPAN_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("t0", "<f8"), ("t1", "<f8")])
+
+
+def scd_refine_continuous(scene: int, eps_s: float, cap: int = 1 << 16):
+    """The continuous-time refinement's spans (i, j, t0, t1) at resolution
+    eps_s (a numpy SPAN_DTYPE array), and the active intervals per round."""
+    n = ctypes.c_int64(0)
+    rounds = ctypes.c_int(0)
+    rb = np.zeros(64, np.int64)
+    while True:
+        out = np.zeros(max(cap, 1), SPAN_DTYPE)
+        rc = lib().scd_refine_continuous(scene, float(eps_s), out.ctypes.data, cap,
+                                         ctypes.byref(n), rb.ctypes.data, ctypes.byref(rounds))
+        if rc == SCD_ERR_BUFFER_TOO_SMALL:
+            cap = int(n.value)
+            continue
+        check(rc, "scd_refine_continuous")
         return out[:n.value].copy(), rb[:rounds.value].copy()
 
 

@@ -109,7 +109,18 @@ struct RfSweepArgs {
   unsigned long long *cand;
   int64_t cap;
   unsigned long long *state;
+  int spans;  // continuous variant, finest level: every meeting pair is a span
 };
+
+// span key of two meeting intervals [ka, ka + 1], [kb, kb + 1] of one level:
+// i (20 bits) | j (20) | the later start (22) | whether the starts agree (1);
+// sorts by (i, j, t0, t1) of the intersection
+__device__ __forceinline__ unsigned long long rf_span_key(uint32_t i, uint32_t j, int32_t ka,
+                                                          int32_t kb) {
+  const uint32_t km = (uint32_t)max(ka, kb), same = ka == kb ? 1u : 0u;
+  return ((unsigned long long)i << 44) | ((unsigned long long)j << 24) |
+         ((unsigned long long)km << 1) | same;
+}
 
 // One thread per interval a (in sorted order): every interval after it
 // whose lower x face is at most a's upper x face meets a on x (a's lower
@@ -136,7 +147,11 @@ __global__ void __launch_bounds__(kRfThreads) k_rf_sweep(RfSweepArgs a) {
     const bool longb = a.t1[ib] > a.t0[ib];
     fa |= RF_HIT | (longb ? RF_HIT_LONG : 0u);
     atomicOr(&a.flags[ib], RF_HIT | (longa ? RF_HIT_LONG : 0u));
-    if (!longa && !longb) {  // two single ticks meet: the same tick
+    if (a.spans) {
+      const unsigned long long q = atomicAdd(&a.state[RF_NCAND], 1ull);
+      if (q < (unsigned long long)a.cap)
+        a.cand[q] = rf_span_key(min(oa, ob), max(oa, ob), ta, a.t0[ib]);
+    } else if (!longa && !longb) {  // two single ticks meet: the same tick
       const unsigned long long q = atomicAdd(&a.state[RF_NCAND], 1ull);
       if (q < (unsigned long long)a.cap)
         a.cand[q] = rf_key((uint32_t)ta, min(oa, ob), max(oa, ob));
@@ -174,6 +189,49 @@ __global__ void __launch_bounds__(kRfThreads) k_rf_split(const uint32_t *__restr
     nt0[q] = a0;
     nt1[q] = a1;
   }
+}
+
+// continuous variant: both halves of an interval [k, k + 1] that met, as
+// [2k, 2k + 1] and [2k + 1, 2k + 2] in units of the next level
+__global__ void __launch_bounds__(kRfThreads) k_rf_split_cont(const uint32_t *__restrict__ obj,
+                                                              const int32_t *__restrict__ t0,
+                                                              const uint32_t *__restrict__ flags,
+                                                              int64_t M, uint32_t *nobj,
+                                                              int32_t *nt0, int32_t *nt1,
+                                                              unsigned long long *state) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M || !(flags[i] & RF_HIT)) return;
+  const unsigned long long q = atomicAdd(&state[RF_NNEXT], 2ull);
+  const int32_t k = t0[i];
+  nobj[q] = obj[i];
+  nt0[q] = 2 * k;
+  nt1[q] = 2 * k + 1;
+  nobj[q + 1] = obj[i];
+  nt0[q + 1] = 2 * k + 1;
+  nt1[q + 1] = 2 * k + 2;
+}
+
+// distinct span keys (sorted) appended to out (in any order)
+__global__ void k_rf_distinct(const unsigned long long *__restrict__ key, int64_t n,
+                              unsigned long long *out, unsigned long long *state) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  if (q > 0 && key[q - 1] == key[q]) return;
+  out[atomicAdd(&state[RF_NUNIQ], 1ull)] = key[q];
+}
+
+__global__ void k_rf_span_decode(const unsigned long long *__restrict__ key, int64_t n,
+                                 double unit, scd_span *out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const unsigned long long k = key[q];
+  const uint32_t km = (uint32_t)((k >> 1) & 0x3fffffull);
+  scd_span sp;
+  sp.i = (uint32_t)(k >> 44);
+  sp.j = (uint32_t)((k >> 24) & 0xfffffull);
+  sp.t0 = (double)km * unit;
+  sp.t1 = (double)(km + (uint32_t)(k & 1ull)) * unit;
+  out[q] = sp;
 }
 
 // distinct tick candidates (sorted keys) as one-tick candidate pairs
@@ -223,6 +281,7 @@ struct RfBuffers {
   DevBuf<uint32_t> count, sort_err;
   DevBuf<scd_pair> pairs;
   DevBuf<scd_witness> wit;
+  DevBuf<scd_span> span;
   SortScratch sc;
   explicit RfBuffers(cudaStream_t s) : st(s) {}
   ~RfBuffers() {
@@ -234,6 +293,7 @@ struct RfBuffers {
     key.release(st); idx.release(st); flags.release(st); first.release(st);
     lo.release(st); hi.release(st); cand.release(st); state.release(st); wkey.release(st);
     count.release(st); sort_err.release(st); pairs.release(st); wit.release(st);
+    span.release(st);
     sc.release(st);
   }
 };
@@ -300,7 +360,7 @@ extern "C" SCD_API int scd_refine_witnesses(scd_scene *s, scd_witness *host_out,
           cudaSuccess)
         return SCD_ERR_CUDA;
       RfSweepArgs sa{B.lo.p, B.hi.p, B.obj[cur].p, B.t0[cur].p, B.t1[cur].p, B.idx.p, M,
-                     B.flags.p, B.cand.p, ccap, B.state.p};
+                     B.flags.p, B.cand.p, ccap, B.state.p, 0};
       k_rf_sweep<<<grid_of(M), kRfThreads, 0, st>>>(sa);
       note_launch();
       if ((rc = rf_read_state(B, h)) != SCD_OK) return rc;
@@ -360,6 +420,129 @@ extern "C" SCD_API int scd_refine_witnesses(scd_scene *s, scd_witness *host_out,
   if (nw > cap) return SCD_ERR_BUFFER_TOO_SMALL;
   if (nw > 0 &&
       (cudaMemcpyAsync(host_out, B.wit.p, sizeof(scd_witness) * (size_t)nw, cudaMemcpyDeviceToHost,
+                       st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    return SCD_ERR_CUDA;
+  return SCD_OK;
+}
+
+namespace scd {
+// levels of the continuous variant: interval starts take 22 bits of a span key
+constexpr int kRfMaxLevels = 22;
+
+// boxes, sort and sweep of one round (with a larger candidate buffer when
+// the round's candidates do not fit); h receives the state words
+static int rf_round(scd_scene *s, RfBuffers &B, int cur, int64_t M, double tick_s, int spans,
+                    int64_t &ncand, int64_t &ccap, unsigned long long h[RF_WORDS]) {
+  cudaStream_t st = B.st;
+  RfBoxArgs ba{s->d_par.p, B.obj[cur].p, B.t0[cur].p, B.t1[cur].p, M, tick_s,
+               B.lo.p, B.hi.p, B.key.p, B.idx.p, B.state.p};
+  k_rf_boxes<<<grid_of(M), kRfThreads, 0, st>>>(ba);
+  note_launch();
+  int rc = radix_sort_u32(B.key.p, B.idx.p, M, 32, B.sc, st);
+  if (rc != SCD_OK) return rc;
+  for (;;) {
+    if (cudaMemsetAsync(B.flags.p, 0, sizeof(uint32_t) * (size_t)M, st) != cudaSuccess)
+      return SCD_ERR_CUDA;
+    const unsigned long long nc0 = (unsigned long long)ncand;
+    if (cudaMemcpyAsync(B.state.p + RF_NCAND, &nc0, sizeof(nc0), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+      return SCD_ERR_CUDA;
+    RfSweepArgs sa{B.lo.p, B.hi.p, B.obj[cur].p, B.t0[cur].p, B.t1[cur].p, B.idx.p, M,
+                   B.flags.p, B.cand.p, ccap, B.state.p, spans};
+    k_rf_sweep<<<grid_of(M), kRfThreads, 0, st>>>(sa);
+    note_launch();
+    if ((rc = rf_read_state(B, h)) != SCD_OK) return rc;
+    if ((int64_t)h[RF_NCAND] <= ccap) break;
+    const int64_t want = (int64_t)h[RF_NCAND] * 2;
+    if (!B.cand.grow_keep(want, ncand, st)) return SCD_ERR_OOM;
+    ccap = want;
+  }
+  ncand = (int64_t)h[RF_NCAND];
+  return SCD_OK;
+}
+}  // namespace scd
+
+extern "C" SCD_API int scd_refine_continuous(scd_scene *s, double eps_s, scd_span *host_out,
+                                             int64_t cap, int64_t *n_out, int64_t *round_boxes,
+                                             int *rounds) {
+  if (!s || !n_out || cap < 0 || (cap > 0 && !host_out) || !(eps_s > 0.0))
+    return SCD_ERR_INVALID_ARG;
+  if (!s->boxes_built) return SCD_ERR_STATE;
+  if (s->n_scenes > 0) return SCD_ERR_INVALID_ARG;
+  if (s->n > kRfMaxObjects) return SCD_ERR_CAPACITY;
+  const double T_s = (double)s->T * s->tick_s;
+  int L = 0;
+  while (L <= kRfMaxLevels && ldexp(T_s, -L) > eps_s) ++L;
+  if (L > kRfMaxLevels) return SCD_ERR_CAPACITY;  // eps_s below T / 2^22
+  cudaStream_t st = s->stream;
+  RfBuffers B(st);
+  const int64_t n = s->n;
+  if (!B.state.ensure(RF_WORDS, st) || !B.sort_err.ensure(1, st)) return SCD_ERR_OOM;
+  if (cudaMemsetAsync(B.state.p, 0, sizeof(unsigned long long) * RF_WORDS, st) != cudaSuccess ||
+      cudaMemsetAsync(B.sort_err.p, 0, sizeof(uint32_t), st) != cudaSuccess)
+    return SCD_ERR_CUDA;
+  B.sc.err = B.sort_err.p;
+  int cur = 0;
+  if (!B.obj[0].ensure(n, st) || !B.t0[0].ensure(n, st) || !B.t1[0].ensure(n, st))
+    return SCD_ERR_OOM;
+  k_rf_init<<<grid_of(n), kRfThreads, 0, st>>>(n, 1, B.obj[0].p, B.t0[0].p, B.t1[0].p);
+  note_launch();
+  int64_t M = n, ncand = 0, ccap = 1 << 16;
+  if (!B.cand.ensure(ccap, st)) return SCD_ERR_OOM;
+  unsigned long long h[RF_WORDS] = {};
+  int r = 0;
+  for (int level = 0; level <= L && M > 0; ++level, ++r) {
+    if (round_boxes) round_boxes[r] = M;
+    const int nx = cur ^ 1;
+    if (!B.lo.ensure(M, st) || !B.hi.ensure(M, st) || !B.key.ensure(M, st) ||
+        !B.idx.ensure(M, st) || !B.flags.ensure(M, st) || !B.obj[nx].ensure(2 * M, st) ||
+        !B.t0[nx].ensure(2 * M, st) || !B.t1[nx].ensure(2 * M, st))
+      return SCD_ERR_OOM;
+    int rc = rf_round(s, B, cur, M, ldexp(T_s, -level), level == L, ncand, ccap, h);
+    if (rc != SCD_OK) return rc;
+    if (level == L) {
+      ++r;
+      break;
+    }
+    const unsigned long long zero = 0;
+    if (cudaMemcpyAsync(B.state.p + RF_NNEXT, &zero, sizeof(zero), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+      return SCD_ERR_CUDA;
+    k_rf_split_cont<<<grid_of(M), kRfThreads, 0, st>>>(B.obj[cur].p, B.t0[cur].p, B.flags.p, M,
+                                                      B.obj[nx].p, B.t0[nx].p, B.t1[nx].p,
+                                                      B.state.p);
+    note_launch();
+    if ((rc = rf_read_state(B, h)) != SCD_OK) return rc;
+    M = (int64_t)h[RF_NNEXT];
+    cur = nx;
+  }
+  if (rounds) *rounds = r;
+  if (h[RF_ERR]) return SCD_ERR_KEPLER_NOCONV;
+  int64_t nu = 0;
+  if (ncand > 0) {  // spans of the finest level: distinct, in (i, j, t0, t1) order
+    int rc = radix_sort_u64(B.cand.p, nullptr, ncand, 64, B.sc, st);
+    if (rc != SCD_OK) return rc;
+    if (!B.wkey.ensure(ncand, st)) return SCD_ERR_OOM;
+    k_rf_distinct<<<grid_of(ncand), kRfThreads, 0, st>>>(B.cand.p, ncand, B.wkey.p, B.state.p);
+    note_launch();
+    if ((rc = rf_read_state(B, h)) != SCD_OK) return rc;
+    nu = (int64_t)h[RF_NUNIQ];
+    if ((rc = radix_sort_u64(B.wkey.p, nullptr, nu, 64, B.sc, st)) != SCD_OK) return rc;
+    if (!B.span.ensure(nu, st)) return SCD_ERR_OOM;
+    k_rf_span_decode<<<grid_of(nu), kRfThreads, 0, st>>>(B.wkey.p, nu, ldexp(T_s, -L), B.span.p);
+    note_launch();
+  }
+  uint32_t serr = 0;
+  if (cudaMemcpyAsync(&serr, B.sort_err.p, sizeof(serr), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SCD_ERR_CUDA;
+  if (serr) return SCD_ERR_TIMEOUT;
+  *n_out = nu;
+  if (nu > cap) return SCD_ERR_BUFFER_TOO_SMALL;
+  if (nu > 0 &&
+      (cudaMemcpyAsync(host_out, B.span.p, sizeof(scd_span) * (size_t)nu, cudaMemcpyDeviceToHost,
                        st) != cudaSuccess ||
        cudaStreamSynchronize(st) != cudaSuccess))
     return SCD_ERR_CUDA;

@@ -114,3 +114,44 @@ def test_far_apart_orbits_and_errors(scd):
     assert rc == scd.SCD_ERR_BUFFER_TOO_SMALL and n.value == 51
     assert not out.view(np.int32).any()
     sc.close()
+
+
+def _crossing_between_ticks(tc=100.5, a=7000.0, r=1.0):
+    # two circular orbits in perpendicular planes, both at (a, 0, 0) at tc,
+    # about 3.8 km apart (infinity norm) at the ticks either side
+    n = math.sqrt(O.MU / a ** 3)
+    return np.array([[a, 0.0, 0.0, 0.0, 0.0, -n * tc, r],
+                     [a, 0.0, math.pi / 2, 0.0, 0.0, -n * tc, r]])
+
+
+def test_continuous_finds_crossing_between_ticks(scd):
+    els = _crossing_between_ticks()
+    sc = _scene(scd, els, 200.0)
+    assert len(sc.refine_witnesses()[0]) == 0  # the discrete problem tunnels
+    spans, rb = sc.refine_continuous(0.1)
+    ospans, orb = O.refine_continuous(els, 200.0, 0.1, O.BOX_SPEED)
+    assert spans.tolist() == ospans.tolist()
+    assert rb.tolist() == orb.tolist()
+    assert np.any((spans["t0"] <= 100.5) & (100.5 <= spans["t1"]))
+    sc.close()
+
+
+@pytest.mark.parametrize("seed", [300, 310])
+def test_continuous_equals_oracle_and_covers_alg1(scd, seed):
+    els = P.uniform_leo(10, seed=seed, radius_km=400.0)
+    T = 300
+    sc = _scene(scd, els, float(T))
+    spans, rb = sc.refine_continuous(0.5)
+    ospans, orb = O.refine_continuous(els, float(T), 0.5, O.BOX_SPEED)
+    # spans are exact multiples of the finest interval; boxes that merely
+    # touch may decide differently between the two FP32 roundings
+    g = set(spans.tolist())
+    o = set(ospans.tolist())
+    assert len(g ^ o) <= 0.01 * len(o)
+    assert len(rb) == len(orb)
+    for i, j, t in O.alg1_witnesses(els, T, 1.0).tolist():
+        m = spans[(spans["i"] == i) & (spans["j"] == j)]
+        assert np.any((m["t0"] <= t) & (t <= m["t1"])), (i, j, t)
+    with pytest.raises(scd.ScdError):
+        sc.refine_continuous(0.0)
+    sc.close()
