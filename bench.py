@@ -475,6 +475,9 @@ def run_refine(args, world):
             return scd.scd_narrow_phase(sc.handle, ptr, m)
 
         ftimes, earliest = timed(fixed, args.steps, args.warmup)
+        # the continuous-time variant at eps = 1 s on the same population
+        ctimes, (spans, crb) = timed(lambda: scd.scd_refine_continuous(sc.handle, 1.0),
+                                     args.steps, args.warmup)
     # algorithmic bytes of the rounds: per interval its box (32 B) and sort
     # key and index (8 B) written, 4 radix passes over key and index (24 B
     # each), the sweep's read of the box (32 B), the flags (4 B) and the
@@ -497,7 +500,10 @@ def run_refine(args, world):
                    "earliest_witness": [int(x) for x in w[0]] if len(w) else None,
                    "fixed_step_ms": statistics.mean(ftimes),
                    "fixed_step_boxes": 512 * 601,
-                   "fixed_step_earliest": list(earliest) if earliest else None}
+                   "fixed_step_earliest": list(earliest) if earliest else None,
+                   "continuous": {"eps_s": 1.0, "ms": statistics.mean(ctimes),
+                                  "rounds": int(len(crb)), "boxes": int(crb.sum()),
+                                  "spans": int(len(spans))}}
     r["roofline_refine"] = {"kernel_phase": "refinement rounds", "bound": "hbm",
                             "achieved": byt / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                             "frac": byt / (ms * 1e-3) / 1e9 / hbm, "traffic": None,
