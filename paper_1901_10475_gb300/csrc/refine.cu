@@ -17,6 +17,15 @@
 // The narrow phase then decides each tick candidate with Alg 1's test, so
 // the result is exactly the set of collision witnesses (Def 4).
 //
+// The continuous-time variant (Sec. 4.6) runs the same rounds over closed
+// real intervals: the interval [k, k + 1] of a level, in units of
+// T / 2^level seconds, is halved into [2k, 2k + 1] and [2k + 1, 2k + 2] of
+// the next level (the halves share their endpoint), down to a length of at
+// most eps; every pair of meeting boxes at that level is reported as a span,
+// the intersection of the two intervals.  The box, sort and sweep kernels
+// serve both: with t0 = k, t1 = k + 1 and the level's unit as the tick, the
+// SPEED box covers the real interval.
+//
 // Boxes are SPEED boxes (position at the interval's midpoint, half-width
 // r + vmax span / 2, rounded outward to FP32), the screen's formula.  The
 // meeting boxes of a round are found by sorting the boxes on their lower x
