@@ -56,3 +56,18 @@ def test_host_side_argument_checks_without_gpu():
             assert e.status == B.SCD_ERR_INVALID_ARG
         else:
             raise AssertionError("accepted invalid input")
+
+
+def test_narrow_and_refinement_refuse_missing_arguments_without_gpu():
+    """The narrow phase and the refinement entry points check their host
+    arguments first (no scene, no output count, eps <= 0): no device work."""
+    import ctypes
+    from paper_1901_10475_gb300 import _binding as B
+    L = B.lib()
+    n = ctypes.c_int64(0)
+    assert L.scd_narrow_phase(None, None, 0, None, None, None) == B.SCD_ERR_INVALID_ARG
+    assert L.scd_narrow_phase(None, None, -1, None, None, None) == B.SCD_ERR_INVALID_ARG
+    assert L.scd_refine_witnesses(None, None, 0, ctypes.byref(n), None, None) == \
+        B.SCD_ERR_INVALID_ARG
+    assert L.scd_refine_continuous(None, 1.0, None, 0, ctypes.byref(n), None, None) == \
+        B.SCD_ERR_INVALID_ARG
