@@ -499,7 +499,7 @@ def run_refine(args, world):
                    "boxes": int(rb.sum()), "witnesses": int(len(w)),
                    "earliest_witness": [int(x) for x in w[0]] if len(w) else None,
                    "fixed_step_ms": statistics.mean(ftimes),
-                   "fixed_step_boxes": 512 * 601,
+                   "fixed_step_boxes": int(sc.metrics()["boxes"]),
                    "fixed_step_earliest": list(earliest) if earliest else None,
                    "continuous": {"eps_s": 1.0, "ms": statistics.mean(ctimes),
                                   "rounds": int(len(crb)), "boxes": int(crb.sum()),
