@@ -82,3 +82,47 @@ def test_features_and_learned_step_clamp():
     ks = S.learned_step_seconds(els, [100.0, -100.0, np.log(P[2] / 100)])
     assert ks[0] == pytest.approx(P[0] / 50) and ks[1] == pytest.approx(P[1] / 400)
     assert ks[2] == pytest.approx(P[2] / 100)
+
+
+def test_feature_columns_by_hand():
+    """Every feature column against values worked out by hand for objects
+    chosen so that most of them are round numbers: a circular orbit 100 km up
+    at i = 0, a polar orbit with perigee 100 km and apogee 10000 km up, and
+    three circular orbits at inclination 30 deg whose middle one has a period
+    of exactly one day, 30 km above and below it the other two."""
+    RE, MU = 6378.137, 398600.4418
+    a_day = (MU * (86400.0 / (2 * np.pi)) ** 2) ** (1.0 / 3.0)  # Kepler's third law
+    a_polar = RE + (100.0 + 10000.0) / 2.0
+    e_polar = (10000.0 - 100.0) / 2.0 / a_polar
+    els = np.array([
+        [RE + 100.0, 0.0, 0.0, 0.1, 0.2, 0.3, 1.0],
+        [a_polar, e_polar, np.pi / 2, 0.1, 0.2, 0.3, 1.0],
+        [a_day, 0.0, np.pi / 6, 0.1, 0.2, 0.3, 1.0],
+        [a_day + 30.0, 0.0, np.pi / 6, 0.1, 0.2, 0.3, 1.0],
+        [a_day - 30.0, 0.0, np.pi / 6, 0.1, 0.2, 0.3, 1.0],
+    ])
+    f = S.features(els)
+    h_day = a_day - RE
+    want = np.array([
+        # log(a/RE), e, sin i, cos i, log(hp/100), log(ha/100), log(P/1h), log(1+density)
+        [np.log((RE + 100.0) / RE), 0.0, 0.0, 1.0, 0.0, 0.0,
+         np.log(2 * np.pi / np.sqrt(MU / (RE + 100.0) ** 3) / 3600.0), 0.0],
+        [np.log(a_polar / RE), 4950.0 / a_polar, 1.0, 0.0, 0.0, np.log(100.0),
+         np.log(2 * np.pi / np.sqrt(MU / a_polar ** 3) / 3600.0), 0.0],
+        [np.log(a_day / RE), 0.0, 0.5, np.sqrt(3) / 2, np.log(h_day / 100.0),
+         np.log(h_day / 100.0), np.log(24.0), np.log(3.0)],
+        [np.log((a_day + 30.0) / RE), 0.0, 0.5, np.sqrt(3) / 2, np.log((h_day + 30.0) / 100.0),
+         np.log((h_day + 30.0) / 100.0), None, np.log(2.0)],
+        [np.log((a_day - 30.0) / RE), 0.0, 0.5, np.sqrt(3) / 2, np.log((h_day - 30.0) / 100.0),
+         np.log((h_day - 30.0) / 100.0), None, np.log(2.0)],
+    ], dtype=object)
+    for r in range(len(els)):
+        for c in range(8):
+            if want[r, c] is not None:
+                assert f[r, c] == pytest.approx(float(want[r, c]), abs=1e-12), (r, c)
+    # the period grows as a^1.5: 30 km more on a one-day orbit is +0.107%
+    assert f[3, 6] - f[2, 6] == pytest.approx(1.5 * np.log1p(30.0 / a_day), abs=1e-12)
+    # the pins have teeth: a swap of sin i and cos i, or of the perigee and
+    # apogee altitudes, or of log a and log P, changes some row
+    for c1, c2 in ((2, 3), (4, 5), (0, 6)):
+        assert np.abs(f[:, c1] - f[:, c2]).max() > 0.1
