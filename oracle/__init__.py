@@ -72,6 +72,8 @@ def lib():
                 "or_boxes": (i64, [vp, i64, i64, d, vp, i32, vp, vp, vp, i64]),
                 "or_raw_cells_bruteforce": (i64, [vp, vp, vp, i64, vp, i64]),
                 "or_raw_cells_sweep": (i64, [vp, vp, vp, i64, vp, i64]),
+                "or_raw_cells_sweep_before": (i64, [vp, vp, vp, i64, i64, vp, i64]),
+                "or_boxes_starting": (i64, [vp, i64, i64, d, vp, i32, i64, i64, vp, vp, vp, i64]),
                 "or_raw_cells_selected": (i64, [vp, vp, vp, i64, vp, vp, i64]),
                 "or_canonicalize": (i64, [vp, i64]),
                 "or_alg1_witnesses": (i64, [vp, i64, i64, d, vp, i64]),
@@ -239,6 +241,23 @@ def boxes(els, T: int, tick_s: float, k, mode: int = BOX_SPEED):
     return lo, hi, obj
 
 
+def boxes_starting(els, T: int, tick_s: float, k, t0: int, t1: int, mode: int = BOX_SPEED):
+    """The boxes of `boxes` whose segments start at a tick in [t0, t1), in
+    the same order: whole segments of the horizon [0, T]."""
+    E = _els(els)
+    k = np.ascontiguousarray(np.asarray(k, dtype=np.int64))
+    f = lib().or_boxes_starting
+    n = f(_p(E), len(E), int(T), float(tick_s), _p(k), mode, int(t0), int(t1), None, None,
+          None, 0)
+    lo = np.zeros((n, 4), np.float32)
+    hi = np.zeros((n, 4), np.float32)
+    obj = np.zeros(n, np.uint32)
+    got = f(_p(E), len(E), int(T), float(tick_s), _p(k), mode, int(t0), int(t1), _p(lo), _p(hi),
+            _p(obj), n)
+    assert got == n
+    return lo, hi, obj
+
+
 # --- pair sets -------------------------------------------------------------
 
 def _cells_call(fn, *args):
@@ -272,6 +291,16 @@ def raw_cells_sweep(lo4, hi4, obj):
     hi4 = np.ascontiguousarray(hi4, np.float32)
     obj = np.ascontiguousarray(obj, np.uint32)
     return _cells_call(lib().or_raw_cells_sweep, _p(lo4), _p(hi4), _p(obj), len(obj))
+
+
+def raw_cells_sweep_before(lo4, hi4, obj, t_end: int):
+    """The sweep's pairs whose earlier box (by lower tick, then index)
+    starts before tick t_end."""
+    lo4 = np.ascontiguousarray(lo4, np.float32)
+    hi4 = np.ascontiguousarray(hi4, np.float32)
+    obj = np.ascontiguousarray(obj, np.uint32)
+    return _cells_call(lib().or_raw_cells_sweep_before, _p(lo4), _p(hi4), _p(obj), len(obj),
+                       int(t_end))
 
 
 def raw_cells_selected(lo4, hi4, obj, sel):

@@ -313,6 +313,31 @@ int64_t or_boxes(const double *els, int64_t n, int64_t T, double tick_s,
   return N;
 }
 
+/* The boxes of or_boxes whose segments start at a tick in [t0, t1), in the
+ * same order: a window of the whole screen's box set (segments are cut from
+ * the whole horizon [0, T], so a window's boxes are whole segments). */
+int64_t or_boxes_starting(const double *els, int64_t n, int64_t T, double tick_s,
+                          const int64_t *k, int mode, int64_t t0, int64_t t1, float *lo4,
+                          float *hi4, uint32_t *obj, int64_t cap) {
+  int64_t N = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t ki = k[i];
+    int64_t S = (T + 1 + ki - 1) / ki;
+    int64_t m0 = t0 > 0 ? (t0 + ki - 1) / ki : 0; /* first segment starting at or after t0 */
+    for (int64_t m = m0; m < S && m * ki < t1; ++m) {
+      if (N < cap) {
+        int64_t tlo = m * ki;
+        int64_t thi = (m + 1) * ki - 1;
+        if (thi > T) thi = T;
+        or_box(els + 7 * i, mode, tlo, thi, tick_s, lo4 + 4 * N, hi4 + 4 * N, NULL, NULL);
+        obj[N] = (uint32_t)i;
+      }
+      ++N;
+    }
+  }
+  return N;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Pair sets.                                                               */
 /* ------------------------------------------------------------------------ */
@@ -482,7 +507,9 @@ int64_t or_raw_cells_tree(const float *lo4, const float *hi4, const uint32_t *ob
   return c;
 }
 
-static const float *g_sort_lo;
+/* the boxes qsort's comparison reads; one per thread, so that calls from
+ * several host threads do not share it */
+static _Thread_local const float *g_sort_lo;
 static int cmp_by_tlo(const void *x, const void *y) {
   int64_t a = *(const int64_t *)x, b = *(const int64_t *)y;
   float ta = g_sort_lo[4 * a + 3], tb = g_sort_lo[4 * b + 3];
@@ -505,6 +532,32 @@ int64_t or_raw_cells_sweep(const float *lo4, const float *hi4,
   int64_t *ord = sorted_by_tlo(lo4, N);
   int64_t c = 0;
   for (int64_t p = 0; p < N; ++p) {
+    int64_t a = ord[p];
+    float tend = hi4[4 * a + 3];
+    for (int64_t q = p + 1; q < N && lo4[4 * ord[q] + 3] <= tend; ++q) {
+      int64_t b = ord[q];
+      if (obj[a] == obj[b]) continue;
+      if (!boxes_overlap(lo4 + 4 * a, hi4 + 4 * a, lo4 + 4 * b, hi4 + 4 * b)) continue;
+      if (c < cap) make_cell(lo4, hi4, obj, a, b, out + c);
+      ++c;
+    }
+  }
+  free(ord);
+  return c;
+}
+
+/* or_raw_cells_sweep restricted to the pairs whose earlier box in the
+ * sweep's order (by lower tick, then index) starts before tick t_end.  Over
+ * windows [t0, t1) of the lower ticks, with the boxes starting in
+ * [t0, t1 + longest box) as input each time, these pair sets partition the
+ * whole screen's: every pair is found from its earlier box, in the window
+ * where that box starts. */
+int64_t or_raw_cells_sweep_before(const float *lo4, const float *hi4,
+                                  const uint32_t *obj, int64_t N, int64_t t_end,
+                                  or_cell *out, int64_t cap) {
+  int64_t *ord = sorted_by_tlo(lo4, N);
+  int64_t c = 0;
+  for (int64_t p = 0; p < N && (int64_t)lo4[4 * ord[p] + 3] < t_end; ++p) {
     int64_t a = ord[p];
     float tend = hi4[4 * a + 3];
     for (int64_t q = p + 1; q < N && lo4[4 * ord[q] + 3] <= tend; ++q) {

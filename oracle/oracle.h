@@ -78,6 +78,11 @@ void or_box(const double *el, int mode, int64_t tlo, int64_t thi,
 int64_t or_boxes(const double *els, int64_t n, int64_t T, double tick_s,
                  const int64_t *k, int mode, float *lo4, float *hi4,
                  uint32_t *obj, int64_t cap);
+/* the boxes of or_boxes whose segments start at a tick in [t0, t1), in the
+ * same order (whole segments of the horizon [0, T]) */
+int64_t or_boxes_starting(const double *els, int64_t n, int64_t T, double tick_s,
+                          const int64_t *k, int mode, int64_t t0, int64_t t1, float *lo4,
+                          float *hi4, uint32_t *obj, int64_t cap);
 
 /* --- pair sets ------------------------------------------------------------ */
 /* every pair of boxes of different objects that overlap, closed, on all four
@@ -90,6 +95,11 @@ int64_t or_raw_cells_bruteforce(const float *lo4, const float *hi4,
 int64_t or_raw_cells_sweep(const float *lo4, const float *hi4,
                            const uint32_t *obj, int64_t N,
                            or_cell *out, int64_t cap);
+/* the sweep's pairs whose earlier box in its order starts before t_end
+ * (windows of the lower tick partition the whole set) */
+int64_t or_raw_cells_sweep_before(const float *lo4, const float *hi4,
+                                  const uint32_t *obj, int64_t N, int64_t t_end,
+                                  or_cell *out, int64_t cap);
 /* the same set restricted to pairs with at least one object in `sel`
  * (sel[obj] != 0), for spot checks on large populations. */
 int64_t or_raw_cells_selected(const float *lo4, const float *hi4,

@@ -199,3 +199,34 @@ def test_aabb_tree_equals_sweep_on_the_small_workload():
     k = O.step_ticks(els, O.STEP_FIXED, 1.0, fixed_ticks=10)
     lo, hi, obj = O.boxes(els, 6000, 1.0, k)
     assert _keys(O.raw_cells_tree(lo, hi, obj)) == _keys(O.raw_cells_sweep(lo, hi, obj))
+
+
+def test_time_windows_partition_the_screen():
+    """The CPU baseline's sample unit: the boxes whose segments start in a
+    window [t0, t1) are exactly those of the whole screen starting there, and
+    the sweep's pairs found from boxes starting in [t0, t1) (with the boxes
+    starting before t1 + the longest box as candidates), over a partition of
+    the horizon into windows, are exactly the whole screen's pairs."""
+    els = P.catalog_mixture(n=150, seed=P.SEED_BASE + 41)
+    T = 1500
+    k = O.step_ticks(els, O.STEP_PERIOD_FRACTION, 1.0, frac=100.0)
+    lo, hi, obj = O.boxes(els, T, 1.0, k, O.BOX_SPEED)
+    want = O.raw_cells_sweep(lo, hi, obj)
+    assert len(want) > 100
+    # the boxes of a window: the whole set's boxes with tlo in [t0, t1)
+    wl, wh, wo = O.boxes_starting(els, T, 1.0, k, 300, 700, O.BOX_SPEED)
+    sel = (lo[:, 3] >= 300) & (lo[:, 3] < 700)
+    assert np.array_equal(wl, lo[sel]) and np.array_equal(wh, hi[sel])
+    assert np.array_equal(wo, obj[sel])
+    longest = int(np.max(k))
+    got = []
+    edges = [0, 137, 400, 401, 950, 1500 + 1]
+    for t0, t1 in zip(edges[:-1], edges[1:]):
+        bl, bh, bo = O.boxes_starting(els, T, 1.0, k, t0, t1 + longest, O.BOX_SPEED)
+        c = O.raw_cells_sweep_before(bl, bh, bo, t1)
+        # a pair's cell starts where its later box starts: not before t0
+        assert (c["tlo"] >= t0).all()
+        got.append(c)
+    got = np.concatenate(got)
+    key = lambda c: np.sort(c, order=["i", "j", "tlo", "thi"]).tolist()
+    assert key(got) == key(want)
