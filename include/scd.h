@@ -139,9 +139,20 @@ typedef struct {
   int nodes_per_step; /* one box per leaf, node width 2: tree nodes each
                          lane visits per traversal step (two independent
                          loads in flight), 1 or 2                          */
-  int node_width;     /* one box per leaf: 2 (binary nodes, 40 bytes) or 4
+  int node_width;     /* one box per leaf: 2 (binary nodes, 36 bytes) or 4
                          (the grandchildren of a binary node in one 128-byte
                          line: one traversal step descends two levels)     */
+  float split_km;     /* 0: off.  Otherwise boxes whose largest spatial side
+                         exceeds |split_km| km are sorted apart from the
+                         others (one more key bit above the Morton key), so
+                         each group gets its own subtree and the large boxes
+                         do not widen the nodes of the small ones; < 0: the
+                         large boxes first (default -1000: each pair of a
+                         small and a large box is then found by the small
+                         box's query), > 0: after the small ones.  Plain
+                         screens apply it with 10- or 12-bit Morton axes
+                         (ignored with 8 or 16), decomposed screens and
+                         batches always.                                   */
 } scd_tuning;
 
 typedef struct scd_scene scd_scene;
@@ -312,12 +323,14 @@ SCD_API int scd_propagate(const scd_element *d_elems, int64_t n, const uint32_t 
  * cannot pay for the device-wide synchronisation of cudaMalloc/cudaFree.
  *
  * Same arguments, layout and result as scd_propagate (obj[q] < n is the
- * caller's duty).  The per-object scratch (128 bytes per object) lives in a
- * fixed array in device memory of SCD_NOALLOC_MAX_OBJECTS entries (4 MiB);
+ * caller's duty).  The per-object scratch (112 bytes per object) lives in a
+ * fixed array in device memory of SCD_NOALLOC_MAX_OBJECTS entries (3.5 MiB);
  * every GPU that loads the library holds it until the process exits.
  * n > SCD_NOALLOC_MAX_OBJECTS fails with SCD_ERR_CAPACITY before any work.
  * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  The call
+ * device current (once per device, safe from several host threads); make
+ * that first call before any stream capture.  The address is not looked up
+ * again after a reset of the device.  The call
  * is asynchronous on cuda_stream and allocates nothing (no cudaMalloc,
  * cudaFree or allocating library routine).  All calls share the one array
  * and it keeps the last call's contents: calls whose work overlaps on the

@@ -101,7 +101,8 @@ __global__ void k_ref_count(const float4 *__restrict__ lo, const float4 *__restr
 __global__ void k_ref_scatter(const float4 *__restrict__ lo, const float4 *__restrict__ hi,
                               const uint32_t *__restrict__ obj, int64_t N, DecompArgs d,
                               const int64_t *__restrict__ off, const DevCounters *__restrict__ ctr,
-                              int bits, float time_scale, int space_warp, int64_t cap,
+                              int bits, float time_scale, int space_warp, float split_km,
+                              int64_t cap,
                               unsigned long long *__restrict__ key, uint32_t *__restrict__ id) {
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= N) return;
@@ -111,6 +112,8 @@ __global__ void k_ref_scatter(const float4 *__restrict__ lo, const float4 *__res
   // the top 32 bits of the box's Morton key order it inside its cell
   unsigned long long m = box_morton(L, H, R, d.T, bits, time_scale, space_warp);
   if (4 * bits > 32) m >>= (4 * bits - 32);
+  // the size group, if any, above the 31 highest Morton bits
+  if (split_km != 0.0f) m = ((unsigned long long)split_bit(L, H, split_km) << 31) | (m >> 1);
   int64_t o = off[b];
   if (d.kind == SCD_DECOMP_SLAB_OCT) {
     for (int s = c.s0; s <= c.s1; ++s)
@@ -220,7 +223,7 @@ int build_decomposed(scd_scene *s, const scd_decomp *dc, int64_t &M, bool captur
     return SCD_ERR_OOM;
   k_ref_scatter<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(
       s->d_lo.p, s->d_hi.p, s->d_obj.p, N, d, s->d_refoff.p, s->d_ctr.p, s->tune.morton_bits,
-      s->tune.time_scale, s->tune.space_warp, R, s->d_refkey.p, s->d_refid.p);
+      s->tune.time_scale, s->tune.space_warp, s->tune.split_km, R, s->d_refkey.p, s->d_refid.p);
   note_launch();
   int cbits = 1;
   while ((1 << cbits) < n_cells) ++cbits;

@@ -237,7 +237,7 @@ __global__ void k_refit_q(const SBox *__restrict__ sbox, int64_t M,
                           const TravNode *__restrict__ nodes, QBox *__restrict__ nq,
                           const int32_t *__restrict__ parent_int,
                           const int32_t *__restrict__ parent_leaf, uint32_t *__restrict__ flags,
-                          QBox *__restrict__ qbox, uint2 *__restrict__ qlink,
+                          QBox *__restrict__ qbox, uint32_t *__restrict__ qlink,
                           const DevCounters *__restrict__ ctr, int64_t T) {
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= M || M == 1) return;
@@ -267,7 +267,7 @@ __global__ void k_refit_q(const SBox *__restrict__ sbox, int64_t M,
     const uint32_t g = (uint32_t)lk.z;  // the split: left child gamma, right gamma + 1
     const uint32_t fl =
         ((lk.x & kLeafBit) ? kQLeftLeaf : 0u) | ((lk.y & kLeafBit) ? kQRightLeaf : 0u);
-    qlink[p] = make_uint2(g | fl, (uint32_t)lk.w);
+    qlink[p] = g | fl;
     const QBox u = qbox_union(ql, qr);
     __stcg(reinterpret_cast<uint4 *>(nq + p), make_uint4(u.lo_xy, u.lo_zt, u.hi_xy, u.hi_zt));
     const int32_t up = parent_int[p];

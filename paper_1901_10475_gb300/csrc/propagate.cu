@@ -4,6 +4,8 @@
 // and the 4D Morton key of every box.
 #include <math.h>
 
+#include <mutex>
+
 #include "kepler.cuh"
 #include "scd_internal.cuh"
 
@@ -132,6 +134,7 @@ struct BoxArgs {
   int bits;          // Morton bits per axis
   float time_scale;  // weight of the time axis in the key
   int space_warp;    // log-compress space coordinates before quantising
+  float split_km;    // large boxes sorted apart (one key bit above the Morton key)
   DevCounters *ctr;
   float4 *lo, *hi;
   uint32_t *obj;
@@ -235,6 +238,7 @@ __global__ void __launch_bounds__(256) k_build_boxes(BoxArgs a) {
   // 4D Morton key of the box centre in the scene's bounding cube
   double R = __longlong_as_double((long long)a.ctr->extent_bits);
   unsigned long long key = box_morton(L, H, R, a.T, a.bits, a.time_scale, a.space_warp);
+  key |= (unsigned long long)split_bit(L, H, a.split_km) << (4 * a.bits);
   if (a.key64) a.key64[b] = key;
   else a.key32[b] = (uint32_t)key;
 }
@@ -252,6 +256,7 @@ int launch_build_boxes(scd_scene *s) {
   a.bits = s->tune.morton_bits;
   a.time_scale = s->tune.time_scale;
   a.space_warp = s->tune.space_warp;
+  a.split_km = split_of(s->tune);
   a.ctr = s->d_ctr.p;
   a.lo = s->d_lo.p;
   a.hi = s->d_hi.p;
@@ -433,30 +438,38 @@ int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, DevBuf<int64_
 // loops that cannot afford the device-wide synchronisation of cudaMalloc and
 // cudaFree.  This variant keeps the scratch in a fixed array in device
 // memory instead; every GPU that loads the library holds that array
-// (kNoAllocMaxObjects * 128 bytes = 4 MiB) until the process exits.
+// (kNoAllocMaxObjects * 112 bytes = 3.5 MiB) until the process exits.
 // ---------------------------------------------------------------------------
 namespace scd {
 constexpr int64_t kNoAllocMaxObjects = SCD_NOALLOC_MAX_OBJECTS;
+static_assert(sizeof(ObjParams) == 112,
+              "the fixed scratch array is documented as 112 bytes per object");
 static __device__ __align__(256) ObjParams g_noalloc_params[kNoAllocMaxObjects];
 
 constexpr int kNoAllocMaxDevices = 64;
+// per device: the array's device address, looked up exactly once
+static std::once_flag g_noalloc_once[kNoAllocMaxDevices];
 static ObjParams *g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
 // Device address of the scratch array on the current device.  Host code
 // only holds a stand-in for the symbol, so the address is looked up once per
-// device, with that device current.
+// device (std::call_once: first calls from several host threads do not
+// race), with that device current.  A failed lookup leaves the slot empty
+// and every later call on that device fails the same way.  The address is
+// not looked up again after a device reset.
 static int noalloc_scratch(ObjParams **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SCD_ERR_CUDA;
   if (dev < 0 || dev >= kNoAllocMaxDevices) return SCD_ERR_CUDA;
-  if (!g_noalloc_ptr[dev]) {
+  std::call_once(g_noalloc_once[dev], [dev] {
     ObjParams *p = nullptr;
-    if (cudaGetSymbolAddress((void **)&p, g_noalloc_params) != cudaSuccess || !p) {
+    if (cudaGetSymbolAddress((void **)&p, g_noalloc_params) != cudaSuccess) {
       cudaGetLastError();
-      return SCD_ERR_CUDA;
+      p = nullptr;
     }
     g_noalloc_ptr[dev] = p;
-  }
+  });
+  if (!g_noalloc_ptr[dev]) return SCD_ERR_CUDA;
   *out = g_noalloc_ptr[dev];
   return SCD_OK;
 }

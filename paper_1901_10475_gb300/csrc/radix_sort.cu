@@ -242,8 +242,11 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_downsweep(
     // the whole block decides together (a barrier; the counters above are
     // zeroed and gbase written before it)
     if (!__syncthreads_and(ok)) {
-      // give up: report, wait (bounded) for the other buffer's copy, leave
+      // give up: report, then leave only once the copies into both buffers
+      // have landed or their (bounded) waits have run out again, so that no
+      // copy is still writing into the block's shared memory when it exits
       if (threadIdx.x == 0 && err) atomicOr(err, (unsigned)ERR_SORT);
+      if (full) mbar_wait(&bar[b], (b ? parity1 : parity0) ^ 1u);
       if (full_tile(tile + gridDim.x)) mbar_wait(&bar[b ^ 1], b ? parity0 : parity1);
       return;
     }

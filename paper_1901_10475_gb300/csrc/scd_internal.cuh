@@ -31,7 +31,7 @@ enum : uint32_t {
 };
 
 // Per-object propagation constants, derived once per scene from the
-// elements (128 bytes, read through the read-only path by every box).
+// elements (112 bytes, read through the read-only path by every box).
 struct __align__(16) ObjParams {
   double A[3];   // a * P  (P: perifocal x axis in ECI)
   double B[3];   // a sqrt(1-e^2) * Q  (Q: perifocal y axis in ECI)
@@ -82,12 +82,11 @@ static_assert(sizeof(TravNode) == 80 && offsetof(TravNode, left) == 64,
 
 constexpr int32_t kLeafBit = (int32_t)0x80000000u;
 
-// Compact node of the one-box-per-leaf traversal (40 bytes): both child
+// Compact node of the one-box-per-leaf traversal (36 bytes): both child
 // boxes quantised in the scene frame (lower faces rounded down, upper faces
-// up, so a quantised test never rejects a pair that overlaps in FP32), the
-// split gamma (left child gamma, right child gamma + 1) with two leaf flags,
-// and the rightmost leaf under the right child (the left child's rightmost
-// leaf is gamma itself).  x and y take 16 bits, z 15 and the tick 17: one
+// up, so a quantised test never rejects a pair that overlaps in FP32) and
+// the split gamma (left child gamma, right child gamma + 1) with two leaf
+// flags; gamma is also the left child's rightmost leaf.  x and y take 16 bits, z 15 and the tick 17: one
 // quantum per tick up to 131071 ticks, so boxes of consecutive segments
 // (which touch, tick hi + 1 = tick lo, but do not overlap) stay apart.
 struct __align__(16) QBox {
@@ -224,6 +223,21 @@ __device__ inline unsigned long long box_morton(float4 L, float4 H, double R, in
   float ut = (float)((0.5 * ((double)L.w + (double)H.w)) / (double)(T + 1)) * time_scale;
   return morton4(quantize(ux, bits), quantize(uy, bits), quantize(uz, bits), quantize(ut, bits),
                  bits);
+}
+
+// The size group of a box (tuning split_km): boxes whose largest spatial
+// side exceeds |split_km| km form one group and the others another; the
+// group bit goes above the Morton key, so each group is sorted apart and
+// gets its own subtree.  1 = the group sorted last: the large boxes when
+// split_km > 0, the small ones when split_km < 0.
+__device__ __forceinline__ uint32_t split_bit(float4 L, float4 H, float split_km) {
+  if (split_km == 0.0f) return 0u;
+  const float ext = fmaxf(fmaxf(H.x - L.x, H.y - L.y), H.z - L.z);
+  return (split_km > 0.0f) == (ext > fabsf(split_km)) ? 1u : 0u;
+}
+// the split applies to Morton keys with room above them: 10 or 12 bits per axis
+inline float split_of(const scd_tuning &t) {
+  return t.morton_bits == 10 || t.morton_bits == 12 ? t.split_km : 0.0f;
 }
 
 // decomposition cells: the tick slab of t, and the altitude band of radius x
@@ -426,7 +440,7 @@ struct scd_scene {
   scd::DevBuf<scd::TravNode> d_nodes;
   scd::DevBuf<scd::QBox> d_qbox;     // 2 per internal node (one box per leaf)
   scd::DevBuf<scd::W4Node> d_w4;     // four-wide nodes (node width 4)
-  scd::DevBuf<uint2> d_qlink;        // per internal node: gamma | flags, last_r
+  scd::DevBuf<uint32_t> d_qlink;     // per internal node: gamma | leaf flags
   scd::DevBuf<float4> d_nlo, d_nhi;     // internal node boxes (refit)
   scd::DevBuf<float4> d_leaflo, d_leafhi;
   scd::DevBuf<int32_t> d_parent_int, d_parent_leaf;

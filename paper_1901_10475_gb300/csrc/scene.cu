@@ -80,6 +80,7 @@ extern "C" SCD_API int scd_default_tuning(scd_tuning *t) {
   t->space_warp = 0;
   t->nodes_per_step = 2;
   t->node_width = 2;
+  t->split_km = -1000.0f;  // boxes wider than 1000 km in their own subtree, first
   return SCD_OK;
 }
 
@@ -93,7 +94,8 @@ static bool tuning_ok(const scd_tuning *t) {
   bool sw = t->space_warp == 0 || t->space_warp == 1;
   bool ns = t->nodes_per_step == 1 || t->nodes_per_step == 2;
   bool nw = t->node_width == 2 || t->node_width == 4;
-  return leaf && st && bs && mb && ts && sw && ns && nw;
+  bool sp = isfinite(t->split_km);
+  return leaf && st && bs && mb && ts && sw && ns && nw && sp;
 }
 
 static bool element_ok(const scd_element &x) {
@@ -224,7 +226,7 @@ extern "C" SCD_API int scd_scene_set_elements_device(scd_scene *s, const scd_ele
 extern "C" SCD_API int scd_scene_set_tuning(scd_scene *s, const scd_tuning *t) {
   if (!s || !t || !tuning_ok(t)) return SCD_ERR_INVALID_ARG;
   bool rekey = t->morton_bits != s->tune.morton_bits || t->time_scale != s->tune.time_scale ||
-               t->space_warp != s->tune.space_warp;
+               t->space_warp != s->tune.space_warp || t->split_km != s->tune.split_km;
   s->tune = *t;
   if (rekey) s->boxes_built = false;
   return SCD_OK;
@@ -362,7 +364,7 @@ static int find_eager(scd_scene *s, const scd_decomp *d, int dkind, int raw_mode
   int64_t M = 0;
   if (dkind == SCD_DECOMP_NONE) {
     // A5: sort box ids along the Morton curve
-    int kb = 4 * s->tune.morton_bits;
+    int kb = 4 * s->tune.morton_bits + (split_of(s->tune) != 0.0f);
     if (s->tune.morton_bits > 8) {
       TRY(radix_sort_u64(s->d_key64.p, s->d_id.p, N, kb, s->sort_sc, st));
     } else {
@@ -435,7 +437,7 @@ static int enqueue_find(scd_scene *s, const scd_decomp *d, int dkind, int ob, in
   int64_t M = 0;
   if (s->events_ready) cudaEventRecord(s->ev[2], st);
   if (dkind == SCD_DECOMP_NONE) {
-    int kb = 4 * s->tune.morton_bits;
+    int kb = 4 * s->tune.morton_bits + (split_of(s->tune) != 0.0f);
     if (s->tune.morton_bits > 8) {
       TRY(radix_sort_u64(s->d_key64.p, s->d_id.p, s->N, kb, s->sort_sc, st));
     } else {
@@ -466,7 +468,7 @@ static void graph_key_of(const scd_scene *s, int64_t key[8]) {
   key[4] = (s->tune.node_width * 10 + s->tune.nodes_per_step) * 100000 +
            s->tune.leaf_size * 1000 + s->tune.stack_depth;
   key[5] = s->tune.morton_bits * 10 + s->tune.space_warp;
-  key[6] = (int64_t)(s->tune.time_scale * 1e6f);
+  key[6] = (int64_t)(s->tune.time_scale * 1e6f) * 1000000 + (int64_t)(split_of(s->tune) * 10.0f);
   key[7] = s->dkind ? s->n_refs : 0;
 }
 
@@ -706,14 +708,14 @@ extern "C" SCD_API int scd_last_metrics(const scd_scene *s, char *json, size_t c
                    "\"ms_traverse\": %.4f, \"ms_canon\": %.4f, \"leaf_size\": %d, "
                    "\"stack_depth\": %d, \"block_threads\": %d, \"morton_bits\": %d, "
                    "\"launches\": %llu, \"refs\": %lld, \"cells\": %d, \"graph\": %d, "
-                   "\"narrow_evals\": %llu, \"narrow_evals_fp64\": %llu}",
+                   "\"narrow_evals\": %llu, \"narrow_evals_fp64\": %llu, \"split_km\": %.1f}",
                    (long long)s->n, (long long)s->T, (long long)s->N, s->last_node_tests,
                    s->last_leaf_tests, s->last_runs, s->last_open, (long long)s->n_out, s->ms_boxes, s->ms_sort,
                    s->ms_build, s->ms_traverse, s->ms_canon, s->tune.leaf_size,
                    s->tune.stack_depth, s->tune.block_threads, s->tune.morton_bits,
                    s->last_launches, (long long)(s->dkind ? s->n_refs : s->N),
                    s->dkind ? s->n_cells : 1, s->last_graph, s->last_np_evals,
-                   s->last_np_evals64);
+                   s->last_np_evals64, (double)split_of(s->tune));
   if (w < 0 || (size_t)w >= cap) return SCD_ERR_BUFFER_TOO_SMALL;
   return SCD_OK;
 }

@@ -28,7 +28,7 @@ namespace scd {
 struct TravArgs {
   const TravNode *nodes;
   const QBox *qbox;           // compact nodes (one box per leaf)
-  const uint2 *qlink;
+  const uint32_t *qlink;      // their split gamma with the two leaf flags
   const W4Node *w4;           // four-wide nodes (one box per leaf, node width 4)
   const SBox *sbox;           // sorted boxes
   const uint32_t *sobj, *sid; // object and unsorted id of each sorted box
@@ -367,23 +367,32 @@ __device__ __forceinline__ void drain_hits(const TravArgs &a, const uint2 *buf, 
 
 // One node's two children against the quantised query: the child nodes to
 // descend into (gl, gr) and the leaf children that are candidates (hl, hr).
+// Only subtrees with a leaf after the query's own leaf p are of interest.
+// The left child's rightmost leaf is the split gamma, so it needs the test
+// gamma > p.  The right child needs none: every node a query visits either
+// holds p or lies wholly after it (the root holds p; a child of a node that
+// holds p either holds p or, being right of the split, lies after it, or
+// being left of it, is kept only when gamma > p; children of a node wholly
+// after p are wholly after p), so the right child always ends after p
+// unless it holds p as its last leaf.  That one case costs a descent along
+// the subtree's right edge down to p itself, whose pair with itself the
+// exact test drops (same object).
 __device__ __forceinline__ void test_children(const TravArgs &a, const QBox &q, int64_t p,
                                               int32_t node, bool &gl, bool &gr, bool &hl,
                                               bool &hr, int32_t &cl) {
   uint4 bl, br;
   ldg_qbox_pair(a.qbox + 2 * (int64_t)node, bl, br);
-  const uint2 lk = __ldg(a.qlink + node);
-  const uint32_t g = lk.x & kQIndex;
+  const uint32_t lk = __ldg(a.qlink + node);
+  const uint32_t g = lk & kQIndex;
   cl = (int32_t)g;
   // child lo <= query hi and query lo <= child hi: x, y per 16-bit lane,
   // then the z and tick fields
   const uint32_t ml = __vcmpleu2(bl.x, q.hi_xy) & __vcmpleu2(q.lo_xy, bl.z);
   const uint32_t mr = __vcmpleu2(br.x, q.hi_xy) & __vcmpleu2(q.lo_xy, br.z);
-  // only subtrees whose rightmost leaf lies after the query's own leaf
   gl = (int64_t)g > p && ml == 0xffffffffu && zt_le(bl.y, q.hi_zt) && zt_le(q.lo_zt, bl.w);
-  gr = (int64_t)lk.y > p && mr == 0xffffffffu && zt_le(br.y, q.hi_zt) && zt_le(q.lo_zt, br.w);
-  hl = gl && (lk.x & kQLeftLeaf);
-  hr = gr && (lk.x & kQRightLeaf);
+  gr = mr == 0xffffffffu && zt_le(br.y, q.hi_zt) && zt_le(q.lo_zt, br.w);
+  hl = gl && (lk & kQLeftLeaf);
+  hr = gr && (lk & kQRightLeaf);
   gl &= !hl;
   gr &= !hr;
 }
@@ -396,7 +405,10 @@ __device__ __forceinline__ bool w4_slot(const QBox &q, int64_t p, const uint4 &b
          zt_le(b.y, q.hi_zt) && zt_le(q.lo_zt, b.w);
 }
 
-// kTwo: two binary nodes per lane and step; kW4: four-wide nodes
+// kTwo: two binary nodes per lane and step; kW4: four-wide nodes.  The
+// lanes' stacks stay in local memory: a stack in shared memory (entry-major,
+// free of bank conflicts) was measured 1.7x slower, because the shared
+// memory it takes comes out of the L1 cache that the node loads rely on.
 template <int kDepth, bool kTwo, bool kW4>
 __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
   __shared__ uint2 hits[kT2Warps][kHitCap];

@@ -4,11 +4,12 @@ Alg 1's predicate (Defs 2-4).
 
 The per-candidate first witness tick and witness count are integers decided
 by FP64 comparisons of positions that agree with the oracle's within 1e-6
-km; they must be equal for every candidate whose oracle distances stay more
-than 1e-5 km away from r_i + r_j at every tick of its interval (a decision
-closer than that could go either way in either precision; such candidates
-are counted and must be rare).  The earliest witness (Def 5, in Alg 1's
-order of tick, then i, then j) must be equal.
+km each; the infinity-norm distance of two of them then agrees within
+2e-6 km, so they must be equal for every candidate whose oracle distances
+stay more than 2e-6 km away from r_i + r_j at every tick of its interval (a
+decision closer than that could go either way between the two
+propagations; such candidates are counted and must be rare).  The earliest
+witness (Def 5, in Alg 1's order of tick, then i, then j) must be equal.
 """
 import numpy as np
 import pytest
@@ -19,7 +20,8 @@ import population as P
 
 pytestmark = pytest.mark.gpu
 
-BOUNDARY_KM = 1e-5
+# two positions within 1e-6 km each: their distance within 2e-6 km
+BOUNDARY_KM = 2e-6
 
 
 @pytest.fixture(scope="module")
