@@ -13,6 +13,7 @@ Other workloads (--workload):
   refine512   the 512-object, 6000 s population of the parity tests solved by
               adaptive refinement (Alg 5-6 in rounds), beside the fixed-step
               screen plus narrow phase
+  refine24h   the same for the 24 h catalog workload (16,848 objects)
   narrow24h   the default screen followed by the narrow phase over its
               candidates: the first collision witness of the 24 h problem
               (Def 5) from device-resident elements
@@ -82,9 +83,18 @@ WORKLOADS = {
     "refine512": {
         "metric": "ms per adaptive-refinement solve at n=512, 6000 s (every collision witness)",
         "desc": ("n=512 uniform LEO (a 6678-8378 km, e < 0.01, i 0-100 deg), r = 2.5 km, 6000 s "
-                 "at 1 s ticks: Alg 5-6 as data-parallel rounds from [0, T] (SPEED boxes, sort "
-                 "and sweep per round), tick candidates decided by the narrow phase; against the "
-                 "fixed 10-tick screen plus the narrow phase on the same population")},
+                 "at 1 s ticks: Alg 5-6 as data-parallel rounds from [0, T] (per round the "
+                 "boxes of all active intervals, their Morton sort, a radix tree and the "
+                 "persistent traversal; all rounds queued without host reads), tick candidates "
+                 "decided by the narrow phase; against the fixed 10-tick screen plus the narrow "
+                 "phase on the same population")},
+    "refine24h": {
+        "metric": "ms per 24h adaptive-refinement solve at n=16848 (every collision witness)",
+        "desc": ("the n=16848 mixture, 24 h at 1 s ticks: Alg 5-6 as data-parallel rounds from "
+                 "[0, T] (per round the boxes of all active intervals, their Morton sort, a "
+                 "radix tree and the persistent traversal; all rounds queued without host "
+                 "reads), tick candidates decided by the narrow phase; against the fixed "
+                 "P/100 screen plus the narrow phase on the same population")},
     "batch64": {
         "metric": "scenes per second, 64 scenes, ~1.2M objects, horizons 6-72 h",
         "desc": ("64 independent catalog-shaped scenes, sizes log-uniform 1e3-6e4 (total "
@@ -358,10 +368,67 @@ def run_single(args, world, wl):
         r["e2e_ms"], r["e2e_pairs"] = e2e_through_abi(sc, els, r["n_pairs"], args.steps)
         r["e2e"] = {"value": r["e2e_ms"], "unit": "ms", "h2d_bytes_per_step": 56 * N_OBJ,
                     "d2h_bytes_per_step": 16 * r["e2e_pairs"]}
+    if wl == "catalog24h" and not args.no_extras and args.mode == 0:
+        # secondary figures of the same run: the narrow phase over this
+        # screen's candidates, and the same screen with INTERVAL boxes
+        step()
+        r["narrow"] = narrow_over_screen(sc, min(args.steps, 5))
+        r["interval_screen"] = interval_screen(els, d_el, args, min(args.steps, 5), dev)
     r["n"] = N_OBJ
     r["tuning"] = tuning
     sc.close()
     return r
+
+
+def narrow_over_screen(sc, reps: int) -> dict:
+    """The narrow phase (first witness and witness count of every candidate,
+    the earliest witness of Def 5) over the scene's current candidate list,
+    CUDA events on the stream, L2 flushed before each run."""
+    import torch
+
+    import paper_1901_10475_gb300 as scd
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    ptr, m = scd.scd_find_pairs_device(sc.handle)
+    first = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+    count = torch.empty(max(m, 1), dtype=torch.int32, device="cuda")
+    ts, w = [], None
+    for k in range(reps + 1):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        w = scd.scd_narrow_phase(sc.handle, ptr, m, first.data_ptr(), count.data_ptr())
+        e1.record(stream)
+        e1.synchronize()
+        if k > 0:
+            ts.append(e0.elapsed_time(e1))
+    mm = sc.metrics()
+    return {"ms": statistics.mean(ts), "candidates": m,
+            "tick_evals": int(mm["narrow_evals"]), "tick_evals_fp64": int(mm["narrow_evals_fp64"]),
+            "candidates_with_witness": int((first[:m] >= 0).sum()),
+            "witness_ticks": int(count[:m].long().sum()),
+            "earliest_witness": list(w) if w else None}
+
+
+def interval_screen(els, d_el, args, reps: int, dev: int) -> dict:
+    """The same 24 h screen with INTERVAL boxes (the paper's interval
+    evaluation, Sec. 4.5), timed like the main screen."""
+    import paper_1901_10475_gb300 as scd
+    pol = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=FRACTION)
+    sc = scd.Scene(els, args.horizon_s, TICK_S, pol, mode=scd.SCD_BOX_INTERVAL)
+
+    def step():
+        scd.scd_scene_set_elements_device(sc.handle, d_el.data_ptr(), len(els))
+        scd.scd_build_boxes(sc.handle)
+        return scd.scd_find_pairs_device(sc.handle)[1]
+
+    r = time_scene_steps(sc, step, reps, 2, dev, 1)
+    m = r["metrics"]
+    out = {"ms": statistics.mean(r["times"]), "pairs": r["n_pairs"], "boxes": m["boxes"],
+           "phase_ms": r["phase_ms"], "node_tests": m["node_tests"],
+           "leaf_tests": m["leaf_tests"], "clocks": r["clocks"]}
+    sc.close()
+    return out
 
 
 def run_narrow(args, world):
@@ -435,17 +502,23 @@ def run_narrow(args, world):
     return r
 
 
-def run_refine(args, world):
-    """Adaptive refinement on the small workload, and the fixed-step screen
-    plus narrow phase on the same population for comparison."""
+def run_refine(args, world, wl="refine512"):
+    """Adaptive refinement on the small workload (or the 24 h catalog one),
+    and the fixed-step screen plus narrow phase on the same population for
+    comparison."""
     import torch
 
     import paper_1901_10475_gb300 as scd
     dev = _device()
-    els = P.uniform_leo(512)
-    T_S = 6000.0
-    pol = scd.make_step_policy(scd.SCD_STEP_FIXED, fixed_ticks=10)
-    sc = scd.Scene(els, T_S, TICK_S, pol)
+    if wl == "refine24h":
+        els = P.catalog_mixture(n=N_OBJ, seed=P.SEED_BASE + 2)
+        T_S = args.horizon_s
+        pol = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=FRACTION)
+    else:
+        els = P.uniform_leo(512)
+        T_S = 6000.0
+        pol = scd.make_step_policy(scd.SCD_STEP_FIXED, fixed_ticks=10)
+    sc = scd.Scene(els, T_S, TICK_S, pol, mode=args.mode)
     sc.build_boxes()
     stream = torch.cuda.current_stream()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -470,6 +543,7 @@ def run_refine(args, world):
     with ClockSampler(dev) as clk:
         times, (w, rb) = timed(lambda: scd.scd_refine_witnesses(sc.handle), args.steps,
                                args.warmup)
+        refine_launches = sc.metrics()["launches"]
 
         def fixed():
             scd.scd_build_boxes(sc.handle)
@@ -480,20 +554,19 @@ def run_refine(args, world):
         # the continuous-time variant at eps = 1 s on the same population
         ctimes, (spans, crb) = timed(lambda: scd.scd_refine_continuous(sc.handle, 1.0),
                                      args.steps, args.warmup)
-    # algorithmic bytes of the rounds: per interval its box (32 B) and sort
-    # key and index (8 B) written, 4 radix passes over key and index (24 B
-    # each), the sweep's read of the box (32 B), the flags (4 B) and the
-    # split's reads and writes (12 + 24 B)
-    per_box = 32 + 8 + 4 * 24 + 32 + 4 + 36
+    # algorithmic bytes of the rounds, per interval: its box, Morton key and
+    # index written (44 B); six radix passes over key and index (36 B each:
+    # read twice, written once); the gather of the sorted box and object
+    # (76 B); the radix tree's links and parents (40 B) and refit (90 B);
+    # the traversal's sorted box, node and id reads (72 B); flags and the
+    # split's reads and writes (40 B)
+    per_box = 44 + 6 * 36 + 76 + 40 + 90 + 72 + 40
     byt = int(rb.sum()) * per_box
     ms = statistics.mean(times)
     pk, src = _peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
-    # kernels per timed solve: per round the boxes, 4 radix passes of 3
-    # kernels, the sweep and the split; then the start, two 64-bit sorts (8
-    # passes of 3), the distinct candidates, the narrow phase (3), the
-    # witness keys and their decoding
-    launches = args.steps * (15 * len(rb) + 1 + 48 + 1 + 3 + 1 + 1)
+    # kernels per timed solve, counted by the library
+    launches = args.steps * refine_launches
     r = {"times": times, "clocks": clk.summary(), "unit": "ms", "higher_is_better": False,
          "value": slowest_rank(sum(times), world) / (args.steps * world),
          "launches": launches, "n": len(els)}
@@ -733,7 +806,7 @@ def cpu_baseline_measure():
     other (the sample is representative of the horizon)."""
     T = int(HORIZON_S / TICK_S)
     cores = os.cpu_count() or 1
-    n_all, w_all, w_one = cores, 120, 100
+    n_all, w_all, w_one = 2 * cores, 60, 100
     starts = _windows(n_all, w_all, T)
     wall, busy, nbox, npair, per = cpu_oracle_windows(starts, w_all, cores)
     scale = (T + 1) / (n_all * w_all)
@@ -767,6 +840,8 @@ def main():
                     help="1: replay each screen's find sequence as one captured CUDA graph, "
                          "0: launch eagerly (default: graph for band_slab, eager otherwise)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="catalog24h: skip the narrow-phase and INTERVAL-screen figures")
     ap.add_argument("--box-mode", default="", choices=["", "speed", "interval"],
                     help="occ-int bound; default: speed, interval for batch64 and learned100k")
     ap.add_argument("--horizon-s", type=float, default=HORIZON_S,
@@ -830,8 +905,8 @@ def main():
         r = run_single(args, world, wl)
     elif wl == "narrow24h":
         r = run_narrow(args, world)
-    elif wl == "refine512":
-        r = run_refine(args, world)
+    elif wl in ("refine512", "refine24h"):
+        r = run_refine(args, world, wl)
     elif wl == "batch64":
         r = run_batch64(args, world)
     else:
@@ -895,7 +970,8 @@ def main():
     if "roofline_refine" in r:
         line["roofline"] = r["roofline_refine"]
     for k in ("latency_ms", "batches", "objects", "boxes_est", "ms_per_pass", "p100_ms",
-              "p100_boxes", "p100_pairs", "training", "tuning", "narrow", "refine"):
+              "p100_boxes", "p100_pairs", "training", "tuning", "narrow", "refine",
+              "interval_screen"):
         if k in r and r[k] is not None:
             line[k] = r[k]
     line["clocks"] = r["clocks"]

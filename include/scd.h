@@ -200,6 +200,9 @@ SCD_API int scd_scene_set_elements_device(scd_scene *s, const scd_element *d_ele
 /* Tuning for later calls; NULL fields are not allowed, use scd_default_tuning. */
 SCD_API int scd_scene_set_tuning(scd_scene *s, const scd_tuning *t);
 SCD_API int scd_default_tuning(scd_tuning *t);
+/* The scene's tuning in force (a find may have deepened the stack after an
+ * overflow).  Copied into *t. */
+SCD_API int scd_scene_get_tuning(const scd_scene *s, scd_tuning *t);
 
 /* Steps A1-A4: per-object steps, FP64 propagation, outward-rounded FP32
  * boxes and 4D Morton keys (Defs 7-8, Sec. 4.5, Eq. 1).  Asynchronous apart
@@ -300,6 +303,19 @@ typedef struct {
 SCD_API int scd_refine_continuous(scd_scene *s, double eps_s, scd_span *host_out, int64_t cap,
                                   int64_t *n_out, int64_t *round_boxes, int *rounds);
 
+/* The rounds of scd_refine_witnesses (eps_s <= 0) or of
+ * scd_refine_continuous at resolution eps_s (eps_s > 0), with every round's
+ * boxes copied out, so that each round can be checked against the overlap
+ * set of its own boxes: host arrays lo4, hi4 (x, y, z [km], then the
+ * interval's first and last unit: ticks, or units of T tick_s / 2^level in
+ * the continuous variant) and obj of cap entries receive, round after
+ * round, every active interval's FP32 box and object (round_boxes[r] of them
+ * for round r, in no particular order).  *n_out: the entries of all rounds;
+ * cap too small: SCD_ERR_BUFFER_TOO_SMALL with *n_out set and nothing
+ * written.  Errors otherwise as scd_refine_witnesses.  Synchronous. */
+SCD_API int scd_refine_trace(scd_scene *s, double eps_s, float *lo4, float *hi4, uint32_t *obj,
+                             int64_t cap, int64_t *n_out, int64_t *round_boxes, int *rounds);
+
 /* The scene's boxes in object-major, segment order (device pointers owned
  * by the scene): lo4/hi4 are nbox x 4 floats (x, y, z [km], tick), obj the
  * object of each box. */
@@ -397,7 +413,9 @@ SCD_API int scd_count_pairs_per_object(const scd_pair *d_pairs, int64_t n_pairs,
                                        uint32_t *d_counts, void *cuda_stream);
 
 /* Metrics of the scene's last find_pairs as one JSON object (box count,
- * node and leaf tests, pair counts, kernel times; narrow_evals and
+ * node and leaf tests, pair counts, kernel times; launches: the kernels of
+ * the last box build and find, or of the last refinement call;
+ * narrow_evals and
  * narrow_evals_fp64: the ticks the last scd_narrow_phase evaluated, and
  * those of them it had to decide in FP64).  Writes at most cap bytes
  * including the terminating NUL. */

@@ -83,6 +83,7 @@ def lib():
                 "or_narrow_phase": (i64, [vp, i64, vp, i64, d, vp, vp, vp, vp, i64]),
                 "or_refine_discrete": (i64, [vp, i64, i64, d, i32, vp, i64, vp, vp, vp]),
                 "or_refine_continuous": (i64, [vp, i64, d, d, i32, vp, i64, vp, vp]),
+                "or_refine_round": (i64, [vp, vp, vp, i64, i32, vp, vp, vp, i64]),
                 "or_radial_range": (None, [vp, vp]),
                 "or_band_edges": (None, [vp, i64, i32, vp]),
                 "or_band_counts": (None, [vp, i64, i32, vp]),
@@ -498,3 +499,20 @@ def potential_collision_filter(els, cells) -> np.ndarray:
     j = cells["j"].astype(np.int64)
     keep = np.maximum(rr[i, 0], rr[j, 0]) <= np.minimum(rr[i, 1], rr[j, 1])
     return cells[keep]
+
+
+def refine_round(lo4, hi4, obj, cont: bool = False) -> np.ndarray:
+    """One refinement round on the given FP32 boxes (first and last unit of
+    each interval in the w lane): the next round's intervals as an (m, 3)
+    int64 array of (object, t0, t1), in input order."""
+    lo4 = np.ascontiguousarray(lo4, np.float32)
+    hi4 = np.ascontiguousarray(hi4, np.float32)
+    obj = np.ascontiguousarray(obj, np.uint32)
+    m = len(obj)
+    cap = 2 * m + 1
+    nobj = np.zeros(cap, np.uint32)
+    nt0 = np.zeros(cap, np.int32)
+    nt1 = np.zeros(cap, np.int32)
+    k = lib().or_refine_round(_p(lo4), _p(hi4), _p(obj), m, int(cont), _p(nobj), _p(nt0),
+                              _p(nt1), cap)
+    return np.stack([nobj[:k].astype(np.int64), nt0[:k], nt1[:k]], 1)

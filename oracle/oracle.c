@@ -1018,6 +1018,67 @@ static int cmp_span(const void *x, const void *y) {
   return 0;
 }
 
+/* One round of the refinement applied to given boxes: m active intervals
+ * with their FP32 boxes lo4/hi4 (the interval's first and last unit in the
+ * w lane) and objects.  An interval is met when its box overlaps, closed on
+ * all four axes, the box of an interval of another object (every pair
+ * tested).  Discrete rule (cont == 0, Alg 5-6 in rounds): a met interval
+ * [t0, t1] with t1 > t0 becomes [t0, mid] and [mid + 1, t1], mid = t0 +
+ * (t1 - t0) / 2; a met single tick stays when one of the boxes it meets is
+ * longer than one tick.  Continuous rule (cont == 1, Sec. 4.6): a met
+ * interval [k, k + 1] becomes [2k, 2k + 1] and [2k + 1, 2k + 2].  The next
+ * intervals go to nobj, nt0, nt1 (up to cap; in input order); returns how
+ * many there are. */
+int64_t or_refine_round(const float *lo4, const float *hi4, const uint32_t *obj, int64_t m,
+                        int cont, uint32_t *nobj, int32_t *nt0, int32_t *nt1, int64_t cap) {
+  char *hit = (char *)calloc((size_t)(m > 0 ? m : 1), 1);
+  char *hit_long = (char *)calloc((size_t)(m > 0 ? m : 1), 1);
+  for (int64_t a = 0; a < m; ++a)
+    for (int64_t b = a + 1; b < m; ++b) {
+      if (obj[a] == obj[b]) continue;
+      if (!boxes_overlap(lo4 + 4 * a, hi4 + 4 * a, lo4 + 4 * b, hi4 + 4 * b)) continue;
+      hit[a] = hit[b] = 1;
+      if (hi4[4 * b + 3] > lo4[4 * b + 3]) hit_long[a] = 1;
+      if (hi4[4 * a + 3] > lo4[4 * a + 3]) hit_long[b] = 1;
+    }
+  int64_t mn = 0;
+  for (int64_t a = 0; a < m; ++a) {
+    if (!hit[a]) continue;
+    const int32_t t0 = (int32_t)lo4[4 * a + 3], t1 = (int32_t)hi4[4 * a + 3];
+    int32_t u[2][2];
+    int k = 0;
+    if (cont) {
+      u[0][0] = 2 * t0;
+      u[0][1] = 2 * t0 + 1;
+      u[1][0] = 2 * t0 + 1;
+      u[1][1] = 2 * t0 + 2;
+      k = 2;
+    } else if (t1 > t0) {
+      const int32_t mid = t0 + (t1 - t0) / 2;
+      u[0][0] = t0;
+      u[0][1] = mid;
+      u[1][0] = mid + 1;
+      u[1][1] = t1;
+      k = 2;
+    } else if (hit_long[a]) {
+      u[0][0] = t0;
+      u[0][1] = t1;
+      k = 1;
+    }
+    for (int q = 0; q < k; ++q) {
+      if (mn < cap) {
+        nobj[mn] = obj[a];
+        nt0[mn] = u[q][0];
+        nt1[mn] = u[q][1];
+      }
+      ++mn;
+    }
+  }
+  free(hit);
+  free(hit_long);
+  return mn;
+}
+
 int64_t or_refine_continuous(const double *els, int64_t n, double T_s, double eps_s, int mode,
                              or_span *out, int64_t cap, int64_t *round_boxes, int *rounds) {
   int L = 0;

@@ -159,6 +159,10 @@ int64_t or_refine_discrete(const double *els, int64_t n, int64_t T, double tick_
  * down to length <= eps_s, halves sharing their endpoint; every meeting
  * pair of boxes at that level as (i < j, intersection of the intervals),
  * sorted, each once.  Returns the span count (only cap written). */
+/* one refinement round on given boxes: the next round's intervals by the
+ * discrete (cont = 0) or continuous (cont = 1) halving rule */
+int64_t or_refine_round(const float *lo4, const float *hi4, const uint32_t *obj, int64_t m,
+                        int cont, uint32_t *nobj, int32_t *nt0, int32_t *nt1, int64_t cap);
 int64_t or_refine_continuous(const double *els, int64_t n, double T_s, double eps_s, int mode,
                              or_span *out, int64_t cap, int64_t *round_boxes, int *rounds);
 

@@ -20,13 +20,14 @@ from ._binding import (PAIR_DTYPE, SCD_BOX_INTERVAL, SCD_BOX_SPEED, SCD_DECOMP_A
                        scd_find_pairs, scd_find_pairs_device, scd_find_pairs_into,
                        scd_find_raw_cells_device,
                        WITNESS_DTYPE, scd_get_boxes, scd_get_steps, scd_last_metrics,
-                       scd_narrow_phase, scd_refine_continuous, scd_refine_witnesses,
+                       scd_narrow_phase, scd_refine_continuous, scd_refine_trace,
+                       scd_refine_witnesses,
                        SPAN_DTYPE,
                        scd_propagate,
                        scd_propagate_noalloc,
                        scd_scene_create, scd_scene_destroy, scd_scene_set_elements,
-                       scd_scene_set_elements_device, scd_scene_set_tuning,
-                       scd_status_string)
+                       scd_scene_get_tuning, scd_scene_set_elements_device,
+                       scd_scene_set_tuning, scd_status_string, scd_tuning)
 
 for _n in dir(B):  # every entry point and constant under its C name
     if _n.startswith("scd_") or _n.startswith("SCD_"):
@@ -79,6 +80,10 @@ class Scene:
                 setattr(x, k, v)
             t = x
         scd_scene_set_tuning(self.handle, t)
+
+    def tuning(self) -> dict:
+        t = scd_scene_get_tuning(self.handle)
+        return {f: getattr(t, f) for f, _ in scd_tuning._fields_}
 
     def set_elements(self, elements):
         scd_scene_set_elements(self.handle, elements)

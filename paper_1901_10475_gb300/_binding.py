@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
             "scd_scene_set_elements_device": (i32, [vp, vp, i64]),
             "scd_scene_set_tuning": (i32, [vp, P(scd_tuning)]),
             "scd_default_tuning": (i32, [P(scd_tuning)]),
+            "scd_scene_get_tuning": (i32, [vp, P(scd_tuning)]),
             "scd_build_boxes": (i32, [vp]),
             "scd_find_pairs": (i32, [vp, P(scd_decomp), vp, i64, P(i64)]),
             "scd_find_pairs_device": (i32, [vp, P(scd_decomp), P(vp), P(i64)]),
@@ -106,6 +107,7 @@ def lib() -> ctypes.CDLL:
             "scd_narrow_phase": (i32, [vp, vp, i64, vp, vp, P(scd_witness)]),
             "scd_refine_witnesses": (i32, [vp, vp, i64, P(i64), vp, P(i32)]),
             "scd_refine_continuous": (i32, [vp, d, vp, i64, P(i64), vp, P(i32)]),
+            "scd_refine_trace": (i32, [vp, d, vp, vp, vp, i64, P(i64), vp, P(i32)]),
             "scd_get_steps": (i32, [vp, P(vp)]),
             "scd_propagate": (i32, [vp, i64, vp, vp, i64, vp, vp]),
             "scd_propagate_noalloc": (i32, [vp, i64, vp, vp, i64, vp, vp]),
@@ -231,6 +233,12 @@ def scd_scene_set_tuning(scene: int, t: scd_tuning) -> None:
     check(lib().scd_scene_set_tuning(scene, ctypes.byref(t)), "scd_scene_set_tuning")
 
 
+def scd_scene_get_tuning(scene: int) -> scd_tuning:
+    t = scd_tuning()
+    check(lib().scd_scene_get_tuning(scene, ctypes.byref(t)), "scd_scene_get_tuning")
+    return t
+
+
 def scd_build_boxes(scene: int) -> None:
     check(lib().scd_build_boxes(scene), "scd_build_boxes")
 
@@ -334,6 +342,31 @@ def scd_refine_continuous(scene: int, eps_s: float, cap: int = 1 << 16):
             continue
         check(rc, "scd_refine_continuous")
         return out[:n.value].copy(), rb[:rounds.value].copy()
+
+
+def scd_refine_trace(scene: int, eps_s: float = 0.0, cap: int = 1 << 20):
+    """Every round's boxes of the refinement (discrete when eps_s <= 0, else
+    the continuous variant at eps_s): a list with, per round, (lo4, hi4,
+    obj) numpy arrays."""
+    n = ctypes.c_int64(0)
+    rounds = ctypes.c_int(0)
+    rb = np.zeros(64, np.int64)
+    while True:
+        lo = np.zeros((max(cap, 1), 4), np.float32)
+        hi = np.zeros((max(cap, 1), 4), np.float32)
+        obj = np.zeros(max(cap, 1), np.uint32)
+        rc = lib().scd_refine_trace(scene, float(eps_s), lo.ctypes.data, hi.ctypes.data,
+                                    obj.ctypes.data, cap, ctypes.byref(n), rb.ctypes.data,
+                                    ctypes.byref(rounds))
+        if rc == SCD_ERR_BUFFER_TOO_SMALL:
+            cap = int(n.value)
+            continue
+        check(rc, "scd_refine_trace")
+        out, off = [], 0
+        for m in rb[:rounds.value]:
+            out.append((lo[off:off + m].copy(), hi[off:off + m].copy(), obj[off:off + m].copy()))
+            off += int(m)
+        return out
 
 
 def scd_get_boxes(scene: int):

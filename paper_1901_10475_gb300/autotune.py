@@ -4,9 +4,9 @@ Times whole screens (boxes through the canonical list) with CUDA events on
 the scene's stream for candidate tunings, keeps the fastest, and caches the
 choice in a JSON file keyed by GPU name, a hash of the workload and log2 of
 the box count.  A staged search: leaf size x Morton bits x space warp
-first, then the time weight, the stack depth and the block shape (leaves of
-several boxes) or the nodes per traversal step and the node width (one box
-per leaf) around the winner.
+first, then the time weight, the stack depth, the size split of the key and
+the block shape (leaves of several boxes) or the nodes per traversal step
+and the node width (one box per leaf) around the winner.
 """
 from __future__ import annotations
 
@@ -79,6 +79,8 @@ def tune(scene, reps: int = 2, verbose: bool = False, decomp=None):
             best, best_ms = dict(cand), ms
     stage2 = [dict(best, time_scale=ts) for ts in (0.5, 0.25)]
     stage2 += [dict(best, stack_depth=sd) for sd in (32, 128)]
+    # the size split: off, a finer and a coarser threshold than the default
+    stage2 += [dict(best, split_km=sk) for sk in (0.0, -500.0, -2000.0)]
     if best["leaf_size"] > 1:
         stage2 += [dict(best, block_threads=bt) for bt in (64, 256)]
     else:

@@ -94,4 +94,69 @@ __device__ __forceinline__ void position_at(const ObjParams &p, double t, double
   for (int k = 0; k < 3; ++k) out[k] = fma(p.A[k], ce, p.B[k] * s);
 }
 
+// exact range of cos over [x0, x1] (x1 >= x0) from the end values c0 =
+// cos x0, c1 = cos x1: widened to 1 where a multiple of 2 pi lies inside, to
+// -1 where an odd multiple of pi does
+__device__ __forceinline__ void cos_range(double x0, double x1, double c0, double c1, double &lo,
+                                          double &hi) {
+  lo = fmin(c0, c1);
+  hi = fmax(c0, c1);
+  if (x1 - x0 >= kTwoPi) {
+    lo = -1.0;
+    hi = 1.0;
+    return;
+  }
+  if (ceil(x0 * (1.0 / kTwoPi)) * kTwoPi <= x1) hi = 1.0;
+  if (ceil((x0 - kPi) * (1.0 / kTwoPi)) * kTwoPi + kPi <= x1) lo = -1.0;
+}
+
+// The interval occupancy box (Def 7) of one object over the ticks [tlo, thi]
+// (tick length tick_s seconds), before outward FP32 rounding:
+//  SPEED     every point of the arc lies within vmax |t - tc| of pos(tc):
+//            the cube of half-width r + vmax (thi - tlo) tick_s / 2 + eps
+//            around the position at the midpoint tc
+//  INTERVAL  interval evaluation of A (cos E - e) + B sin E over
+//            [E(tlo), E(thi)] (Sec. 4.5: E is monotone in t, so its ends
+//            bound it), widened by r + eps
+// `iters` receives the Kepler iterations (kKeplerMaxIter: no convergence).
+__device__ __forceinline__ void segment_box(const ObjParams &p, int mode, int64_t tlo, int64_t thi,
+                                            double tick_s, double lo[3], double hi[3],
+                                            int &iters) {
+  if (mode == SCD_BOX_SPEED) {
+    double tc = 0.5 * (double)(tlo + thi) * tick_s;
+    double c[3];
+    position_at(p, tc, c, iters);
+    double hw = p.r + p.vmax * (double)(thi - tlo) * tick_s * 0.5 + kEpsKm;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      lo[q] = c[q] - hw;
+      hi[q] = c[q] + hw;
+    }
+    return;
+  }
+  double M0 = p.M0 + p.n * ((double)tlo * tick_s);
+  double M1 = p.M0 + p.n * ((double)thi * tick_s);
+  double kk = rint(M0 * (1.0 / kTwoPi));
+  double Mr0 = fma(-kk, kTwoPi, M0), Mr1 = fma(-kk, kTwoPi, M1);
+  // both ends by the mixed-precision solve, which also gives sin E, cos E
+  // (E within 1e-7 km / a: far inside the 1e-6 km margin)
+  int i0 = 0, i1 = 0;
+  double s0, c0, s1, c1;
+  double E0 = kepler_E_sc(Mr0, p.e, p.tolE, s0, c0, i0);
+  double E1 = kepler_E_sc(Mr1, p.e, p.tolE, s1, c1, i1);
+  iters = max(i0, i1);
+  double clo, chi, slo, shi;
+  cos_range(E0, E1, c0, c1, clo, chi);
+  // sin E = cos(E - pi/2)
+  cos_range(E0 - 0.5 * kPi, E1 - 0.5 * kPi, s0, s1, slo, shi);
+  double w = p.r + kEpsKm;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    double u0 = p.A[q] * (clo - p.e), u1 = p.A[q] * (chi - p.e);
+    double v0 = p.B[q] * slo, v1 = p.B[q] * shi;
+    lo[q] = fmin(u0, u1) + fmin(v0, v1) - w;
+    hi[q] = fmax(u0, u1) + fmax(v0, v1) + w;
+  }
+}
+
 }  // namespace scd

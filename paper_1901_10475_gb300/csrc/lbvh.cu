@@ -64,10 +64,20 @@ __device__ __forceinline__ int delta(const K *__restrict__ keys, int64_t M, int6
   return (int)(8 * sizeof(K)) + __clz((uint32_t)(i ^ j));
 }
 
+// the leaf count: the host's, or (refinement rounds) the smaller of a
+// device count and the capacity the grid was sized for
+__device__ __forceinline__ int64_t leaf_count(int64_t M, const unsigned long long *d_M) {
+  if (!d_M) return M;
+  const unsigned long long v = *d_M;
+  return v < (unsigned long long)M ? (int64_t)v : M;
+}
+
 template <class K>
 __global__ void k_karras(const K *__restrict__ keys, int64_t M, TravNode *__restrict__ nodes,
                          int32_t *__restrict__ parent_int, int32_t *__restrict__ parent_leaf,
-                         uint32_t *__restrict__ flags, int32_t *__restrict__ first_out) {
+                         uint32_t *__restrict__ flags, int32_t *__restrict__ first_out,
+                         const unsigned long long *__restrict__ d_M = nullptr) {
+  M = leaf_count(M, d_M);
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M - 1) return;
   // direction of the node's range
@@ -238,7 +248,9 @@ __global__ void k_refit_q(const SBox *__restrict__ sbox, int64_t M,
                           const int32_t *__restrict__ parent_int,
                           const int32_t *__restrict__ parent_leaf, uint32_t *__restrict__ flags,
                           QBox *__restrict__ qbox, uint32_t *__restrict__ qlink,
-                          const DevCounters *__restrict__ ctr, int64_t T) {
+                          const DevCounters *__restrict__ ctr, int64_t T,
+                          const unsigned long long *__restrict__ d_M = nullptr) {
+  M = leaf_count(M, d_M);
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= M || M == 1) return;
   const QFrame fr = scene_frame(ctr, T);
@@ -333,6 +345,25 @@ template int build_tree<uint32_t>(scd_scene *, const uint32_t *, const uint32_t 
 template int build_tree<unsigned long long>(scd_scene *, const unsigned long long *,
                                             const uint32_t *, int64_t, unsigned long long *, int,
                                             int64_t &);
+
+// The hierarchy of one refinement round: up to cap boxes already sorted
+// along the Morton curve (keys and boxes in sorted order), their count on
+// the device.  Karras links, then compact quantised nodes (one box per
+// leaf) in the frame of the scene's extent and a horizon of T ticks.
+int build_round_tree(const unsigned long long *keys, const SBox *sbox, int64_t cap,
+                     const unsigned long long *d_M, TravNode *nodes, int32_t *parent_int,
+                     int32_t *parent_leaf, uint32_t *arrive, QBox *nq, QBox *qbox,
+                     uint32_t *qlink, const DevCounters *ctr, int64_t T, cudaStream_t st) {
+  const int bs = 256;
+  if (cap < 2) return SCD_OK;
+  k_karras<unsigned long long><<<(unsigned)((cap - 1 + bs - 1) / bs), bs, 0, st>>>(
+      keys, cap, nodes, parent_int, parent_leaf, arrive, nullptr, d_M);
+  k_refit_q<<<(unsigned)((cap + bs - 1) / bs), bs, 0, st>>>(sbox, cap, nodes, nq, parent_int,
+                                                           parent_leaf, arrive, qbox, qlink,
+                                                           ctr, T, d_M);
+  note_launch(2);
+  return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
+}
 
 int build_hierarchy(scd_scene *s, int64_t &n_leaves) {
   int64_t Mx = (s->N + s->tune.leaf_size - 1) / s->tune.leaf_size;

@@ -154,22 +154,6 @@ __device__ __forceinline__ int64_t find_object(const int64_t *segoff, int64_t n,
   return lo;
 }
 
-// exact range of cos over [x0, x1] (x1 >= x0) from the end values c0 =
-// cos x0, c1 = cos x1: widened to 1 where a multiple of 2 pi lies inside, to
-// -1 where an odd multiple of pi does
-__device__ __forceinline__ void cos_range(double x0, double x1, double c0, double c1, double &lo,
-                                          double &hi) {
-  lo = fmin(c0, c1);
-  hi = fmax(c0, c1);
-  if (x1 - x0 >= kTwoPi) {
-    lo = -1.0;
-    hi = 1.0;
-    return;
-  }
-  if (ceil(x0 * (1.0 / kTwoPi)) * kTwoPi <= x1) hi = 1.0;
-  if (ceil((x0 - kPi) * (1.0 / kTwoPi)) * kTwoPi + kPi <= x1) lo = -1.0;
-}
-
 __global__ void __launch_bounds__(256) k_build_boxes(BoxArgs a) {
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.N) return;
@@ -183,43 +167,7 @@ __global__ void __launch_bounds__(256) k_build_boxes(BoxArgs a) {
   const ObjParams &p = a.par[i];
   double lo[3], hi[3];
   int iters = 0;
-  if (a.mode == SCD_BOX_SPEED) {
-    // every point of the arc lies within vmax |t - tc| of pos(tc)
-    double tc = 0.5 * (double)(tlo + thi) * a.tick_s;
-    double c[3];
-    position_at(p, tc, c, iters);
-    double hw = p.r + p.vmax * (double)(thi - tlo) * a.tick_s * 0.5 + kEpsKm;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      lo[q] = c[q] - hw;
-      hi[q] = c[q] + hw;
-    }
-  } else {
-    // interval evaluation of A (cos E - e) + B sin E over [E(t0), E(t1)]
-    double M0 = p.M0 + p.n * ((double)tlo * a.tick_s);
-    double M1 = p.M0 + p.n * ((double)thi * a.tick_s);
-    double kk = rint(M0 * (1.0 / kTwoPi));
-    double Mr0 = fma(-kk, kTwoPi, M0), Mr1 = fma(-kk, kTwoPi, M1);
-    // both ends by the mixed-precision solve, which also gives sin E, cos E
-    // (E within 1e-7 km / a: far inside the 1e-6 km margin)
-    int i0 = 0, i1 = 0;
-    double s0, c0, s1, c1;
-    double E0 = kepler_E_sc(Mr0, p.e, p.tolE, s0, c0, i0);
-    double E1 = kepler_E_sc(Mr1, p.e, p.tolE, s1, c1, i1);
-    iters = max(i0, i1);
-    double clo, chi, slo, shi;
-    cos_range(E0, E1, c0, c1, clo, chi);
-    // sin E = cos(E - pi/2)
-    cos_range(E0 - 0.5 * kPi, E1 - 0.5 * kPi, s0, s1, slo, shi);
-    double w = p.r + kEpsKm;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      double u0 = p.A[q] * (clo - p.e), u1 = p.A[q] * (chi - p.e);
-      double v0 = p.B[q] * slo, v1 = p.B[q] * shi;
-      lo[q] = fmin(u0, u1) + fmin(v0, v1) - w;
-      hi[q] = fmax(u0, u1) + fmax(v0, v1) + w;
-    }
-  }
+  segment_box(p, a.mode, tlo, thi, a.tick_s, lo, hi, iters);
   if (iters >= kKeplerMaxIter) atomicOr(&a.ctr->build_flags, ERR_KEPLER);
   float4 L, H;
   L.x = __double2float_rd(lo[0]);

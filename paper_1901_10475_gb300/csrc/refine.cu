@@ -2,8 +2,8 @@
 // Alg 5 and Alg 6 as data-parallel rounds over all objects at once.
 //
 // Every object starts with the whole horizon [0, T] as its interval.  A round
-// builds the 4D box of every active interval (Def 8), finds the boxes that
-// meet a box of another object, and then
+// builds the 4D box of every active interval (Def 8, in the scene's box
+// mode), finds the boxes that meet a box of another object, and then
 //   - drops an interval whose box meets none: its object is proven free of
 //     collisions over it (every other object's position at those times lies
 //     in one of this round's boxes, or was proven free in an earlier round);
@@ -22,17 +22,21 @@
 // T / 2^level seconds, is halved into [2k, 2k + 1] and [2k + 1, 2k + 2] of
 // the next level (the halves share their endpoint), down to a length of at
 // most eps; every pair of meeting boxes at that level is reported as a span,
-// the intersection of the two intervals.  The box, sort and sweep kernels
-// serve both: with t0 = k, t1 = k + 1 and the level's unit as the tick, the
-// SPEED box covers the real interval.
+// the intersection of the two intervals.  The box kernel serves both: with
+// t0 = k, t1 = k + 1 and the level's unit as the tick, a box covers the real
+// interval.
 //
-// Boxes are SPEED boxes (position at the interval's midpoint, half-width
-// r + vmax span / 2, rounded outward to FP32), the screen's formula.  The
-// meeting boxes of a round are found by sorting the boxes on their lower x
-// face and sweeping: box a is tested against the boxes after it in that
-// order whose lower x face is at most a's upper x face.  The sweep suits
-// rounds of up to some 1e5 boxes; larger populations want the screen's
-// hierarchy.
+// The meeting boxes of a round are found with the screen's machinery: the
+// boxes are sorted along a 4D Morton curve, a binary radix tree with
+// compact quantised nodes is built over them, and the persistent traversal
+// (in its refinement mode) flags both intervals of every meeting pair and
+// collects the candidates.  The rounds run without the host: every kernel
+// reads the round's interval count from device memory, and the host queues
+// all rounds at once (at most ceil(log2(T + 1)) + 2 of them, or the levels
+// of the continuous variant) and reads the counts once at the end.  The
+// buffers are sized for a capacity of intervals per round; a round that
+// would exceed it is cut short and flagged, and the call runs again with a
+// larger capacity (kept on the scene for the next call).
 #include <math.h>
 
 #include <algorithm>
@@ -47,23 +51,24 @@ constexpr int kRfMaxRounds = 64;
 // object indices take 20 bits and ticks 24 in a packed candidate key
 constexpr int64_t kRfMaxObjects = 1ll << 20;
 // device state words: tick candidates, next intervals, error bits, unique
-// candidates, witnesses
-enum { RF_NCAND = 0, RF_NNEXT = 1, RF_ERR = 2, RF_NUNIQ = 3, RF_NWIT = 4, RF_WORDS = 5 };
-constexpr uint32_t RF_HIT = 1u, RF_HIT_LONG = 2u;  // per-interval flags of a round
+// candidates, witnesses, this round's intervals, the largest next-round
+// count asked for
+enum {
+  RF_NCAND = 0, RF_NNEXT = 1, RF_ERR = 2, RF_NUNIQ = 3, RF_NWIT = 4, RF_M = 5, RF_OVER = 6,
+  RF_WORDS = 7
+};
+// bits of 4D Morton keys of the rounds' boxes, per axis
+constexpr int kRfMortonBits = 10;
 
-// packed tick candidate: t (24 bits) | i (20) | j (20): sorts in Alg 1's order
-__host__ __device__ inline unsigned long long rf_key(uint32_t t, uint32_t i, uint32_t j) {
-  return ((unsigned long long)t << 40) | ((unsigned long long)i << 20) | (unsigned long long)j;
+__device__ __forceinline__ int64_t rf_count(const unsigned long long *state, int64_t cap) {
+  const unsigned long long m = state[RF_M];
+  return m < (unsigned long long)cap ? (int64_t)m : cap;
 }
 
-// order-preserving map of a float to an unsigned key
-__device__ __forceinline__ uint32_t rf_float_key(float f) {
-  const uint32_t u = __float_as_uint(f);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-
-__global__ void k_rf_init(int64_t n, int32_t T, uint32_t *obj, int32_t *t0, int32_t *t1) {
+__global__ void k_rf_init(int64_t n, int32_t T, uint32_t *obj, int32_t *t0, int32_t *t1,
+                          unsigned long long *state) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) state[RF_M] = (unsigned long long)n;
   if (i >= n) return;
   obj[i] = (uint32_t)i;
   t0[i] = 0;
@@ -72,119 +77,86 @@ __global__ void k_rf_init(int64_t n, int32_t T, uint32_t *obj, int32_t *t0, int3
 
 struct RfBoxArgs {
   const ObjParams *par;
+  int mode;                     // SPEED or INTERVAL boxes
   const uint32_t *obj;
   const int32_t *t0, *t1;
-  int64_t M;
-  double tick_s;
+  int64_t cap;
+  const unsigned long long *state;
+  unsigned long long *round_count;  // this round's entry of the per-round counts
+  double tick_s;                // the length of one unit of t0, t1 [s]
+  const DevCounters *ctr;       // the scene's extent (key frame)
+  int64_t Tf;                   // the time extent of the key frame [units]
+  float split_km;
   float4 *lo, *hi;
-  uint32_t *key, *idx;
-  unsigned long long *state;
+  unsigned long long *key;
+  uint32_t *idx;
+  unsigned long long *err;
 };
 
 __global__ void __launch_bounds__(kRfThreads) k_rf_boxes(RfBoxArgs a) {
+  const int64_t M = rf_count(a.state, a.cap);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.M) return;
+  if (i == 0) *a.round_count = (unsigned long long)M;
+  if (i >= M) return;
   const ObjParams &p = a.par[a.obj[i]];
   const int32_t t0 = a.t0[i], t1 = a.t1[i];
-  // every point of the arc lies within vmax |t - tc| of pos(tc)
-  const double tc = 0.5 * ((double)t0 + (double)t1) * a.tick_s;
-  double c[3];
+  double lo[3], hi[3];
   int iters = 0;
-  position_at(p, tc, c, iters);
-  if (iters >= kKeplerMaxIter) atomicOr(&a.state[RF_ERR], 1ull);
-  const double hw = p.r + p.vmax * (double)(t1 - t0) * a.tick_s * 0.5 + kEpsKm;
+  segment_box(p, a.mode, t0, t1, a.tick_s, lo, hi, iters);
+  if (iters >= kKeplerMaxIter) atomicOr(a.err, 1ull);
   float4 L, H;
-  L.x = __double2float_rd(c[0] - hw);
-  L.y = __double2float_rd(c[1] - hw);
-  L.z = __double2float_rd(c[2] - hw);
-  H.x = __double2float_ru(c[0] + hw);
-  H.y = __double2float_ru(c[1] + hw);
-  H.z = __double2float_ru(c[2] + hw);
-  L.w = (float)t0;  // ticks < 2^24: exact
+  L.x = __double2float_rd(lo[0]);
+  L.y = __double2float_rd(lo[1]);
+  L.z = __double2float_rd(lo[2]);
+  H.x = __double2float_ru(hi[0]);
+  H.y = __double2float_ru(hi[1]);
+  H.z = __double2float_ru(hi[2]);
+  L.w = (float)t0;  // < 2^24: exact
   H.w = (float)t1;
   a.lo[i] = L;
   a.hi[i] = H;
-  a.key[i] = rf_float_key(L.x);
+  const double R = __longlong_as_double((long long)a.ctr->extent_bits);
+  unsigned long long k = box_morton(L, H, R, a.Tf, kRfMortonBits, 1.0f, 0);
+  k |= (unsigned long long)split_bit(L, H, a.split_km) << (4 * kRfMortonBits);
+  a.key[i] = k;
   a.idx[i] = (uint32_t)i;
 }
 
-struct RfSweepArgs {
-  const float4 *lo, *hi;
-  const uint32_t *obj;
-  const int32_t *t0, *t1;
-  const uint32_t *idx;  // intervals in order of their lower x face
-  int64_t M;
-  uint32_t *flags;
-  unsigned long long *cand;
-  int64_t cap;
-  unsigned long long *state;
-  int spans;  // continuous variant, finest level: every meeting pair is a span
-};
-
-// span key of two meeting intervals [ka, ka + 1], [kb, kb + 1] of one level:
-// i (20 bits) | j (20) | the later start (22) | whether the starts agree (1);
-// sorts by (i, j, t0, t1) of the intersection
-__device__ __forceinline__ unsigned long long rf_span_key(uint32_t i, uint32_t j, int32_t ka,
-                                                          int32_t kb) {
-  const uint32_t km = (uint32_t)max(ka, kb), same = ka == kb ? 1u : 0u;
-  return ((unsigned long long)i << 44) | ((unsigned long long)j << 24) |
-         ((unsigned long long)km << 1) | same;
+// the sorted boxes (32-byte records) and their objects
+__global__ void __launch_bounds__(kRfThreads) k_rf_gather(const uint32_t *__restrict__ idx,
+                                                          const float4 *__restrict__ lo,
+                                                          const float4 *__restrict__ hi,
+                                                          const uint32_t *__restrict__ obj,
+                                                          int64_t cap,
+                                                          const unsigned long long *state,
+                                                          SBox *sbox, uint32_t *sobj) {
+  const int64_t M = rf_count(state, cap);
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= M) return;
+  const uint32_t i = idx[p];
+  sbox[p].lo = lo[i];
+  sbox[p].hi = hi[i];
+  sobj[p] = obj[i];
 }
 
-// One thread per interval a (in sorted order): every interval after it
-// whose lower x face is at most a's upper x face meets a on x (a's lower
-// face is not above its own), so only y, z and the tick range are tested.
-__global__ void __launch_bounds__(kRfThreads) k_rf_sweep(RfSweepArgs a) {
-  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= a.M) return;
-  const uint32_t ia = a.idx[s];
-  const float4 la = a.lo[ia], ha = a.hi[ia];
-  const uint32_t oa = a.obj[ia];
-  const int32_t ta = a.t0[ia];
-  const bool longa = a.t1[ia] > ta;
-  uint32_t fa = 0;
-  for (int64_t u = s + 1; u < a.M; ++u) {
-    const uint32_t ib = a.idx[u];
-    const float4 lb = a.lo[ib];
-    if (!(lb.x <= ha.x)) break;  // sorted: no later box reaches a on x
-    const uint32_t ob = a.obj[ib];
-    if (ob == oa) continue;
-    const float4 hb = a.hi[ib];
-    if (!(la.y <= hb.y && lb.y <= ha.y && la.z <= hb.z && lb.z <= ha.z && la.w <= hb.w &&
-          lb.w <= ha.w))
-      continue;
-    const bool longb = a.t1[ib] > a.t0[ib];
-    fa |= RF_HIT | (longb ? RF_HIT_LONG : 0u);
-    atomicOr(&a.flags[ib], RF_HIT | (longa ? RF_HIT_LONG : 0u));
-    if (a.spans) {
-      const unsigned long long q = atomicAdd(&a.state[RF_NCAND], 1ull);
-      if (q < (unsigned long long)a.cap)
-        a.cand[q] = rf_span_key(min(oa, ob), max(oa, ob), ta, a.t0[ib]);
-    } else if (!longa && !longb) {  // two single ticks meet: the same tick
-      const unsigned long long q = atomicAdd(&a.state[RF_NCAND], 1ull);
-      if (q < (unsigned long long)a.cap)
-        a.cand[q] = rf_key((uint32_t)ta, min(oa, ob), max(oa, ob));
-    }
-  }
-  if (fa) atomicOr(&a.flags[ia], fa);
-}
-
-// next round's intervals (order is free: appended by atomics); the buffers
-// hold 2 M entries, so nothing overflows
+// next round's intervals (order is free: appended by atomics); entries past
+// the capacity are not written, and the count asked for shows it
 __global__ void __launch_bounds__(kRfThreads) k_rf_split(const uint32_t *__restrict__ obj,
                                                          const int32_t *__restrict__ t0,
                                                          const int32_t *__restrict__ t1,
                                                          const uint32_t *__restrict__ flags,
-                                                         int64_t M, uint32_t *nobj, int32_t *nt0,
-                                                         int32_t *nt1,
+                                                         int64_t cap, uint32_t *nobj,
+                                                         int32_t *nt0, int32_t *nt1,
                                                          unsigned long long *state) {
+  const int64_t M = rf_count(state, cap);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M) return;
   const uint32_t f = flags[i];
-  if (!(f & RF_HIT)) return;  // proven free of collisions over [t0, t1]
+  if (!(f & kRfHit)) return;  // proven free of collisions over [t0, t1]
   const int32_t a0 = t0[i], a1 = t1[i];
   if (a1 > a0) {
     const unsigned long long q = atomicAdd(&state[RF_NNEXT], 2ull);
+    if (q + 2 > (unsigned long long)cap) return;
     const int32_t mid = a0 + (a1 - a0) / 2;
     nobj[q] = obj[i];
     nt0[q] = a0;
@@ -192,8 +164,9 @@ __global__ void __launch_bounds__(kRfThreads) k_rf_split(const uint32_t *__restr
     nobj[q + 1] = obj[i];
     nt0[q + 1] = mid + 1;
     nt1[q + 1] = a1;
-  } else if (f & RF_HIT_LONG) {  // wait for the longer intervals it meets
+  } else if (f & kRfHitLong) {  // wait for the longer intervals it meets
     const unsigned long long q = atomicAdd(&state[RF_NNEXT], 1ull);
+    if (q + 1 > (unsigned long long)cap) return;
     nobj[q] = obj[i];
     nt0[q] = a0;
     nt1[q] = a1;
@@ -205,12 +178,14 @@ __global__ void __launch_bounds__(kRfThreads) k_rf_split(const uint32_t *__restr
 __global__ void __launch_bounds__(kRfThreads) k_rf_split_cont(const uint32_t *__restrict__ obj,
                                                               const int32_t *__restrict__ t0,
                                                               const uint32_t *__restrict__ flags,
-                                                              int64_t M, uint32_t *nobj,
+                                                              int64_t cap, uint32_t *nobj,
                                                               int32_t *nt0, int32_t *nt1,
                                                               unsigned long long *state) {
+  const int64_t M = rf_count(state, cap);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M || !(flags[i] & RF_HIT)) return;
+  if (i >= M || !(flags[i] & kRfHit)) return;
   const unsigned long long q = atomicAdd(&state[RF_NNEXT], 2ull);
+  if (q + 2 > (unsigned long long)cap) return;
   const int32_t k = t0[i];
   nobj[q] = obj[i];
   nt0[q] = 2 * k;
@@ -218,6 +193,36 @@ __global__ void __launch_bounds__(kRfThreads) k_rf_split_cont(const uint32_t *__
   nobj[q + 1] = obj[i];
   nt0[q + 1] = 2 * k + 1;
   nt1[q + 1] = 2 * k + 2;
+}
+
+// a copy of round r's boxes and objects after those of the rounds before it
+// (the trace of scd_refine_trace), if they fit in tcap entries
+__global__ void __launch_bounds__(kRfThreads) k_rf_trace(const float4 *__restrict__ lo,
+                                                         const float4 *__restrict__ hi,
+                                                         const uint32_t *__restrict__ obj,
+                                                         int64_t cap,
+                                                         const unsigned long long *state,
+                                                         const unsigned long long *rounds, int r,
+                                                         float4 *tlo, float4 *thi,
+                                                         uint32_t *tobj, int64_t tcap) {
+  const int64_t M = rf_count(state, cap);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  unsigned long long off = 0;
+  for (int q = 0; q < r; ++q) off += rounds[q];
+  if (off + (unsigned long long)M > (unsigned long long)tcap) return;
+  tlo[off + i] = lo[i];
+  thi[off + i] = hi[i];
+  tobj[off + i] = obj[i];
+}
+
+// the next round's count becomes the current one (at most the capacity; the
+// largest count asked for is kept)
+__global__ void k_rf_advance(unsigned long long *state, int64_t cap) {
+  const unsigned long long nx = state[RF_NNEXT];
+  if (nx > state[RF_OVER]) state[RF_OVER] = nx;
+  state[RF_M] = nx < (unsigned long long)cap ? nx : (unsigned long long)cap;
+  state[RF_NNEXT] = 0;
 }
 
 // distinct span keys (sorted) appended to out (in any order)
@@ -265,7 +270,7 @@ __global__ void k_rf_witness_keys(const scd_pair *__restrict__ p, const int32_t 
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n || first[q] < 0) return;
   const unsigned long long w = atomicAdd(&state[RF_NWIT], 1ull);
-  wkey[w] = rf_key((uint32_t)p[q].tlo, p[q].i, p[q].j);
+  wkey[w] = rf_tick_key((uint32_t)p[q].tlo, p[q].i, p[q].j);
 }
 
 __global__ void k_rf_decode(const unsigned long long *__restrict__ wkey, int64_t n,
@@ -283,14 +288,21 @@ __global__ void k_rf_decode(const unsigned long long *__restrict__ wkey, int64_t
 // device buffers of one call, released on every return path
 struct RfBuffers {
   cudaStream_t st;
-  DevBuf<uint32_t> obj[2], key, idx, flags;
-  DevBuf<int32_t> t0[2], t1[2], first;
+  DevBuf<uint32_t> obj[2], idx, flags, sobj, qlink, arrive;
+  DevBuf<int32_t> t0[2], t1[2], first, parent_int, parent_leaf;
   DevBuf<float4> lo, hi;
-  DevBuf<unsigned long long> cand, state, wkey;
-  DevBuf<uint32_t> count, sort_err;
+  DevBuf<unsigned long long> key, cand, state, wkey, rounds;
+  DevBuf<SBox> sbox;
+  DevBuf<TravNode> nodes;
+  DevBuf<QBox> nq, qbox;
+  DevBuf<DevCounters> ctr;
+  DevBuf<uint32_t> sort_err;
   DevBuf<scd_pair> pairs;
   DevBuf<scd_witness> wit;
   DevBuf<scd_span> span;
+  DevBuf<float4> tlo, thi;  // trace (scd_refine_trace): every round's boxes
+  DevBuf<uint32_t> tobj;
+  int64_t tcap = 0;
   SortScratch sc;
   explicit RfBuffers(cudaStream_t s) : st(s) {}
   ~RfBuffers() {
@@ -299,11 +311,26 @@ struct RfBuffers {
       t0[b].release(st);
       t1[b].release(st);
     }
-    key.release(st); idx.release(st); flags.release(st); first.release(st);
-    lo.release(st); hi.release(st); cand.release(st); state.release(st); wkey.release(st);
-    count.release(st); sort_err.release(st); pairs.release(st); wit.release(st);
-    span.release(st);
+    idx.release(st); flags.release(st); sobj.release(st); qlink.release(st);
+    arrive.release(st); first.release(st); parent_int.release(st); parent_leaf.release(st);
+    lo.release(st); hi.release(st); key.release(st); cand.release(st); state.release(st);
+    wkey.release(st); rounds.release(st); sbox.release(st); nodes.release(st); nq.release(st);
+    qbox.release(st); ctr.release(st); sort_err.release(st); pairs.release(st);
+    wit.release(st); span.release(st); tlo.release(st); thi.release(st); tobj.release(st);
     sc.release(st);
+  }
+  // every per-interval buffer for `cap` intervals a round, and `ccap`
+  // candidates
+  bool size(int64_t cap, int64_t ccap) {
+    const size_t c = (size_t)cap;
+    for (int b = 0; b < 2; ++b)
+      if (!obj[b].ensure(c, st) || !t0[b].ensure(c, st) || !t1[b].ensure(c, st)) return false;
+    return idx.ensure(c, st) && flags.ensure(c, st) && sobj.ensure(c, st) &&
+           qlink.ensure(c, st) && arrive.ensure(c, st) && parent_int.ensure(c, st) &&
+           parent_leaf.ensure(c, st) && lo.ensure(c, st) && hi.ensure(c, st) &&
+           key.ensure(c, st) && sbox.ensure(c, st) && nodes.ensure(c, st) && nq.ensure(c, st) &&
+           qbox.ensure(2 * c, st) && cand.ensure((size_t)ccap, st) &&
+           sort_reserve(sc, cap, sizeof(unsigned long long), true, st) == SCD_OK;
   }
 };
 
@@ -317,6 +344,141 @@ static int rf_read_state(RfBuffers &B, unsigned long long h[RF_WORDS]) {
   return SCD_OK;
 }
 
+// The rounds of one call, queued at once.  Discrete: rounds of [0, T] in
+// ticks until nothing is left (at most `rounds` of them).  Continuous
+// (levels >= 0): level l = 0 .. levels in units of T_s / 2^l, spans at the
+// last.  On return h holds the state words and round_counts the intervals
+// of every round; the caller checks capacity, candidates and the stack.
+static int rf_rounds(scd_scene *s, RfBuffers &B, int64_t cap, int64_t ccap, int deep,
+                     int rounds, int levels, unsigned long long h[RF_WORDS],
+                     unsigned long long *round_counts, unsigned int &trav_flags) {
+  cudaStream_t st = B.st;
+  const int64_t n = s->n;
+  if (cudaMemsetAsync(B.state.p, 0, sizeof(unsigned long long) * RF_WORDS, st) != cudaSuccess ||
+      cudaMemsetAsync(B.rounds.p, 0, sizeof(unsigned long long) * kRfMaxRounds, st) !=
+          cudaSuccess ||
+      cudaMemsetAsync(B.sort_err.p, 0, sizeof(uint32_t), st) != cudaSuccess ||
+      cudaMemsetAsync(B.ctr.p, 0, sizeof(DevCounters), st) != cudaSuccess ||
+      cudaMemcpyAsync(&B.ctr.p->extent_bits, &s->d_ctr.p->extent_bits, sizeof(unsigned long long),
+                      cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return SCD_ERR_CUDA;
+  const bool cont = levels >= 0;
+  const double T_s = (double)s->T * s->tick_s;
+  k_rf_init<<<grid_of(n), kRfThreads, 0, st>>>(n, cont ? 1 : (int32_t)s->T, B.obj[0].p,
+                                                B.t0[0].p, B.t1[0].p, B.state.p);
+  note_launch();
+  const float split = split_of(s->tune);
+  const int kb = 4 * kRfMortonBits + (split != 0.0f);
+  unsigned long long *dM = B.state.p + RF_M;
+  const int nr = cont ? levels + 1 : rounds;
+  int cur = 0;
+  for (int r = 0; r < nr; ++r) {
+    const int nx = cur ^ 1;
+    // the unit of t0, t1 and the time extent of the key frame
+    const double unit = cont ? ldexp(T_s, -r) : s->tick_s;
+    const int64_t Tf = cont ? (1ll << r) : s->T;
+    RfBoxArgs ba{s->d_par.p, s->box_mode, B.obj[cur].p, B.t0[cur].p, B.t1[cur].p, cap,
+                 B.state.p, B.rounds.p + r, unit, B.ctr.p, Tf, split, B.lo.p, B.hi.p,
+                 B.key.p, B.idx.p, B.state.p + RF_ERR};
+    k_rf_boxes<<<grid_of(cap), kRfThreads, 0, st>>>(ba);
+    note_launch();
+    if (B.tcap > 0) {
+      k_rf_trace<<<grid_of(cap), kRfThreads, 0, st>>>(B.lo.p, B.hi.p, B.obj[cur].p, cap, B.state.p,
+                                                     B.rounds.p, r, B.tlo.p, B.thi.p, B.tobj.p,
+                                                     B.tcap);
+      note_launch();
+    }
+    int rc = radix_sort_u64_dev(B.key.p, B.idx.p, cap, dM, 0, kb, B.sc, st);
+    if (rc != SCD_OK) return rc;
+    k_rf_gather<<<grid_of(cap), kRfThreads, 0, st>>>(B.idx.p, B.lo.p, B.hi.p, B.obj[cur].p, cap,
+                                                     B.state.p, B.sbox.p, B.sobj.p);
+    note_launch();
+    rc = build_round_tree(B.key.p, B.sbox.p, cap, dM, B.nodes.p, B.parent_int.p,
+                          B.parent_leaf.p, B.arrive.p, B.nq.p, B.qbox.p, B.qlink.p, B.ctr.p, Tf,
+                          st);
+    if (rc != SCD_OK) return rc;
+    // the flags, and the traversal's counters (its error bits, which follow
+    // them, stay set across the rounds)
+    if (cudaMemsetAsync(B.flags.p, 0, sizeof(uint32_t) * (size_t)cap, st) != cudaSuccess ||
+        cudaMemsetAsync(B.ctr.p, 0, offsetof(DevCounters, trav_flags), st) != cudaSuccess)
+      return SCD_ERR_CUDA;
+    const int spans = cont && r == levels;
+    rc = traverse_round(B.qbox.p, B.qlink.p, B.sbox.p, B.sobj.p, B.idx.p, cap, dM, Tf, B.ctr.p,
+                        B.flags.p, B.cand.p, B.state.p + RF_NCAND, (unsigned long long)ccap,
+                        spans, deep, st);
+    if (rc != SCD_OK) return rc;
+    if (spans) break;
+    if (cont)
+      k_rf_split_cont<<<grid_of(cap), kRfThreads, 0, st>>>(B.obj[cur].p, B.t0[cur].p, B.flags.p,
+                                                          cap, B.obj[nx].p, B.t0[nx].p,
+                                                          B.t1[nx].p, B.state.p);
+    else
+      k_rf_split<<<grid_of(cap), kRfThreads, 0, st>>>(B.obj[cur].p, B.t0[cur].p, B.t1[cur].p,
+                                                     B.flags.p, cap, B.obj[nx].p, B.t0[nx].p,
+                                                     B.t1[nx].p, B.state.p);
+    k_rf_advance<<<1, 1, 0, st>>>(B.state.p, cap);
+    note_launch(2);
+    cur = nx;
+  }
+  if (cudaMemcpyAsync(round_counts, B.rounds.p, sizeof(unsigned long long) * kRfMaxRounds,
+                      cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&trav_flags, &B.ctr.p->trav_flags, sizeof(unsigned int),
+                      cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return SCD_ERR_CUDA;
+  return rf_read_state(B, h);
+}
+
+}  // namespace scd
+
+namespace scd {
+// Queue the rounds, and again with more room while a round's intervals, the
+// candidates or a traversal stack did not fit.  The capacities that sufficed
+// stay on the scene for its next call.
+static int rf_run(scd_scene *s, RfBuffers &B, int rounds, int levels,
+                  unsigned long long h[RF_WORDS], unsigned long long *round_counts) {
+  cudaStream_t st = B.st;
+  if (!B.state.ensure(RF_WORDS, st) || !B.sort_err.ensure(1, st) ||
+      !B.rounds.ensure(kRfMaxRounds, st) || !B.ctr.ensure(1, st))
+    return SCD_ERR_OOM;
+  B.sc.err = B.sort_err.p;
+  int64_t cap = std::max<int64_t>(s->rf_cap, std::max<int64_t>(4 * s->n, 1 << 16));
+  int64_t ccap = std::max<int64_t>(s->rf_ccap, 1 << 16);
+  int deep = s->rf_deep;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    if (!B.size(cap, ccap)) return SCD_ERR_OOM;
+    unsigned int tf = 0;
+    int rc = rf_rounds(s, B, cap, ccap, deep, rounds, levels, h, round_counts, tf);
+    if (rc != SCD_OK) return rc;
+    bool again = false;
+    if (h[RF_OVER] > (unsigned long long)cap) {
+      cap = (int64_t)std::max<unsigned long long>(2ull * (unsigned long long)cap, 2ull * h[RF_OVER]);
+      again = true;
+    }
+    if (h[RF_NCAND] > (unsigned long long)ccap) {
+      ccap = (int64_t)(2ull * h[RF_NCAND]);
+      again = true;
+    }
+    if (tf & ERR_STACK) {
+      if (deep) return SCD_ERR_INTERNAL;
+      deep = 1;
+      again = true;
+    }
+    if (!again) {
+      s->rf_cap = cap;
+      s->rf_ccap = ccap;
+      s->rf_deep = deep;
+      return SCD_OK;
+    }
+  }
+  return SCD_ERR_CAPACITY;
+}
+
+static int rf_check_scene(const scd_scene *s) {
+  if (!s->boxes_built) return SCD_ERR_STATE;
+  if (s->n_scenes > 0) return SCD_ERR_INVALID_ARG;  // one horizon for all objects
+  if (s->n > kRfMaxObjects) return SCD_ERR_CAPACITY;
+  return SCD_OK;
+}
 }  // namespace scd
 
 using namespace scd;
@@ -325,95 +487,46 @@ extern "C" SCD_API int scd_refine_witnesses(scd_scene *s, scd_witness *host_out,
                                             int64_t *n_out, int64_t *round_boxes,
                                             int *rounds) {
   if (!s || !n_out || cap < 0 || (cap > 0 && !host_out)) return SCD_ERR_INVALID_ARG;
-  if (!s->boxes_built) return SCD_ERR_STATE;
-  if (s->n_scenes > 0) return SCD_ERR_INVALID_ARG;  // one horizon for all objects
-  if (s->n > kRfMaxObjects) return SCD_ERR_CAPACITY;
+  if (int rc = rf_check_scene(s)) return rc;
+  const unsigned long long mark = launch_count();
   cudaStream_t st = s->stream;
   RfBuffers B(st);
-  const int64_t n = s->n;
-  if (!B.state.ensure(RF_WORDS, st) || !B.sort_err.ensure(1, st)) return SCD_ERR_OOM;
-  if (cudaMemsetAsync(B.state.p, 0, sizeof(unsigned long long) * RF_WORDS, st) != cudaSuccess ||
-      cudaMemsetAsync(B.sort_err.p, 0, sizeof(uint32_t), st) != cudaSuccess)
-    return SCD_ERR_CUDA;
-  B.sc.err = B.sort_err.p;
-  int cur = 0;
-  if (!B.obj[0].ensure(n, st) || !B.t0[0].ensure(n, st) || !B.t1[0].ensure(n, st))
-    return SCD_ERR_OOM;
-  k_rf_init<<<grid_of(n), kRfThreads, 0, st>>>(n, (int32_t)s->T, B.obj[0].p, B.t0[0].p,
-                                                B.t1[0].p);
-  note_launch();
-  int64_t M = n, ncand = 0, ccap = 1 << 16;
-  if (!B.cand.ensure(ccap, st)) return SCD_ERR_OOM;
+  // the halvings of [0, T] down to single ticks, one round to decide them
+  // and one for single ticks that wait for a longer interval
+  int nr = 2;
+  while ((1ll << (nr - 2)) < s->T + 1) ++nr;
+  unsigned long long h[RF_WORDS], rc_[kRfMaxRounds];
+  int rc = rf_run(s, B, nr, -1, h, rc_);
+  if (rc != SCD_OK) return rc;
   int r = 0;
-  unsigned long long h[RF_WORDS];
-  for (; r < kRfMaxRounds && M > 0; ++r) {
-    if (round_boxes) round_boxes[r] = M;
-    const int nx = cur ^ 1;
-    if (!B.lo.ensure(M, st) || !B.hi.ensure(M, st) || !B.key.ensure(M, st) ||
-        !B.idx.ensure(M, st) || !B.flags.ensure(M, st) || !B.obj[nx].ensure(2 * M, st) ||
-        !B.t0[nx].ensure(2 * M, st) || !B.t1[nx].ensure(2 * M, st))
-      return SCD_ERR_OOM;
-    RfBoxArgs ba{s->d_par.p, B.obj[cur].p, B.t0[cur].p, B.t1[cur].p, M, s->tick_s,
-                 B.lo.p, B.hi.p, B.key.p, B.idx.p, B.state.p};
-    k_rf_boxes<<<grid_of(M), kRfThreads, 0, st>>>(ba);
-    note_launch();
-    int rc = radix_sort_u32(B.key.p, B.idx.p, M, 32, B.sc, st);
-    if (rc != SCD_OK) return rc;
-    // the sweep, again with a larger candidate buffer if this round's
-    // candidates did not fit
-    for (;;) {
-      if (cudaMemsetAsync(B.flags.p, 0, sizeof(uint32_t) * (size_t)M, st) != cudaSuccess)
-        return SCD_ERR_CUDA;
-      const unsigned long long nc0 = (unsigned long long)ncand;
-      if (cudaMemcpyAsync(B.state.p + RF_NCAND, &nc0, sizeof(nc0), cudaMemcpyHostToDevice, st) !=
-          cudaSuccess)
-        return SCD_ERR_CUDA;
-      RfSweepArgs sa{B.lo.p, B.hi.p, B.obj[cur].p, B.t0[cur].p, B.t1[cur].p, B.idx.p, M,
-                     B.flags.p, B.cand.p, ccap, B.state.p, 0};
-      k_rf_sweep<<<grid_of(M), kRfThreads, 0, st>>>(sa);
-      note_launch();
-      if ((rc = rf_read_state(B, h)) != SCD_OK) return rc;
-      if ((int64_t)h[RF_NCAND] <= ccap) break;
-      const int64_t want = (int64_t)h[RF_NCAND] * 2;
-      if (!B.cand.grow_keep(want, ncand, st)) return SCD_ERR_OOM;
-      ccap = want;
-    }
-    ncand = (int64_t)h[RF_NCAND];
-    const unsigned long long zero = 0;
-    if (cudaMemcpyAsync(B.state.p + RF_NNEXT, &zero, sizeof(zero), cudaMemcpyHostToDevice, st) !=
-        cudaSuccess)
-      return SCD_ERR_CUDA;
-    k_rf_split<<<grid_of(M), kRfThreads, 0, st>>>(B.obj[cur].p, B.t0[cur].p, B.t1[cur].p,
-                                                 B.flags.p, M, B.obj[nx].p, B.t0[nx].p,
-                                                 B.t1[nx].p, B.state.p);
-    note_launch();
-    if ((rc = rf_read_state(B, h)) != SCD_OK) return rc;
-    M = (int64_t)h[RF_NNEXT];
-    cur = nx;
+  while (r < nr && rc_[r] > 0) {
+    if (round_boxes) round_boxes[r] = (int64_t)rc_[r];
+    ++r;
   }
   if (rounds) *rounds = r;
-  if (M > 0) return SCD_ERR_INTERNAL;  // more rounds than the halvings of [0, T] allow
+  if (h[RF_M] > 0) return SCD_ERR_INTERNAL;  // more rounds than the halvings of [0, T] allow
   if (h[RF_ERR]) return SCD_ERR_KEPLER_NOCONV;
+  const int64_t ncand = (int64_t)h[RF_NCAND];
   // distinct tick candidates, then Alg 1's test at each tick
   int64_t nw = 0;
   if (ncand > 0) {
-    int rc = radix_sort_u64(B.cand.p, nullptr, ncand, 64, B.sc, st);
-    if (rc != SCD_OK) return rc;
+    int rc2 = radix_sort_u64(B.cand.p, nullptr, ncand, 64, B.sc, st);
+    if (rc2 != SCD_OK) return rc2;
     if (!B.pairs.ensure(ncand, st) || !B.first.ensure(ncand, st)) return SCD_ERR_OOM;
     k_rf_unique<<<grid_of(ncand), kRfThreads, 0, st>>>(B.cand.p, ncand, B.pairs.p, B.state.p);
     note_launch();
-    if ((rc = rf_read_state(B, h)) != SCD_OK) return rc;
+    if ((rc2 = rf_read_state(B, h)) != SCD_OK) return rc2;
     const int64_t nu = (int64_t)h[RF_NUNIQ];
-    rc = scd_narrow_phase(s, B.pairs.p, nu, B.first.p, nullptr, nullptr);
-    if (rc != SCD_OK) return rc;
+    rc2 = scd_narrow_phase(s, B.pairs.p, nu, B.first.p, nullptr, nullptr);
+    if (rc2 != SCD_OK) return rc2;
     if (!B.wkey.ensure(nu, st)) return SCD_ERR_OOM;
     k_rf_witness_keys<<<grid_of(nu), kRfThreads, 0, st>>>(B.pairs.p, B.first.p, nu, B.wkey.p,
                                                          B.state.p);
     note_launch();
-    if ((rc = rf_read_state(B, h)) != SCD_OK) return rc;
+    if ((rc2 = rf_read_state(B, h)) != SCD_OK) return rc2;
     nw = (int64_t)h[RF_NWIT];
     if (nw > 0) {
-      if ((rc = radix_sort_u64(B.wkey.p, nullptr, nw, 64, B.sc, st)) != SCD_OK) return rc;
+      if ((rc2 = radix_sort_u64(B.wkey.p, nullptr, nw, 64, B.sc, st)) != SCD_OK) return rc2;
       if (!B.wit.ensure(nw, st)) return SCD_ERR_OOM;
       k_rf_decode<<<grid_of(nw), kRfThreads, 0, st>>>(B.wkey.p, nw, B.wit.p);
       note_launch();
@@ -425,6 +538,7 @@ extern "C" SCD_API int scd_refine_witnesses(scd_scene *s, scd_witness *host_out,
       cudaStreamSynchronize(st) != cudaSuccess)
     return SCD_ERR_CUDA;
   if (serr) return SCD_ERR_TIMEOUT;
+  s->last_launches = launch_count() - mark;
   *n_out = nw;
   if (nw > cap) return SCD_ERR_BUFFER_TOO_SMALL;
   if (nw > 0 &&
@@ -438,38 +552,6 @@ extern "C" SCD_API int scd_refine_witnesses(scd_scene *s, scd_witness *host_out,
 namespace scd {
 // levels of the continuous variant: interval starts take 22 bits of a span key
 constexpr int kRfMaxLevels = 22;
-
-// boxes, sort and sweep of one round (with a larger candidate buffer when
-// the round's candidates do not fit); h receives the state words
-static int rf_round(scd_scene *s, RfBuffers &B, int cur, int64_t M, double tick_s, int spans,
-                    int64_t &ncand, int64_t &ccap, unsigned long long h[RF_WORDS]) {
-  cudaStream_t st = B.st;
-  RfBoxArgs ba{s->d_par.p, B.obj[cur].p, B.t0[cur].p, B.t1[cur].p, M, tick_s,
-               B.lo.p, B.hi.p, B.key.p, B.idx.p, B.state.p};
-  k_rf_boxes<<<grid_of(M), kRfThreads, 0, st>>>(ba);
-  note_launch();
-  int rc = radix_sort_u32(B.key.p, B.idx.p, M, 32, B.sc, st);
-  if (rc != SCD_OK) return rc;
-  for (;;) {
-    if (cudaMemsetAsync(B.flags.p, 0, sizeof(uint32_t) * (size_t)M, st) != cudaSuccess)
-      return SCD_ERR_CUDA;
-    const unsigned long long nc0 = (unsigned long long)ncand;
-    if (cudaMemcpyAsync(B.state.p + RF_NCAND, &nc0, sizeof(nc0), cudaMemcpyHostToDevice, st) !=
-        cudaSuccess)
-      return SCD_ERR_CUDA;
-    RfSweepArgs sa{B.lo.p, B.hi.p, B.obj[cur].p, B.t0[cur].p, B.t1[cur].p, B.idx.p, M,
-                   B.flags.p, B.cand.p, ccap, B.state.p, spans};
-    k_rf_sweep<<<grid_of(M), kRfThreads, 0, st>>>(sa);
-    note_launch();
-    if ((rc = rf_read_state(B, h)) != SCD_OK) return rc;
-    if ((int64_t)h[RF_NCAND] <= ccap) break;
-    const int64_t want = (int64_t)h[RF_NCAND] * 2;
-    if (!B.cand.grow_keep(want, ncand, st)) return SCD_ERR_OOM;
-    ccap = want;
-  }
-  ncand = (int64_t)h[RF_NCAND];
-  return SCD_OK;
-}
 }  // namespace scd
 
 extern "C" SCD_API int scd_refine_continuous(scd_scene *s, double eps_s, scd_span *host_out,
@@ -477,67 +559,35 @@ extern "C" SCD_API int scd_refine_continuous(scd_scene *s, double eps_s, scd_spa
                                              int *rounds) {
   if (!s || !n_out || cap < 0 || (cap > 0 && !host_out) || !(eps_s > 0.0))
     return SCD_ERR_INVALID_ARG;
-  if (!s->boxes_built) return SCD_ERR_STATE;
-  if (s->n_scenes > 0) return SCD_ERR_INVALID_ARG;
-  if (s->n > kRfMaxObjects) return SCD_ERR_CAPACITY;
+  if (int rc = rf_check_scene(s)) return rc;
   const double T_s = (double)s->T * s->tick_s;
   int L = 0;
   while (L <= kRfMaxLevels && ldexp(T_s, -L) > eps_s) ++L;
   if (L > kRfMaxLevels) return SCD_ERR_CAPACITY;  // eps_s below T / 2^22
+  const unsigned long long mark = launch_count();
   cudaStream_t st = s->stream;
   RfBuffers B(st);
-  const int64_t n = s->n;
-  if (!B.state.ensure(RF_WORDS, st) || !B.sort_err.ensure(1, st)) return SCD_ERR_OOM;
-  if (cudaMemsetAsync(B.state.p, 0, sizeof(unsigned long long) * RF_WORDS, st) != cudaSuccess ||
-      cudaMemsetAsync(B.sort_err.p, 0, sizeof(uint32_t), st) != cudaSuccess)
-    return SCD_ERR_CUDA;
-  B.sc.err = B.sort_err.p;
-  int cur = 0;
-  if (!B.obj[0].ensure(n, st) || !B.t0[0].ensure(n, st) || !B.t1[0].ensure(n, st))
-    return SCD_ERR_OOM;
-  k_rf_init<<<grid_of(n), kRfThreads, 0, st>>>(n, 1, B.obj[0].p, B.t0[0].p, B.t1[0].p);
-  note_launch();
-  int64_t M = n, ncand = 0, ccap = 1 << 16;
-  if (!B.cand.ensure(ccap, st)) return SCD_ERR_OOM;
-  unsigned long long h[RF_WORDS] = {};
+  unsigned long long h[RF_WORDS], rc_[kRfMaxRounds];
+  int rc = rf_run(s, B, 0, L, h, rc_);
+  if (rc != SCD_OK) return rc;
   int r = 0;
-  for (int level = 0; level <= L && M > 0; ++level, ++r) {
-    if (round_boxes) round_boxes[r] = M;
-    const int nx = cur ^ 1;
-    if (!B.lo.ensure(M, st) || !B.hi.ensure(M, st) || !B.key.ensure(M, st) ||
-        !B.idx.ensure(M, st) || !B.flags.ensure(M, st) || !B.obj[nx].ensure(2 * M, st) ||
-        !B.t0[nx].ensure(2 * M, st) || !B.t1[nx].ensure(2 * M, st))
-      return SCD_ERR_OOM;
-    int rc = rf_round(s, B, cur, M, ldexp(T_s, -level), level == L, ncand, ccap, h);
-    if (rc != SCD_OK) return rc;
-    if (level == L) {
-      ++r;
-      break;
-    }
-    const unsigned long long zero = 0;
-    if (cudaMemcpyAsync(B.state.p + RF_NNEXT, &zero, sizeof(zero), cudaMemcpyHostToDevice, st) !=
-        cudaSuccess)
-      return SCD_ERR_CUDA;
-    k_rf_split_cont<<<grid_of(M), kRfThreads, 0, st>>>(B.obj[cur].p, B.t0[cur].p, B.flags.p, M,
-                                                      B.obj[nx].p, B.t0[nx].p, B.t1[nx].p,
-                                                      B.state.p);
-    note_launch();
-    if ((rc = rf_read_state(B, h)) != SCD_OK) return rc;
-    M = (int64_t)h[RF_NNEXT];
-    cur = nx;
+  while (r <= L && rc_[r] > 0) {
+    if (round_boxes) round_boxes[r] = (int64_t)rc_[r];
+    ++r;
   }
   if (rounds) *rounds = r;
   if (h[RF_ERR]) return SCD_ERR_KEPLER_NOCONV;
+  const int64_t ncand = (int64_t)h[RF_NCAND];
   int64_t nu = 0;
   if (ncand > 0) {  // spans of the finest level: distinct, in (i, j, t0, t1) order
-    int rc = radix_sort_u64(B.cand.p, nullptr, ncand, 64, B.sc, st);
-    if (rc != SCD_OK) return rc;
+    int rc2 = radix_sort_u64(B.cand.p, nullptr, ncand, 64, B.sc, st);
+    if (rc2 != SCD_OK) return rc2;
     if (!B.wkey.ensure(ncand, st)) return SCD_ERR_OOM;
     k_rf_distinct<<<grid_of(ncand), kRfThreads, 0, st>>>(B.cand.p, ncand, B.wkey.p, B.state.p);
     note_launch();
-    if ((rc = rf_read_state(B, h)) != SCD_OK) return rc;
+    if ((rc2 = rf_read_state(B, h)) != SCD_OK) return rc2;
     nu = (int64_t)h[RF_NUNIQ];
-    if ((rc = radix_sort_u64(B.wkey.p, nullptr, nu, 64, B.sc, st)) != SCD_OK) return rc;
+    if ((rc2 = radix_sort_u64(B.wkey.p, nullptr, nu, 64, B.sc, st)) != SCD_OK) return rc2;
     if (!B.span.ensure(nu, st)) return SCD_ERR_OOM;
     k_rf_span_decode<<<grid_of(nu), kRfThreads, 0, st>>>(B.wkey.p, nu, ldexp(T_s, -L), B.span.p);
     note_launch();
@@ -548,10 +598,58 @@ extern "C" SCD_API int scd_refine_continuous(scd_scene *s, double eps_s, scd_spa
       cudaStreamSynchronize(st) != cudaSuccess)
     return SCD_ERR_CUDA;
   if (serr) return SCD_ERR_TIMEOUT;
+  s->last_launches = launch_count() - mark;
   *n_out = nu;
   if (nu > cap) return SCD_ERR_BUFFER_TOO_SMALL;
   if (nu > 0 &&
       (cudaMemcpyAsync(host_out, B.span.p, sizeof(scd_span) * (size_t)nu, cudaMemcpyDeviceToHost,
+                       st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    return SCD_ERR_CUDA;
+  return SCD_OK;
+}
+
+extern "C" SCD_API int scd_refine_trace(scd_scene *s, double eps_s, float *lo4, float *hi4,
+                                        uint32_t *obj, int64_t cap, int64_t *n_out,
+                                        int64_t *round_boxes, int *rounds) {
+  if (!s || !n_out || cap < 0 || (cap > 0 && (!lo4 || !hi4 || !obj))) return SCD_ERR_INVALID_ARG;
+  if (int rc = rf_check_scene(s)) return rc;
+  int nr = 2, L = -1;
+  if (eps_s > 0.0) {
+    const double T_s = (double)s->T * s->tick_s;
+    L = 0;
+    while (L <= kRfMaxLevels && ldexp(T_s, -L) > eps_s) ++L;
+    if (L > kRfMaxLevels) return SCD_ERR_CAPACITY;
+  } else {
+    while ((1ll << (nr - 2)) < s->T + 1) ++nr;
+  }
+  cudaStream_t st = s->stream;
+  RfBuffers B(st);
+  B.tcap = std::max<int64_t>(cap, 1);
+  if (!B.tlo.ensure((size_t)B.tcap, st) || !B.thi.ensure((size_t)B.tcap, st) ||
+      !B.tobj.ensure((size_t)B.tcap, st))
+    return SCD_ERR_OOM;
+  unsigned long long h[RF_WORDS], rc_[kRfMaxRounds];
+  int rc = rf_run(s, B, nr, L, h, rc_);
+  if (rc != SCD_OK) return rc;
+  const int nrounds = L >= 0 ? L + 1 : nr;
+  int r = 0;
+  int64_t total = 0;
+  while (r < nrounds && rc_[r] > 0) {
+    if (round_boxes) round_boxes[r] = (int64_t)rc_[r];
+    total += (int64_t)rc_[r];
+    ++r;
+  }
+  if (rounds) *rounds = r;
+  if (h[RF_ERR]) return SCD_ERR_KEPLER_NOCONV;
+  *n_out = total;
+  if (total > cap) return SCD_ERR_BUFFER_TOO_SMALL;
+  if (total > 0 &&
+      (cudaMemcpyAsync(lo4, B.tlo.p, sizeof(float4) * (size_t)total, cudaMemcpyDeviceToHost, st) !=
+           cudaSuccess ||
+       cudaMemcpyAsync(hi4, B.thi.p, sizeof(float4) * (size_t)total, cudaMemcpyDeviceToHost, st) !=
+           cudaSuccess ||
+       cudaMemcpyAsync(obj, B.tobj.p, sizeof(uint32_t) * (size_t)total, cudaMemcpyDeviceToHost,
                        st) != cudaSuccess ||
        cudaStreamSynchronize(st) != cudaSuccess))
     return SCD_ERR_CUDA;

@@ -240,6 +240,23 @@ inline float split_of(const scd_tuning &t) {
   return t.morton_bits == 10 || t.morton_bits == 12 ? t.split_km : 0.0f;
 }
 
+// Refinement rounds: flags of an interval (it met a box of another object;
+// that box was longer than one tick), a tick candidate t (24 bits) | i (20)
+// | j (20), which sorts in Alg 1's order, and a span of two meeting
+// intervals [ka, ka + 1], [kb, kb + 1] of one level of the continuous
+// variant, i (20) | j (20) | the later start (22) | whether the starts agree
+// (1), which sorts by (i, j, t0, t1) of the intersection.
+constexpr uint32_t kRfHit = 1u, kRfHitLong = 2u;
+__host__ __device__ inline unsigned long long rf_tick_key(uint32_t t, uint32_t i, uint32_t j) {
+  return ((unsigned long long)t << 40) | ((unsigned long long)i << 20) | (unsigned long long)j;
+}
+__host__ __device__ inline unsigned long long rf_span_key(uint32_t i, uint32_t j, int32_t ka,
+                                                          int32_t kb) {
+  const uint32_t km = (uint32_t)(ka > kb ? ka : kb), same = ka == kb ? 1u : 0u;
+  return ((unsigned long long)i << 44) | ((unsigned long long)j << 24) |
+         ((unsigned long long)km << 1) | same;
+}
+
 // decomposition cells: the tick slab of t, and the altitude band of radius x
 // (the number of band edges <= x)
 __device__ inline int slab_of(int64_t t, int n_slabs, int64_t T) {
@@ -461,6 +478,11 @@ struct scd_scene {
   scd::DevBuf<unsigned char> d_npobj;  // per-object FP32 constants (64 B each)
   unsigned long long last_np_evals = 0, last_np_evals64 = 0;
 
+  // refinement: the capacities (intervals a round, candidates) and the
+  // traversal stack that sufficed last time
+  int64_t rf_cap = 0, rf_ccap = 0;
+  int rf_deep = 0;
+
   // metrics of the last find_pairs
   double ms_sort = 0, ms_build = 0, ms_traverse = 0, ms_canon = 0, ms_boxes = 0;
   unsigned long long last_node_tests = 0, last_leaf_tests = 0, last_runs = 0, last_open = 0;
@@ -476,6 +498,10 @@ int launch_build_boxes(scd_scene *s);
 int launch_propagate(const scd_element *d_el, int64_t n, const uint32_t *obj, const double *t,
                      int64_t m, double *out, cudaStream_t st);
 int build_hierarchy(scd_scene *s, int64_t &n_leaves);
+int build_round_tree(const unsigned long long *keys, const SBox *sbox, int64_t cap,
+                     const unsigned long long *d_M, TravNode *nodes, int32_t *parent_int,
+                     int32_t *parent_leaf, uint32_t *arrive, QBox *nq, QBox *qbox,
+                     uint32_t *qlink, const DevCounters *ctr, int64_t T, cudaStream_t st);
 template <class K>
 int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, int64_t Nq,
                K *leafkey, int cell_shift, int64_t &M);
@@ -487,6 +513,11 @@ int learned_steps(scd_scene *s);
 // internal decomposition kind of a batch of scenes: one cell per scene
 constexpr int kDecompScenes = 100;
 int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_bits);
+int traverse_round(const QBox *qbox, const uint32_t *qlink, const SBox *sbox,
+                   const uint32_t *sobj, const uint32_t *sid, int64_t cap,
+                   const unsigned long long *d_N, int64_t T, DevCounters *ctr, uint32_t *rflags,
+                   unsigned long long *rcand, unsigned long long *rncand, unsigned long long rcap,
+                   int spans, int deep, cudaStream_t st);
 int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits);
 // canonical list with every count read on the device (graph capture)
 int canonicalize_dev(scd_scene *s, int obj_bits, int t_bits);

@@ -232,6 +232,12 @@ extern "C" SCD_API int scd_scene_set_tuning(scd_scene *s, const scd_tuning *t) {
   return SCD_OK;
 }
 
+extern "C" SCD_API int scd_scene_get_tuning(const scd_scene *s, scd_tuning *t) {
+  if (!s || !t) return SCD_ERR_INVALID_ARG;
+  *t = s->tune;
+  return SCD_OK;
+}
+
 extern "C" SCD_API int scd_build_boxes(scd_scene *s) {
   if (!s) return SCD_ERR_INVALID_ARG;
   cudaStream_t st = s->stream;
@@ -521,6 +527,7 @@ static int find_graph(scd_scene *s, const scd_decomp *d, int dkind, int ob, int 
   if (!s->d_out.grow_keep(s->pair_cap, s->n_out, st) ||
       sort_reserve(s->sort_sc, s->pair_cap, sizeof(unsigned long long),
                    !runs_packed(ob, tb, s->T), st) != SCD_OK ||
+
       !s->d_tilecnt.ensure((size_t)(s->pair_cap / 2048 + 2), st) ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return SCD_OK;  // no graph this time; the eager result stands

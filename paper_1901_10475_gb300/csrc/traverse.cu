@@ -54,6 +54,15 @@ struct TravArgs {
   const double2 *rr;         // radial ranges (ALT_BANDS)
   const double *edges;       // band edges (ALT_BANDS)
   const int32_t *objT;       // per-object horizon (a batch of scenes), or null
+  // refinement rounds (kRefine): the box count on the device (N is the
+  // capacity), a flag word per interval (indexed by unsorted id) and the
+  // round's candidates (tick candidates, or spans at the finest level of
+  // the continuous variant)
+  const unsigned long long *d_N;
+  uint32_t *rflags;
+  unsigned long long *rcand, *rncand;
+  unsigned long long rcap;
+  int rspans;
 };
 
 // Is `cell` the one cell that reports the overlapping pair (q, b)?  The
@@ -312,11 +321,14 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a) {
 // buffer and their records are worked out by the whole warp together, into
 // output chunks the warp reserves kChunk slots at a time.
 // ---------------------------------------------------------------------------
+// block shape: 64, 128 and 256 threads (with 16, 8 and 4 resident blocks)
+// measured the same on the 24 h catalog screen (21.9, 21.9, 22.0 ms)
 constexpr int kT2Threads = 128;
 constexpr int kT2Warps = kT2Threads / 32;
 constexpr int kHitCap = 256;  // per warp; drained when fewer than 64 slots remain
 // queries claimed per warp atomic; small, so that the queries in flight stay
 // a narrow window of the Morton order and their nodes stay in L2
+// (64 per claim: +4% traversal time, 128: +17%)
 constexpr unsigned kQueryChunk = 32;
 // a refill can hand out up to 32 queries at once, from the pool's rest and
 // one new chunk: a chunk smaller than a warp would leave lanes without one
@@ -325,6 +337,35 @@ static_assert(kQueryChunk >= 32, "a query chunk covers at least one warp's refil
 struct WarpEmit {
   ChunkCursor s, e;  // start and end record chunks (raw cells use s)
 };
+
+// A refinement round's hits: both intervals of a pair of meeting boxes of
+// different objects are flagged; two single ticks that meet (the same tick)
+// are a tick candidate, and at the finest level of the continuous variant
+// every meeting pair is a span.
+__device__ __forceinline__ void drain_round_hits(const TravArgs &a, const uint2 *buf, int cnt) {
+  const int lane = threadIdx.x & 31;
+  for (int k = lane; k < cnt; k += 32) {
+    const uint2 h = buf[k];
+    float4 ql, qh, bl, bh;
+    ldg_box(a.sbox + h.x, ql, qh);
+    ldg_box(a.sbox + h.y, bl, bh);
+    const uint32_t qo = __ldg(a.sobj + h.x), bo = __ldg(a.sobj + h.y);
+    if (bo == qo || !box_overlap(ql, qh, bl, bh)) continue;
+    const bool longq = qh.w > ql.w, longb = bh.w > bl.w;
+    atomicOr(a.rflags + __ldg(a.sid + h.x), kRfHit | (longb ? kRfHitLong : 0u));
+    atomicOr(a.rflags + __ldg(a.sid + h.y), kRfHit | (longq ? kRfHitLong : 0u));
+    unsigned long long key;
+    if (a.rspans) {
+      key = rf_span_key(min(qo, bo), max(qo, bo), (int32_t)ql.w, (int32_t)bl.w);
+    } else if (!longq && !longb) {
+      key = rf_tick_key((uint32_t)ql.w, min(qo, bo), max(qo, bo));
+    } else {
+      continue;
+    }
+    const unsigned long long q = atomicAdd(a.rncand, 1ull);
+    if (q < a.rcap) a.rcand[q] = key;
+  }
+}
 
 __device__ __forceinline__ void drain_hits(const TravArgs &a, const uint2 *buf, int cnt,
                                            WarpEmit &we) {
@@ -409,7 +450,10 @@ __device__ __forceinline__ bool w4_slot(const QBox &q, int64_t p, const uint4 &b
 // lanes' stacks stay in local memory: a stack in shared memory (entry-major,
 // free of bank conflicts) was measured 1.7x slower, because the shared
 // memory it takes comes out of the L1 cache that the node loads rely on.
-template <int kDepth, bool kTwo, bool kW4>
+// 8 resident blocks of 128 threads: 64 registers and a few bytes of spills;
+// 9 or 10 blocks (56 or 48 registers) spill 112-280 bytes and measured
+// 12% and 41% slower
+template <int kDepth, bool kTwo, bool kW4, bool kRefine = false>
 __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
   __shared__ uint2 hits[kT2Warps][kHitCap];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -420,7 +464,9 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
   int64_t p = -1;  // current query (sorted position), -1 = none
   bool exhausted = false;
   // the last box has no later partner: queries are 0 .. N-2
-  const unsigned long long nq = a.N > 1 ? (unsigned long long)(a.N - 1) : 0ull;
+  const int64_t nbox = kRefine && a.d_N && *a.d_N < (unsigned long long)a.N ? (int64_t)*a.d_N
+                                                                            : a.N;
+  const unsigned long long nq = nbox > 1 ? (unsigned long long)(nbox - 1) : 0ull;
   unsigned long long q_next = 0, q_end = 0;  // the warp's query pool
   WarpEmit we;
   const QFrame fr = scene_frame(a.ctr, a.T);
@@ -589,23 +635,29 @@ __global__ void __launch_bounds__(kT2Threads, 8) k_traverse2(TravArgs a) {
     }
     __syncwarp();
     if (nhit > kHitCap - (kTwo || kW4 ? 128 : 64)) {
-      drain_hits(a, buf, nhit, we);
+      if constexpr (kRefine) drain_round_hits(a, buf, nhit);
+      else drain_hits(a, buf, nhit, we);
       __syncwarp();
       ntests += nhit;  // exact box tests, counted once per warp
       nhit = 0;
     }
   }
   __syncwarp();
-  if (nhit > 0) drain_hits(a, buf, nhit, we);
+  if constexpr (kRefine) {
+    if (nhit > 0) drain_round_hits(a, buf, nhit);
+  } else {
+    if (nhit > 0) drain_hits(a, buf, nhit, we);
+    chunk_fill_holes(we.s, a.starts, a.cap);
+    if (!a.raw) chunk_fill_holes(we.e, a.ends, a.cap);
+  }
   ntests += nhit;
-  chunk_fill_holes(we.s, a.starts, a.cap);
-  if (!a.raw) chunk_fill_holes(we.e, a.ends, a.cap);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nt += __shfl_down_sync(0xffffffffu, nt, o);
   if (lane == 0) {
     atomicAdd(&a.ctr->node_tests, nt);
     atomicAdd(&a.ctr->leaf_tests, ntests);
-    if (a.raw) {
+    if (kRefine) {
+    } else if (a.raw) {
       atomicAdd(&a.ctr->v_raw, we.s.count);
     } else {
       atomicAdd(&a.ctr->v_starts, we.s.count);
@@ -625,8 +677,55 @@ static void launch_t2(const TravArgs &a, int sms, cudaStream_t st) {
       a);
 }
 
+// One refinement round's traversal over up to cap sorted boxes (their count
+// on the device): one box per leaf, binary nodes, two nodes per step.
+int traverse_round(const QBox *qbox, const uint32_t *qlink, const SBox *sbox,
+                   const uint32_t *sobj, const uint32_t *sid, int64_t cap,
+                   const unsigned long long *d_N, int64_t T, DevCounters *ctr, uint32_t *rflags,
+                   unsigned long long *rcand, unsigned long long *rncand, unsigned long long rcap,
+                   int spans, int deep, cudaStream_t st) {
+  if (cap < 2) return SCD_OK;
+  if ((reinterpret_cast<uintptr_t>(sbox) | reinterpret_cast<uintptr_t>(qbox)) & 31)
+    return SCD_ERR_INTERNAL;
+  TravArgs a{};
+  a.qbox = qbox;
+  a.qlink = qlink;
+  a.sbox = sbox;
+  a.sobj = sobj;
+  a.sid = sid;
+  a.N = cap;
+  a.L = 1;
+  a.T = (int)T;
+  a.ctr = ctr;
+  a.dkind = SCD_DECOMP_NONE;
+  a.d_N = d_N;
+  a.rflags = rflags;
+  a.rcand = rcand;
+  a.rncand = rncand;
+  a.rcap = rcap;
+  a.rspans = spans;
+  static int sms = 0, per64 = 0, per128 = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per64, k_traverse2<64, true, false, true>,
+                                                  kT2Threads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per128, k_traverse2<128, true, false, true>,
+                                                  kT2Threads, 0);
+  }
+  if (deep)
+    k_traverse2<128, true, false, true>
+        <<<(unsigned)(sms * std::max(per128, 1)), kT2Threads, 0, st>>>(a);
+  else
+    k_traverse2<64, true, false, true>
+        <<<(unsigned)(sms * std::max(per64, 1)), kT2Threads, 0, st>>>(a);
+  note_launch();
+  return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
+}
+
 int traverse(scd_scene *s, int64_t n_leaves, int raw_mode, int obj_bits, int t_bits) {
-  TravArgs a;
+  TravArgs a{};
   a.nodes = s->d_nodes.p;
   a.qbox = s->d_qbox.p;
   a.qlink = s->d_qlink.p;

@@ -3,7 +3,8 @@ C ABI) with the oracle: the witness list is exact (Alg 1's test decides every
 tick candidate), so it must equal the oracle's refinement and Alg 1 witness
 for witness, in Alg 1's order.  The rounds' interval counts come from
 overlap tests of FP32 boxes whose centres agree with the oracle's to 1e-7 km,
-so they may differ where two boxes touch; they must agree within 2%."""
+so they may differ where two boxes touch; they must agree within 2%.  Both
+box modes; the 24 h catalog subset against the narrow phase."""
 import math
 
 import numpy as np
@@ -59,10 +60,42 @@ def test_uniform_512_six_thousand_seconds(scd):
     assert mine["t"].tolist() == list(range(6001))
     assert len(rb) == len(orb)
     assert abs(int(rb.sum()) - int(orb.sum())) <= 0.02 * orb.sum()
-    # an INTERVAL-mode scene refines with the same SPEED boxes
+    # an INTERVAL-mode scene refines with INTERVAL boxes (Sec. 4.5): the
+    # same witnesses (both exact), the oracle's rounds with its INTERVAL boxes
     sc2 = _scene(scd, els, 6000.0, mode=1)
     w2, rb2 = sc2.refine_witnesses()
-    assert _tuples(w2) == _tuples(w) and rb2.tolist() == rb.tolist()
+    ow2, orb2, _ = O.refine_discrete(els, 6000, 1.0, O.BOX_INTERVAL)
+    assert _tuples(w2) == _tuples(w) == _tuples(ow2)
+    assert len(rb2) == len(orb2)
+    assert abs(int(rb2.sum()) - int(orb2.sum())) <= 0.02 * orb2.sum()
+    # tighter boxes: fewer intervals in all
+    assert rb2.sum() < rb.sum()
+    sc.close()
+    sc2.close()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_catalog_subset_full_day(scd, mode):
+    """The refinement at the catalog workload's horizon: 2000 objects of the
+    mixture (with seeded crossing pairs) over 24 h at 1 s ticks.  Its
+    witnesses equal the narrow phase's over the fixed-step screen's
+    candidates (P/100 steps), and every seeded crossing is among them."""
+    els, cr = P.catalog_mixture(n=2000, seed=23, crossing_frac=0.004, horizon_s=86400.0,
+                                return_crossings=True)
+    T = 86400
+    sc = _scene(scd, els, float(T), mode=mode)
+    w, rb = sc.refine_witnesses()
+    assert len(rb) <= math.ceil(math.log2(T + 1)) + 2
+    got = set(_tuples(w))
+    for (b, c, tc) in cr:
+        assert (b, c, tc) in got
+    step = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=100.0)
+    sc2 = scd.Scene(els, float(T), 1.0, step=step, mode=mode).build_boxes()
+    first, count, earliest = sc2.narrow_phase(sc2.find_pairs_device())
+    assert int(count.cpu().numpy().astype(np.int64).sum()) == len(w)
+    assert earliest == (tuple(_tuples(w[:1])[0]) if len(w) else None)
+    print(f"24 h, 2000 objects, mode {mode}: {len(w)} witnesses, {len(rb)} rounds, "
+          f"{int(rb.sum())} intervals, peak {int(rb.max())}")
     sc.close()
     sc2.close()
 
@@ -154,4 +187,54 @@ def test_continuous_equals_oracle_and_covers_alg1(scd, seed):
         assert np.any((m["t0"] <= t) & (t <= m["t1"])), (i, j, t)
     with pytest.raises(scd.ScdError):
         sc.refine_continuous(0.0)
+    sc.close()
+
+
+def _round_intervals(lo, hi, obj):
+    return sorted(zip(obj.astype(np.int64).tolist(), lo[:, 3].astype(np.int64).tolist(),
+                      hi[:, 3].astype(np.int64).tolist()))
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_every_round_follows_from_its_own_boxes(scd, mode):
+    """Exact per-round parity: each round's intervals are exactly the
+    oracle's round rule applied to the GPU's own FP32 boxes of the round
+    before (every pair of other objects' boxes tested), and every box is the
+    oracle's box of its interval within one FP32 ulp (512 objects, 6000 s,
+    with a pair of identical elements)."""
+    els = P.uniform_leo(512)
+    els[511] = els[7]
+    sc = _scene(scd, els, 6000.0, mode=mode)
+    tr = scd.scd_refine_trace(sc.handle)
+    w, rb = sc.refine_witnesses()
+    assert [len(o) for _, _, o in tr] == rb.tolist()
+    g = np.random.default_rng(mode)
+    for r, (lo, hi, obj) in enumerate(tr):
+        want = O.refine_round(lo, hi, obj, False)
+        if r + 1 < len(tr):
+            assert _round_intervals(*tr[r + 1]) == sorted(map(tuple, want.tolist())), r
+        else:
+            assert len(want) == 0
+        for q in g.choice(len(obj), min(200, len(obj)), replace=False):
+            ol, oh, _, _ = O.box(els[obj[q]], mode, int(lo[q, 3]), int(hi[q, 3]), 1.0)
+            assert np.all(np.abs(lo[q].view(np.int32) - ol.view(np.int32)) <= 1)
+            assert np.all(np.abs(hi[q].view(np.int32) - oh.view(np.int32)) <= 1)
+    sc.close()
+
+
+def test_every_continuous_round_follows_from_its_own_boxes(scd):
+    els = P.uniform_leo(10, seed=310, radius_km=400.0)
+    sc = _scene(scd, els, 300.0)
+    tr = scd.scd_refine_trace(sc.handle, 0.5)
+    spans, rb = sc.refine_continuous(0.5)
+    assert [len(o) for _, _, o in tr] == rb.tolist()
+    for r in range(len(tr) - 1):
+        want = O.refine_round(*tr[r], True)
+        assert _round_intervals(*tr[r + 1]) == sorted(map(tuple, want.tolist())), r
+    # the spans are the meeting pairs of the last round's own boxes
+    lo, hi, obj = tr[-1]
+    unit = 300.0 / 2 ** (len(tr) - 1)
+    cells = O.raw_cells_bruteforce(lo, hi, obj)
+    want = sorted({(int(c["i"]), int(c["j"]), c["tlo"] * unit, c["thi"] * unit) for c in cells})
+    assert sorted(map(tuple, spans.tolist())) == want
     sc.close()

@@ -123,7 +123,70 @@ def test_trained_steps_beat_the_period_rule_on_held_out_objects(mods):
           f"(c_box={c_box:.3e}, c_hit={c_hit:.3e})")
     assert cost_learned <= cost_rule
     sc.close()
+    # measured: the held-out screen (boxes through the canonical list) under
+    # both step rules, CUDA events on the stream, median of 7 after 2 warm-up
+    # screens, L2 flushed before each
+    rule = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=100.0)
+    ms, cands = {}, {}
+    for name, pol in (("learned", net.policy()), ("P/100", rule)):
+        sc = scd.Scene(test_els, 21600.0, 1.0, pol)
+        ms[name], cands[name] = _timed_screen(scd, sc, reps=7)
+        sc.close()
+    # at this size the learned steps give fewer candidates but more boxes,
+    # and measured they are not faster (the linear cost model misjudges a
+    # 2 ms screen); the gain in time is asserted at scale below
+    print(f"measured: learned {ms['learned']:.3f} ms, {cands['learned']} candidates; "
+          f"P/100 {ms['P/100']:.3f} ms, {cands['P/100']} candidates")
+    assert cands["learned"] < cands["P/100"]
     net.close()
+
+
+def test_learned_steps_are_faster_at_scale(mods):
+    """Measured gain at the size the learned component is meant for: train on
+    the sweeps of one 100,000-object population with dense LEO shells (24 h,
+    INTERVAL boxes, ten step multipliers P/70-P/280), then screen a held-out
+    population of the same shape under the learned steps and under P/100:
+    fewer candidates and a shorter screen (CUDA events, median of 5 after 2
+    warm-up screens, L2 flushed before each)."""
+    scd, sn = mods
+    mode = scd.SCD_BOX_INTERVAL
+    train_els = P.catalog_mixture(n=100000, seed=P.SEED_BASE + 6, dense_shells=True)
+    mults = tuple(float(70.0 * 4.0 ** (q / 9.0)) for q in range(10))
+    sw = sn.sweep(train_els, 86400.0, multipliers=mults, mode=mode, count="runs")
+    c_box, c_hit = sn.fit_cost_model(sw)
+    Y = sn.targets(train_els, sw, c_box, c_hit).astype(np.float32)
+    X = sn.features(train_els).cpu().numpy()
+    net = sn.StepNet(seed=7)
+    sn.train(net, X, Y, epochs=40, batch=1024, lr=3e-3)
+    test_els = P.catalog_mixture(n=100000, seed=P.SEED_BASE + 5, dense_shells=True)
+    rule = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=100.0)
+    ms, cands = {}, {}
+    for name, pol in (("learned", net.policy()), ("P/100", rule)):
+        sc = scd.Scene(test_els, 86400.0, 1.0, pol, mode=mode)
+        ms[name], cands[name] = _timed_screen(scd, sc, reps=5)
+        sc.close()
+    print(f"100k, 24 h, INTERVAL: learned {ms['learned']:.1f} ms, {cands['learned']} "
+          f"candidates; P/100 {ms['P/100']:.1f} ms, {cands['P/100']} candidates")
+    assert cands["learned"] < cands["P/100"]
+    assert ms["learned"] < ms["P/100"]
+    net.close()
+
+
+def _timed_screen(scd, sc, reps):
+    st = torch.cuda.current_stream()
+    flush = torch.empty(2 * 129 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ts, n = [], 0
+    for k in range(reps + 2):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        scd.scd_build_boxes(sc.handle)
+        n = scd.scd_find_pairs_device(sc.handle)[1]
+        e1.record(st)
+        e1.synchronize()
+        if k >= 2:
+            ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts)), n
 
 
 def _covered(pairs, near):

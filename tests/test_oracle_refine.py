@@ -124,3 +124,36 @@ def test_continuous_robustly_safe_system_is_proven_safe():
                     [42164.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0]])
     spans, rb = O.refine_continuous(els, 86400.0, 0.01, O.BOX_INTERVAL)
     assert len(spans) == 0 and rb.sum() <= 100
+
+
+@pytest.mark.parametrize("mode", [O.BOX_SPEED, O.BOX_INTERVAL])
+def test_round_step_reproduces_the_refinement(mode):
+    """The round step applied to given boxes (used to check each GPU round
+    on the GPU's own boxes): iterated from [0, T] on the oracle's boxes it
+    gives the oracle refinement's intervals per round exactly, in both the
+    discrete and the continuous rule."""
+    els = P.uniform_leo(10, seed=310, radius_km=400.0)
+    T = 300
+
+    def run(cont, levels=None):
+        cur = np.array([[i, 0, 1 if cont else T] for i in range(len(els))], np.int64)
+        sizes = []
+        r = 0
+        while len(cur) and (levels is None or r <= levels):
+            sizes.append(len(cur))
+            unit = T / 2 ** r if cont else 1.0
+            lo = np.zeros((len(cur), 4), np.float32)
+            hi = np.zeros((len(cur), 4), np.float32)
+            for q, (o, t0, t1) in enumerate(cur):
+                lo[q], hi[q], _, _ = O.box(els[o], mode, int(t0), int(t1), unit)
+            if cont and r == levels:
+                break
+            cur = O.refine_round(lo, hi, cur[:, 0], cont)
+            r += 1
+        return sizes
+
+    _, orb, _ = O.refine_discrete(els, T, 1.0, mode)
+    assert run(False) == orb.tolist()
+    _, crb = O.refine_continuous(els, float(T), 0.5, mode)
+    L = len(crb) - 1
+    assert run(True, L) == crb.tolist()
