@@ -19,7 +19,7 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib",
                              "autotune_cache.json")
 
 STAGE1 = [dict(leaf_size=L, morton_bits=b, space_warp=w)
-          for L in (1, 2, 4) for b in (8, 10, 16) for w in (0, 1)]
+          for L in (1, 2, 4) for b in (8, 10, 12, 16) for w in (0, 1)]
 
 
 def _time_screen(scene, reps: int, decomp=None) -> float:
@@ -51,7 +51,7 @@ def workload_key(elements, horizon_s: float, tick_s: float, step_desc: str, nbox
 
 
 STAGE1_DECOMPOSED = [dict(leaf_size=1, morton_bits=b, space_warp=w)
-                     for b in (8, 10) for w in (0, 1)]
+                     for b in (8, 10, 12) for w in (0, 1)]
 
 
 def tune(scene, reps: int = 2, verbose: bool = False, decomp=None):
@@ -60,6 +60,10 @@ def tune(scene, reps: int = 2, verbose: bool = False, decomp=None):
     list of (tuning, ms))."""
     from . import _binding as B
     base = {f: getattr(B.scd_default_tuning(), f) for f, _ in B.scd_tuning._fields_}
+    if decomp is not None:
+        # decomposed screens start from time and space weighed equally and no
+        # size split (the plain screen's choices; stage 2 tries the others)
+        base.update(time_scale=1.0, split_km=0.0)
     results = []
 
     def run(cand):
@@ -77,10 +81,11 @@ def tune(scene, reps: int = 2, verbose: bool = False, decomp=None):
         ms = run(cand)
         if ms < best_ms:
             best, best_ms = dict(cand), ms
-    stage2 = [dict(best, time_scale=ts) for ts in (0.5, 0.25)]
+    stage2 = [dict(best, time_scale=ts) for ts in (1.0, 4.0, 8.0, 16.0) if ts != base["time_scale"]]
     stage2 += [dict(best, stack_depth=sd) for sd in (32, 128)]
     # the size split: off, a finer and a coarser threshold than the default
-    stage2 += [dict(best, split_km=sk) for sk in (0.0, -500.0, -2000.0)]
+    stage2 += [dict(best, split_km=sk) for sk in (0.0, -500.0, -1000.0, -2000.0)
+               if sk != base["split_km"]]
     if best["leaf_size"] > 1:
         stage2 += [dict(best, block_threads=bt) for bt in (64, 256)]
     else:

@@ -203,24 +203,29 @@ __device__ inline unsigned long long morton4(uint32_t x, uint32_t y, uint32_t z,
 
 // 4D Morton key (bits per axis) of a box centre in the scene cube [-R, R]^3
 // x [0, T]; optionally log-compressed in space (a monotone map, so any key
-// order is a valid tree order)
+// order is a valid tree order).  time_scale weighs time against space: below
+// 1 the horizon takes that share of the time axis's cells, above 1 the
+// scene cube takes 1 / time_scale of the space axes' cells (around the
+// centre), so time counts that many times more in the curve's order.
 __device__ inline unsigned long long box_morton(float4 L, float4 H, double R, int64_t T, int bits,
                                                 float time_scale, int space_warp) {
+  const float sw = time_scale > 1.0f ? 1.0f / time_scale : 1.0f;
+  const float tw = time_scale > 1.0f ? 1.0f : time_scale;
   float ux, uy, uz;
   if (space_warp) {
     const float s_km = 1000.0f;
-    float inv = 0.5f / log1pf((float)R / s_km);
+    float inv = sw * 0.5f / log1pf((float)R / s_km);
     float cx = 0.5f * (L.x + H.x), cy = 0.5f * (L.y + H.y), cz = 0.5f * (L.z + H.z);
     ux = copysignf(log1pf(fabsf(cx) / s_km), cx) * inv + 0.5f;
     uy = copysignf(log1pf(fabsf(cy) / s_km), cy) * inv + 0.5f;
     uz = copysignf(log1pf(fabsf(cz) / s_km), cz) * inv + 0.5f;
   } else {
-    float inv = (float)(0.5 / R);
+    float inv = sw * (float)(0.5 / R);
     ux = (0.5f * (L.x + H.x)) * inv + 0.5f;
     uy = (0.5f * (L.y + H.y)) * inv + 0.5f;
     uz = (0.5f * (L.z + H.z)) * inv + 0.5f;
   }
-  float ut = (float)((0.5 * ((double)L.w + (double)H.w)) / (double)(T + 1)) * time_scale;
+  float ut = (float)((0.5 * ((double)L.w + (double)H.w)) / (double)(T + 1)) * tw;
   return morton4(quantize(ux, bits), quantize(uy, bits), quantize(uz, bits), quantize(ut, bits),
                  bits);
 }

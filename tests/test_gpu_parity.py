@@ -172,7 +172,8 @@ def test_tunings_give_identical_sets(scd, leaf, bits):
     els = P.uniform_leo(200, seed=77, radius_km=40.0)
     pol = scd.make_step_policy(scd.SCD_STEP_FIXED, fixed_ticks=7)
     tuning = dict(leaf_size=leaf, morton_bits=bits, stack_depth=32, block_threads=64,
-                  space_warp=int(bits == 10), time_scale=0.5 if bits == 16 else 1.0,
+                  space_warp=int(bits == 10),
+                  time_scale={8: 4.0, 10: 1.0, 16: 0.5}[bits],
                   nodes_per_step=1 if bits == 10 else 2,
                   node_width=4 if leaf == 1 and bits != 10 else 2)
     _screen_parity(scd, els, 1500, pol, tuning=tuning, raw_too=(leaf == 4))
@@ -183,6 +184,19 @@ def test_mixture_variable_steps_bit_exact(scd, mode):
     els = P.catalog_mixture(n=600, seed=31, radius_km=25.0)
     pol = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=100.0)
     got, m = _screen_parity(scd, els, 20000, pol, mode=mode)
+    assert len(got) > 100
+
+
+@pytest.mark.parametrize("split_km,time_scale", [(0.0, 1.0), (-1000.0, 4.0), (1000.0, 16.0),
+                                                 (-300.0, 0.25)])
+def test_key_order_options_bit_exact(scd, split_km, time_scale):
+    # the mixture has boxes on both sides of every threshold (LEO, MEO, GEO,
+    # HEO SPEED boxes): the size split and the time weight only reorder the
+    # tree, so the pair list stays the oracle's
+    els = P.catalog_mixture(n=600, seed=32, radius_km=25.0)
+    pol = scd.make_step_policy(scd.SCD_STEP_PERIOD_FRACTION, period_fraction=100.0)
+    tuning = dict(split_km=split_km, time_scale=time_scale)
+    got, m = _screen_parity(scd, els, 20000, pol, tuning=tuning)
     assert len(got) > 100
 
 
