@@ -953,6 +953,9 @@ def main():
         line["roofline"] = {"kernel_phase": name, "bound": "hbm", "achieved": achieved,
                             "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                             "traffic": traffic,
+                            "traffic_source": ("committed ncu capture of these sources "
+                                               "(profiles/k_traverse2_catalog16848_24h.md)"
+                                               if traffic is not None else None),
                             "peak_source": src, "phase_ms": ph,
                             "algorithmic_bytes": byt[name]}
         if "phase_ms_source" in r:
