@@ -806,7 +806,7 @@ def cpu_baseline_measure():
     other (the sample is representative of the horizon)."""
     T = int(HORIZON_S / TICK_S)
     cores = os.cpu_count() or 1
-    n_all, w_all, w_one = 2 * cores, 60, 100
+    n_all, w_all, w_one = 3 * cores, 60, 100
     starts = _windows(n_all, w_all, T)
     wall, busy, nbox, npair, per = cpu_oracle_windows(starts, w_all, cores)
     scale = (T + 1) / (n_all * w_all)
@@ -871,7 +871,7 @@ def main():
         # all host cores (a bounded share of the horizon, scaled up)
         T = int(HORIZON_S / TICK_S)
         cores = os.cpu_count() or 1
-        n_w, w_t = cores, 60
+        n_w, w_t = 2 * cores, 60
         vals, sdesc = [], ""
         for _ in range(args.warmup):  # warm-up steps: one short window
             cpu_oracle_windows(_windows(1, 10, T), 10, 1)
