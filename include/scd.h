@@ -136,7 +136,10 @@ typedef struct {
   float time_scale;   /* weight of time against space in the Morton key,
                          (0, 16]: below 1 the horizon takes that share of
                          the time axis's cells; above 1 the scene cube takes
-                         1/time_scale of the space axes' cells (default 8) */
+                         1/time_scale of the space axes' cells (default 8).
+                         The time axis spans the horizon; in a decomposed
+                         screen a tick slab's ticks, in a batch the box's
+                         own scene's horizon                               */
   int use_graph;      /* 1: replay find_pairs as one captured CUDA graph    */
   int space_warp;     /* 1: log-compress |x| before quantising (finer keys
                          near Earth, where most boxes are); 0: linear      */
@@ -373,8 +376,8 @@ SCD_API int scd_propagate_noalloc(const scd_element *d_elems, int64_t n, const u
  * sorted by (i, j, tlo) with batch-wide object indices, so each scene's
  * pairs are contiguous; scd_batch_scene_offsets gives where (host array of
  * n_scenes + 1 entries).  Pairs never join objects of different scenes.
- * The batch's tuning starts as scd_default_tuning with split_km = 0,
- * time_scale = 1 and morton_bits = 10 (measured best for batches). */
+ * The batch's tuning starts as scd_default_tuning; each scene's boxes are
+ * keyed in a time frame of that scene's own horizon. */
 SCD_API int scd_batch_scene_create(const scd_element *elems, const int64_t *scene_offsets,
                                    const double *horizons_s, int n_scenes, double tick_s,
                                    const scd_step_policy *step, scd_box_mode mode,

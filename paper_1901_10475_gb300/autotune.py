@@ -60,10 +60,6 @@ def tune(scene, reps: int = 2, verbose: bool = False, decomp=None):
     list of (tuning, ms))."""
     from . import _binding as B
     base = {f: getattr(B.scd_default_tuning(), f) for f, _ in B.scd_tuning._fields_}
-    if decomp is not None:
-        # decomposed screens start from time and space weighed equally and no
-        # size split (the plain screen's choices; stage 2 tries the others)
-        base.update(time_scale=1.0, split_km=0.0)
     results = []
 
     def run(cand):

@@ -19,6 +19,8 @@
 //              meets; two objects are joined in the potential-collision
 //              graph (Def 9) iff their ranges intersect, and the point is the
 //              lower end of that intersection.
+#include <algorithm>
+
 #include "scd_internal.cuh"
 
 namespace scd {
@@ -31,6 +33,7 @@ struct DecompArgs {
   const double2 *rr;  // radial ranges (ALT_BANDS)
   const double *edges;
   const int32_t *objscene;  // scene of each object (a batch of scenes)
+  const int32_t *objT;      // horizon of each object's scene [ticks] (a batch)
 };
 
 __global__ void k_radial(const scd_element *__restrict__ el, int64_t n, double2 *__restrict__ rr,
@@ -98,39 +101,62 @@ __global__ void k_ref_count(const float4 *__restrict__ lo, const float4 *__restr
     cnt[b] = c.b1 - c.b0 + 1;
 }
 
+// A reference's key: its cell above the size bit (if any) above the top
+// mbits bits of the box's Morton key.  The key's time frame is the cell's
+// own: a tick slab's ticks, a batch scene's horizon, else the scene's.
+struct RefKeyArgs {
+  int bits;          // Morton bits per axis
+  int mbits;         // Morton bits kept (the top ones)
+  float time_scale;
+  int space_warp;
+  float split_km;    // 0: no size bit
+};
+
+__device__ __forceinline__ unsigned long long ref_morton(const RefKeyArgs &k, float4 L, float4 H,
+                                                         float R, float t0, float T1) {
+  L.w -= t0;
+  H.w -= t0;
+  unsigned long long m = box_morton(L, H, R, T1, k.bits, k.time_scale, k.space_warp);
+  m >>= (4 * k.bits - k.mbits);
+  if (k.split_km != 0.0f)
+    m |= (unsigned long long)split_bit(L, H, k.split_km) << k.mbits;
+  return m;
+}
+
 __global__ void k_ref_scatter(const float4 *__restrict__ lo, const float4 *__restrict__ hi,
                               const uint32_t *__restrict__ obj, int64_t N, DecompArgs d,
                               const int64_t *__restrict__ off, const DevCounters *__restrict__ ctr,
-                              int bits, float time_scale, int space_warp, float split_km,
-                              int64_t cap,
+                              RefKeyArgs ka, int64_t cap,
                               unsigned long long *__restrict__ key, uint32_t *__restrict__ id) {
   int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= N) return;
   float4 L = lo[b], H = hi[b];
-  CellSpan c = cell_span(d, L, H, obj[b]);
-  double R = __longlong_as_double((long long)ctr->extent_bits);
-  // the top 32 bits of the box's Morton key order it inside its cell
-  unsigned long long m = box_morton(L, H, R, d.T, bits, time_scale, space_warp);
-  if (4 * bits > 32) m >>= (4 * bits - 32);
-  // the size group, if any, above the 31 highest Morton bits
-  if (split_km != 0.0f) m = ((unsigned long long)split_bit(L, H, split_km) << 31) | (m >> 1);
+  const uint32_t ob = obj[b];
+  CellSpan c = cell_span(d, L, H, ob);
+  const float R = (float)__longlong_as_double((long long)ctr->extent_bits);
+  const int cshift = ka.mbits + (ka.split_km != 0.0f ? 1 : 0);
   int64_t o = off[b];
   if (d.kind == SCD_DECOMP_SLAB_OCT) {
-    for (int s = c.s0; s <= c.s1; ++s)
+    const float slab = (float)(d.T + 1) / (float)d.n_slabs;
+    for (int s = c.s0; s <= c.s1; ++s) {
+      const unsigned long long m = ref_morton(ka, L, H, R, (float)s * slab, slab);
       for (int x = c.x0; x <= c.x1; ++x)
         for (int y = c.y0; y <= c.y1; ++y)
           for (int z = c.z0; z <= c.z1; ++z) {
             unsigned long long cell = (unsigned long long)(s * 8 + (x << 2) + (y << 1) + z);
             if (o < cap) {
-              key[o] = (cell << 32) | m;
+              key[o] = (cell << cshift) | m;
               id[o] = (uint32_t)b;
             }
             ++o;
           }
+    }
   } else {
+    const float T1 = (float)((d.objT ? (int64_t)d.objT[ob] : d.T) + 1);
+    const unsigned long long m = ref_morton(ka, L, H, R, 0.0f, T1);
     for (int k = c.b0; k <= c.b1; ++k) {
       if (o < cap) {
-        key[o] = ((unsigned long long)k << 32) | m;
+        key[o] = ((unsigned long long)k << cshift) | m;
         id[o] = (uint32_t)b;
       }
       ++o;
@@ -174,6 +200,7 @@ int build_decomposed(scd_scene *s, const scd_decomp *dc, int64_t &M, bool captur
   d.rr = nullptr;
   d.edges = nullptr;
   d.objscene = s->d_objscene.p;
+  d.objT = s->n_scenes > 0 ? s->d_objT.p : nullptr;
   int n_cells = d.kind == SCD_DECOMP_SLAB_OCT ? d.n_slabs * 8
                 : d.kind == kDecompScenes     ? s->n_scenes
                                               : d.p;
@@ -221,15 +248,26 @@ int build_decomposed(scd_scene *s, const scd_decomp *dc, int64_t &M, bool captur
       !s->s_leafkey64.ensure(R, st) || !s->d_cellroot.ensure(n_cells, st) ||
       !s->d_refcnt.ensure(2 * (size_t)n_cells > (size_t)N ? 2 * n_cells : N, st))
     return SCD_ERR_OOM;
-  k_ref_scatter<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(
-      s->d_lo.p, s->d_hi.p, s->d_obj.p, N, d, s->d_refoff.p, s->d_ctr.p, s->tune.morton_bits,
-      s->tune.time_scale, s->tune.space_warp, s->tune.split_km, R, s->d_refkey.p, s->d_refid.p);
-  note_launch();
+  // the cell's bits above the size bit and as many of the Morton key's top
+  // bits as the rest of 64 holds
   int cbits = 1;
   while ((1 << cbits) < n_cells) ++cbits;
-  rc = radix_sort_u64(s->d_refkey.p, s->d_refid.p, R, 32 + cbits, s->sort_sc, st);
+  RefKeyArgs ka;
+  ka.bits = s->tune.morton_bits;
+  ka.time_scale = s->tune.time_scale;
+  ka.space_warp = s->tune.space_warp;
+  ka.split_km = s->tune.split_km;
+  const int sb = ka.split_km != 0.0f ? 1 : 0;
+  ka.mbits = std::min(4 * ka.bits, 64 - cbits - sb);
+  k_ref_scatter<<<(unsigned)((N + bs - 1) / bs), bs, 0, st>>>(
+      s->d_lo.p, s->d_hi.p, s->d_obj.p, N, d, s->d_refoff.p, s->d_ctr.p, ka, R, s->d_refkey.p,
+      s->d_refid.p);
+  note_launch();
+  const int cshift = ka.mbits + sb;
+  rc = radix_sort_u64(s->d_refkey.p, s->d_refid.p, R, cshift + cbits, s->sort_sc, st);
   if (rc) return rc;
-  rc = build_tree<unsigned long long>(s, s->d_refkey.p, s->d_refid.p, R, s->s_leafkey64.p, 32, M);
+  rc = build_tree<unsigned long long>(s, s->d_refkey.p, s->d_refid.p, R, s->s_leafkey64.p, cshift,
+                                      M);
   if (rc) return rc;
   // cell bounds (reusing the count buffer as two int32 arrays) and roots
   int32_t *cfirst = (int32_t *)s->d_refcnt.p, *clast = cfirst + n_cells;

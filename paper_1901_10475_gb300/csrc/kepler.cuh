@@ -78,6 +78,20 @@ __device__ __forceinline__ void sincos_tab(double x, double &s, double &c) {
   c = fma(ck, cr, -(sk * sr));
 }
 
+// num / den for the Newton step's denominator 1 - e cos E (in [1 - e, 1 + e],
+// e < 1): the single-precision reciprocal estimate of PTX rcp.approx (within
+// 2^-22 with the rounding of den to FP32) refined by one Newton-Raphson step
+// for 1 / den, r <- r + r (1 - den r), which squares its relative error (to
+// about 2^-44).  The quotient is a Newton correction, so an error of 1e-13 of
+// it is far below the solve's tolerance.
+__device__ __forceinline__ double div_newton(double num, double den) {
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)den));
+  double r = (double)rf;
+  r = fma(r, fma(-den, r, 1.0), r);
+  return num * r;
+}
+
 // ---------------------------------------------------------------------------
 // Kepler's equation E - e sin E = M by Newton's method.  The start is
 // M + e sin M for moderate e and Danby's M + 0.85 e sign(sin M) above
@@ -110,7 +124,7 @@ static __device__ __noinline__ void kepler_more_fp64(double M, double e, double 
     Ed -= d;
     sincos_tab(Ed, s, c);
     const double fp = 1.0 - e * c;
-    d = (Ed - e * s - M) / fp;
+    d = div_newton(Ed - e * s - M, fp);
     iters += 1;
     if (!(2.0 * fabs(e * s) * d * d > tol * fp || fabs(d) > 1e-5)) return;
   }
@@ -138,7 +152,7 @@ __device__ __forceinline__ double kepler_E_sc(double M, double e, double tol, do
   double Ed = (double)E, s, c;
   sincos_tab(Ed, s, c);
   double fp = 1.0 - e * c;
-  double d = (Ed - e * s - M) / fp;
+  double d = div_newton(Ed - e * s - M, fp);
   iters = it + 1;
   // error left after this step (with a factor 4 of safety) above tol,
   // compared without a second FP64 division: 2 |e s| d^2 / fp > tol

@@ -129,6 +129,7 @@ struct BoxArgs {
   int64_t n;
   int64_t N;
   int64_t T;
+  float T1f;         // T + 1 (the key frame's time extent)
   double tick_s;
   int mode;
   int bits;          // Morton bits per axis
@@ -184,8 +185,8 @@ __global__ void __launch_bounds__(256) k_build_boxes(BoxArgs a) {
   a.id[b] = (uint32_t)b;
 
   // 4D Morton key of the box centre in the scene's bounding cube
-  double R = __longlong_as_double((long long)a.ctr->extent_bits);
-  unsigned long long key = box_morton(L, H, R, a.T, a.bits, a.time_scale, a.space_warp);
+  const float R = (float)__longlong_as_double((long long)a.ctr->extent_bits);
+  unsigned long long key = box_morton(L, H, R, a.T1f, a.bits, a.time_scale, a.space_warp);
   key |= (unsigned long long)split_bit(L, H, a.split_km) << (4 * a.bits);
   if (a.key64) a.key64[b] = key;
   else a.key32[b] = (uint32_t)key;
@@ -199,6 +200,7 @@ int launch_build_boxes(scd_scene *s) {
   a.n = s->n;
   a.N = s->N;
   a.T = s->T;
+  a.T1f = (float)(s->T + 1);
   a.tick_s = s->tick_s;
   a.mode = s->box_mode;
   a.bits = s->tune.morton_bits;

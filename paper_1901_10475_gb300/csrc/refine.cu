@@ -118,8 +118,9 @@ __global__ void __launch_bounds__(kRfThreads) k_rf_boxes(RfBoxArgs a) {
   H.w = (float)t1;
   a.lo[i] = L;
   a.hi[i] = H;
-  const double R = __longlong_as_double((long long)a.ctr->extent_bits);
-  unsigned long long k = box_morton(L, H, R, a.Tf, kRfMortonBits, kRfTimeScale, 0);
+  const float R = (float)__longlong_as_double((long long)a.ctr->extent_bits);
+  unsigned long long k =
+      box_morton(L, H, R, (float)(a.Tf + 1), kRfMortonBits, kRfTimeScale, 0);
   k |= (unsigned long long)split_bit(L, H, a.split_km) << (4 * kRfMortonBits);
   a.key[i] = k;
   a.idx[i] = (uint32_t)i;

@@ -207,25 +207,26 @@ __device__ inline unsigned long long morton4(uint32_t x, uint32_t y, uint32_t z,
 // 1 the horizon takes that share of the time axis's cells, above 1 the
 // scene cube takes 1 / time_scale of the space axes' cells (around the
 // centre), so time counts that many times more in the curve's order.
-__device__ inline unsigned long long box_morton(float4 L, float4 H, double R, int64_t T, int bits,
+// R is the cube's half-side, T1 the horizon plus one tick; all in FP32.
+__device__ inline unsigned long long box_morton(float4 L, float4 H, float R, float T1, int bits,
                                                 float time_scale, int space_warp) {
   const float sw = time_scale > 1.0f ? 1.0f / time_scale : 1.0f;
   const float tw = time_scale > 1.0f ? 1.0f : time_scale;
   float ux, uy, uz;
   if (space_warp) {
     const float s_km = 1000.0f;
-    float inv = sw * 0.5f / log1pf((float)R / s_km);
+    float inv = sw * 0.5f / log1pf(R / s_km);
     float cx = 0.5f * (L.x + H.x), cy = 0.5f * (L.y + H.y), cz = 0.5f * (L.z + H.z);
     ux = copysignf(log1pf(fabsf(cx) / s_km), cx) * inv + 0.5f;
     uy = copysignf(log1pf(fabsf(cy) / s_km), cy) * inv + 0.5f;
     uz = copysignf(log1pf(fabsf(cz) / s_km), cz) * inv + 0.5f;
   } else {
-    float inv = sw * (float)(0.5 / R);
+    float inv = sw * (0.5f / R);
     ux = (0.5f * (L.x + H.x)) * inv + 0.5f;
     uy = (0.5f * (L.y + H.y)) * inv + 0.5f;
     uz = (0.5f * (L.z + H.z)) * inv + 0.5f;
   }
-  float ut = (float)((0.5 * ((double)L.w + (double)H.w)) / (double)(T + 1)) * tw;
+  float ut = (0.5f * (L.w + H.w)) / T1 * tw;  // ticks below 2^24: the sum is exact
   return morton4(quantize(ux, bits), quantize(uy, bits), quantize(uz, bits), quantize(ut, bits),
                  bits);
 }

@@ -656,13 +656,6 @@ extern "C" SCD_API int scd_batch_scene_create(const scd_element *elems,
   cudaStream_t st = s->stream;
   s->n_scenes = n_scenes;
   s->scene_off.assign(scene_offsets, scene_offsets + n_scenes + 1);
-  // a batch keys its boxes without the size split, with time and space
-  // weighed equally and 10-bit axes: on the 64-scene batch (INTERVAL boxes,
-  // horizons up to 72 h) the plain screen's split and time weight made the
-  // traversal 3.2x slower
-  s->tune.split_km = 0.0f;
-  s->tune.time_scale = 1.0f;
-  s->tune.morton_bits = 10;
   if (!s->d_objT.ensure(n, st) || !s->d_objscene.ensure(n, st) ||
       !s->d_sceneoff.ensure(n_scenes + 1, st) || !s->d_pairoff.ensure(n_scenes + 1, st)) {
     scd_scene_destroy(s);
