@@ -220,7 +220,12 @@ SCD_API int scd_build_boxes(scd_scene *s);
  * (Sec. 3.2 query semantics; Sec. 5 decomposition when d != NULL and
  * d->kind != NONE).  host_out: host array of cap pairs.  On success *n_out
  * is the number of pairs written.  If cap is too small: BUFFER_TOO_SMALL,
- * *n_out = the count needed, nothing written.  Synchronous. */
+ * *n_out = the count needed, nothing written.  Synchronous.  When the list
+ * fits, an eager find sorts it in buckets of the pairs' first objects and
+ * copies each bucket out while the next ones are sorted (the copies overlap
+ * the sort when host_out is pinned); the contents equal the device list of
+ * scd_find_pairs_device.  On any other error the contents of host_out are
+ * unspecified. */
 SCD_API int scd_find_pairs(scd_scene *s, const scd_decomp *d, scd_pair *host_out,
                            int64_t cap, int64_t *n_out);
 

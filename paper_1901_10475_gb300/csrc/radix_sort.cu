@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_downsweep(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t n, const unsigned long long *__restrict__ d_n, int shift,
     const uint32_t *__restrict__ counts, const uint32_t *__restrict__ totals, int64_t nblk,
-    unsigned int *err) {
+    unsigned int *err, int even = 0) {
   n = sort_count(n, d_n);
   const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -213,7 +213,8 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_downsweep(
     if (kVals) bulk_load(b ? vbuf1 : vbuf0, vin + t * kRsTile, 4u * kRsTile, &bar[b]);
   };
 
-  gdig[d] = digit_scan_excl(totals[d], scanbuf);
+  // (even: every digit's range rounded up to an even length)
+  gdig[d] = digit_scan_excl(even ? (totals[d] + 1u) & ~1u : totals[d], scanbuf);
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -386,6 +387,52 @@ static int rs_impl(K *keys, uint32_t *vals, int64_t n, const unsigned long long 
     if (vals) cudaMemcpyAsync(vals, va, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, st);
   }
   return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
+}
+
+// the one slot that ends an odd digit's range of the even partition: a hole
+__global__ void k_partition_gaps(const uint32_t *__restrict__ totals,
+                                 unsigned long long *__restrict__ out) {
+  __shared__ uint32_t scanbuf[256];
+  const uint32_t c = totals[threadIdx.x];
+  const uint32_t at = digit_scan_excl((c + 1u) & ~1u, scanbuf);
+  if (c & 1u) out[at + c] = ~0ull;
+}
+
+int radix_partition_u64(const unsigned long long *kin, unsigned long long *kout, int64_t n,
+                        int shift, SortScratch &sc, uint32_t *h_totals, cudaStream_t st) {
+  for (int d = 0; d < 256; ++d) h_totals[d] = 0;
+  if (n <= 0) return SCD_OK;
+  if (n >= (1ll << 32) - 512) return SCD_ERR_CAPACITY;
+  if ((reinterpret_cast<uintptr_t>(kin) | reinterpret_cast<uintptr_t>(kout)) & 15)
+    return SCD_ERR_INTERNAL;
+  const int64_t nblk = (n + kRsTile - 1) / kRsTile;
+  if (!sc.counts.ensure((size_t)(256 * nblk + 256), st)) return SCD_ERR_OOM;
+  uint32_t *counts = sc.counts.p, *totals = sc.counts.p + 256 * nblk;
+  const size_t smem = 2 * sizeof(unsigned long long) * kRsTile;
+  static int grid = 0;
+  if (!grid) {
+    int sms = 0, per_sm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(k_rs_downsweep<unsigned long long, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rs_downsweep<unsigned long long, false>,
+                                                  kRsThreads, smem);
+    grid = std::max(1, sms) * std::max(1, per_sm);
+  }
+  k_rs_upsweep<unsigned long long><<<(unsigned)nblk, kRsThreads, 0, st>>>(kin, n, nullptr, shift,
+                                                                          counts, nblk);
+  k_rs_scan<<<256, 1024, 0, st>>>(counts, nblk, totals);
+  k_rs_downsweep<unsigned long long, false>
+      <<<(unsigned)std::min<int64_t>(nblk, grid), kRsThreads, smem, st>>>(
+          kin, nullptr, kout, nullptr, n, nullptr, shift, counts, totals, nblk, sc.err, 1);
+  k_partition_gaps<<<1, 256, 0, st>>>(totals, kout);
+  note_launch(4);
+  if (cudaMemcpyAsync(h_totals, totals, 256 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SCD_ERR_CUDA;
+  return SCD_OK;
 }
 
 int radix_sort_u32(uint32_t *keys, uint32_t *vals, int64_t n, int bits, SortScratch &sc,

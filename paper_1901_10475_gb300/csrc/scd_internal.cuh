@@ -372,6 +372,14 @@ inline uint32_t open_tag(bool packed, int t_bits) {
 
 // exclusive prefix sum of a[0..n) in place; *total = the sum (one block)
 void scan_u32_exclusive(uint32_t *a, int64_t n, uint32_t *total, cudaStream_t st);
+// One stable scatter pass of the keys kin[0, n) by their 8-bit digit at
+// `shift` into kout, every digit's range starting at an even position (an
+// odd range is followed by one hole key, all ones), so that every run of
+// whole digits starts 16-byte aligned; kout holds n + 256 keys.  h_totals
+// (host, 256 entries) receives each digit's key count (the call waits for
+// the stream).
+int radix_partition_u64(const unsigned long long *kin, unsigned long long *kout, int64_t n,
+                        int shift, SortScratch &sc, uint32_t *h_totals, cudaStream_t st);
 
 // process-wide count of kernel launches issued by this library
 void note_launch(int k = 1);
@@ -384,6 +392,10 @@ int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, DevBuf<int64_
 }  // namespace scd
 
 // the scene (opaque in the ABI)
+namespace scd {
+constexpr int kStreamBuckets = 8;  // buckets of a canonical list streamed to the host
+}
+
 struct scd_scene {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -456,6 +468,14 @@ struct scd_scene {
   // be captured)
   cudaStream_t gstream = nullptr;
   cudaEvent_t g_in = nullptr, g_out = nullptr;
+  // a find into host memory: the destination, its room, and whether the
+  // canonical list was streamed into it (buckets copied on cstream)
+  scd_pair *host_dst = nullptr;
+  int64_t host_cap = 0;
+  bool host_done = false;
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t cev[scd::kStreamBuckets] = {};
+  scd::DevBuf<unsigned long long> d_part, d_parte;  // the records split by their top digit
   int64_t graph_key[8] = {};
   int64_t graph_M = 0;
   scd::DevBuf<uint32_t> s_leafkey32;
@@ -527,4 +547,8 @@ int traverse_round(const QBox *qbox, const uint32_t *qlink, const SBox *sbox,
 int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits);
 // canonical list with every count read on the device (graph capture)
 int canonicalize_dev(scd_scene *s, int obj_bits, int t_bits);
+// canonical list streamed into host memory bucket by bucket (run starts
+// packed with their last tick); SCD_ERR_STATE when the records do not allow
+// it; the copies are left running on the scene's copy stream
+int canonicalize_streamed(scd_scene *s, int obj_bits, int t_bits, scd_pair *host);
 }  // namespace scd

@@ -421,10 +421,17 @@ static int find_eager(scd_scene *s, const scd_decomp *d, int dkind, int raw_mode
   if (s->h_ctr.build_flags & ERR_INVALID) return SCD_ERR_INVALID_ARG;
   if (s->h_ctr.build_flags & ERR_KEPLER) return SCD_ERR_KEPLER_NOCONV;
   if (s->events_ready) cudaEventRecord(s->ev[5], st);
-  // A9: canonical list
-  TRY(canonicalize(s, raw_mode, ob, tb));
+  // A9: canonical list (into host memory: streamed out bucket by bucket)
+  s->host_done = false;
+  int crc = SCD_ERR_STATE;
+  if (s->host_dst && !raw_mode && (int64_t)s->h_ctr.v_starts <= s->host_cap)
+    crc = canonicalize_streamed(s, ob, tb, s->host_dst);
+  if (crc == SCD_OK) s->host_done = true;
+  else if (crc != SCD_ERR_STATE) return crc;
+  else TRY(canonicalize(s, raw_mode, ob, tb));
   if (s->events_ready) cudaEventRecord(s->ev[6], st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return SCD_ERR_CUDA;
+  if (s->host_done && cudaStreamSynchronize(s->cstream) != cudaSuccess) return SCD_ERR_CUDA;
   unsigned int flags[2] = {0, 0};
   cudaMemcpy(&flags[0], &s->d_ctr.p->trav_flags, sizeof(unsigned int), cudaMemcpyDeviceToHost);
   cudaMemcpy(&flags[1], &s->d_ctr.p->sort_flags, sizeof(unsigned int), cudaMemcpyDeviceToHost);
@@ -574,10 +581,18 @@ extern "C" SCD_API int scd_find_raw_cells_device(scd_scene *s, const scd_pair **
 extern "C" SCD_API int scd_find_pairs(scd_scene *s, const scd_decomp *d, scd_pair *host_out,
                                       int64_t cap, int64_t *n_out) {
   if (!n_out || (cap > 0 && !host_out) || cap < 0) return SCD_ERR_INVALID_ARG;
-  TRY(find_pairs_impl(s, d, 0));
+  s->host_dst = host_out;
+  s->host_cap = cap;
+  s->host_done = false;
+  int rc = find_pairs_impl(s, d, 0);
+  const bool streamed = s->host_done;
+  s->host_dst = nullptr;
+  s->host_cap = 0;
+  s->host_done = false;
+  TRY(rc);
   *n_out = s->n_out;
   if (s->n_out > cap) return SCD_ERR_BUFFER_TOO_SMALL;
-  if (s->n_out > 0) {
+  if (s->n_out > 0 && !streamed) {
     if (cudaMemcpyAsync(host_out, s->d_out.p, sizeof(scd_pair) * (size_t)s->n_out,
                         cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
       return SCD_ERR_CUDA;
@@ -757,12 +772,19 @@ extern "C" SCD_API void scd_scene_destroy(scd_scene *s) {
   s->d_feat.release(st); s->d_ny.release(st); s->d_learned.release(st);
   s->d_objT.release(st); s->d_objscene.release(st); s->d_sceneoff.release(st);
   s->d_pairoff.release(st);
+  s->d_part.release(st); s->d_parte.release(st);
   if (s->events_ready)
     for (int k = 0; k < 8; ++k) cudaEventDestroy(s->ev[k]);
   if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
   if (s->gstream) cudaStreamDestroy(s->gstream);
   if (s->g_in) cudaEventDestroy(s->g_in);
   if (s->g_out) cudaEventDestroy(s->g_out);
+  if (s->cstream) {
+    cudaStreamSynchronize(s->cstream);
+    cudaStreamDestroy(s->cstream);
+  }
+  for (int b = 0; b < scd::kStreamBuckets; ++b)
+    if (s->cev[b]) cudaEventDestroy(s->cev[b]);
   if (s->h_ctr_pinned) cudaFreeHost(s->h_ctr_pinned);
   delete s;
 }

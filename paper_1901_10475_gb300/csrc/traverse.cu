@@ -977,6 +977,96 @@ int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits) {
   return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
 }
 
+// The canonical list for a host destination, in buckets of the pair's
+// first object that go to the host while the next ones are sorted: one
+// stable pass over the top digit of the starts' and the ends' keys (the top
+// bits of i) splits both into digit ranges (starting 16-byte aligned); runs
+// of whole digits with about equal numbers of starts form the buckets, and
+// each bucket is sorted by the whole key, unpacked into its place in the
+// output and copied out on a second stream.  A pair's starts and ends share
+// their i, so each bucket zips its own open starts with its own ends.  The
+// output equals canonicalize's; one more pass over the records, hidden
+// under the copies.
+#define TRY_(x)                   \
+  do {                            \
+    int rc_ = (x);                \
+    if (rc_ != SCD_OK) return rc_; \
+  } while (0)
+
+int canonicalize_streamed(scd_scene *s, int obj_bits, int t_bits, scd_pair *host) {
+  cudaStream_t st = s->stream;
+  UnpackArgs a = unpack_args(s, 0, obj_bits, t_bits);
+  const int lo = t_bits, bits = 2 * obj_bits + t_bits;
+  // the top digit must lie inside the (i, j) fields, so that a pair's open
+  // start and its end (different ticks) fall into the same bucket
+  if (!a.packed || 2 * obj_bits < 8) return SCD_ERR_STATE;
+  const int64_t ns = (int64_t)s->h_ctr.n_starts, n = (int64_t)s->h_ctr.v_starts;
+  const int64_t nes = (int64_t)s->h_ctr.n_ends, ne = (int64_t)s->h_ctr.v_ends;
+  if (!s->d_out.ensure(n > 0 ? n : 1, st) || !s->d_part.ensure(ns + 256, st) ||
+      !s->d_parte.ensure(nes + 256, st))
+    return SCD_ERR_OOM;
+  if (!s->cstream) {
+    if (cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess)
+      return SCD_ERR_CUDA;
+    for (int b = 0; b < kStreamBuckets; ++b)
+      if (cudaEventCreateWithFlags(&s->cev[b], cudaEventDisableTiming) != cudaSuccess)
+        return SCD_ERR_CUDA;
+  }
+  uint32_t ts[256], te[256];
+  TRY_(radix_partition_u64(s->d_starts.p, s->d_part.p, ns, lo + bits - 8, s->sort_sc, ts, st));
+  TRY_(radix_partition_u64(s->d_ends.p, s->d_parte.p, nes, bits - 8, s->sort_sc, te, st));
+  // digit d's range starts at ps[d] (pe[d]); its records: the keys of the
+  // digit, except that the all-ones digit also holds the holes
+  int64_t ps[257], pe[257], vs[256], ve[256], sum_s = 0, sum_e = 0;
+  ps[0] = pe[0] = 0;
+  for (int d = 0; d < 256; ++d) {
+    ps[d + 1] = ps[d] + ((ts[d] + 1) & ~1u);
+    pe[d + 1] = pe[d] + ((te[d] + 1) & ~1u);
+    vs[d] = d < 255 ? ts[d] : n - sum_s;
+    ve[d] = d < 255 ? te[d] : ne - sum_e;
+    sum_s += vs[d];
+    sum_e += ve[d];
+  }
+  if (vs[255] < 0 || ve[255] < 0 || sum_s != n || sum_e != ne) return SCD_ERR_INTERNAL;
+  int64_t out_at = 0;
+  int d0 = 0;
+  for (int b = 0; b < kStreamBuckets && d0 < 256; ++b) {
+    // whole digits up to about an equal share of the starts still left
+    const int64_t share = (n - out_at + (kStreamBuckets - b) - 1) / (kStreamBuckets - b);
+    int d1 = d0;
+    int64_t m = 0, me = 0;
+    while (d1 < 256 && (m < share || b == kStreamBuckets - 1)) {
+      m += vs[d1];
+      me += ve[d1];
+      ++d1;
+    }
+    const int64_t slots = ps[d1] - ps[d0], eslots = pe[d1] - pe[d0];
+    unsigned long long *ks = s->d_part.p + ps[d0], *ke = s->d_parte.p + pe[d0];
+    TRY_(radix_sort_u64(ks, nullptr, slots, lo, bits + lo, s->sort_sc, st));
+    if (me > 0) TRY_(radix_sort_u64(ke, nullptr, eslots, bits, s->sort_sc, st));
+    UnpackArgs u = a;
+    u.starts = ks;
+    u.ends = ke;
+    u.n = m;
+    u.n_ends = (unsigned long long)me;
+    u.out = s->d_out.p + out_at;
+    TRY_(unpack(s, u, st));
+    if (m > 0) {
+      if (cudaEventRecord(s->cev[b], st) != cudaSuccess ||
+          cudaStreamWaitEvent(s->cstream, s->cev[b], 0) != cudaSuccess ||
+          cudaMemcpyAsync(host + out_at, s->d_out.p + out_at, sizeof(scd_pair) * (size_t)m,
+                          cudaMemcpyDeviceToHost, s->cstream) != cudaSuccess)
+        return SCD_ERR_CUDA;
+    }
+    out_at += m;
+    d0 = d1;
+  }
+  if (out_at != n) return SCD_ERR_INTERNAL;
+  s->n_out = n;
+  return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
+}
+#undef TRY_
+
 int canonicalize_dev(scd_scene *s, int obj_bits, int t_bits) {
   cudaStream_t st = s->stream;
   const int64_t cap = s->pair_cap;
