@@ -243,6 +243,43 @@ __device__ __forceinline__ QBox qbox_union(const QBox &a, const QBox &b) {
 // quantisation is monotone per coordinate, so that union equals the
 // quantised union of the exact boxes, bit for bit, at half the bytes per
 // node (16 instead of 32).
+// One compact node's work in the refit: both children's quantised boxes
+// into the node's pair, the split with the leaf flags, and the union as the
+// node's own box for its parent.
+__device__ __forceinline__ void refit_q_node(const SBox *__restrict__ sbox, const QFrame &fr,
+                                             int32_t p, const int4 &lk, QBox *__restrict__ nq,
+                                             QBox *__restrict__ qbox,
+                                             uint32_t *__restrict__ qlink) {
+  auto child = [&](int32_t link) {
+    if (link & kLeafBit) {
+      const int32_t q = link & ~kLeafBit;
+      return quantize_box(fr, __ldcg(&sbox[q].lo), __ldcg(&sbox[q].hi));
+    }
+    const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(nq + link));
+    return QBox{v.x, v.y, v.z, v.w};
+  };
+  const QBox ql = child(lk.x), qr = child(lk.y);
+  qbox[2 * p] = ql;
+  qbox[2 * p + 1] = qr;
+  const uint32_t g = (uint32_t)lk.z;  // the split: left child gamma, right gamma + 1
+  const uint32_t fl =
+      ((lk.x & kLeafBit) ? kQLeftLeaf : 0u) | ((lk.y & kLeafBit) ? kQRightLeaf : 0u);
+  qlink[p] = g | fl;
+  const QBox u = qbox_union(ql, qr);
+  __stcg(reinterpret_cast<uint4 *>(nq + p), make_uint4(u.lo_xy, u.lo_zt, u.hi_xy, u.hi_zt));
+}
+
+// the arrival at node p: true for the second thread to arrive, which then
+// sees its sibling's writes (acquire) after releasing its own
+__device__ __forceinline__ bool arrive_gpu(uint32_t *flags, int32_t p) {
+  uint32_t arrived;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+               : "=r"(arrived)
+               : "l"(flags + p)
+               : "memory");
+  return arrived != 0u;
+}
+
 __global__ void k_refit_q(const SBox *__restrict__ sbox, int64_t M,
                           const TravNode *__restrict__ nodes, QBox *__restrict__ nq,
                           const int32_t *__restrict__ parent_int,
@@ -254,36 +291,58 @@ __global__ void k_refit_q(const SBox *__restrict__ sbox, int64_t M,
   int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= M || M == 1) return;
   const QFrame fr = scene_frame(ctr, T);
-  auto child = [&](int32_t link) {
-    if (link & kLeafBit) {
-      const int32_t q = link & ~kLeafBit;
-      return quantize_box(fr, __ldcg(&sbox[q].lo), __ldcg(&sbox[q].hi));
-    }
-    const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(nq + link));
-    return QBox{v.x, v.y, v.z, v.w};
-  };
   int32_t p = parent_leaf[c];
   while (p >= 0) {
-    // release this thread's node box, acquire the sibling's (the second
-    // thread to arrive reads both)
-    uint32_t arrived;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
-                 : "=r"(arrived)
-                 : "l"(flags + p)
-                 : "memory");
-    if (arrived == 0u) return;
+    if (!arrive_gpu(flags, p)) return;
     const int4 lk = __ldcg(reinterpret_cast<const int4 *>(nodes + p) + 4);
-    const QBox ql = child(lk.x), qr = child(lk.y);
-    qbox[2 * p] = ql;
-    qbox[2 * p + 1] = qr;
-    const uint32_t g = (uint32_t)lk.z;  // the split: left child gamma, right gamma + 1
-    const uint32_t fl =
-        ((lk.x & kLeafBit) ? kQLeftLeaf : 0u) | ((lk.y & kLeafBit) ? kQRightLeaf : 0u);
-    qlink[p] = g | fl;
-    const QBox u = qbox_union(ql, qr);
-    __stcg(reinterpret_cast<uint4 *>(nq + p), make_uint4(u.lo_xy, u.lo_zt, u.hi_xy, u.hi_zt));
+    refit_q_node(sbox, fr, p, lk, nq, qbox, qlink);
     const int32_t up = parent_int[p];
     p = up >= 0 ? (up & ~kRightChildBit) : -1;
+  }
+}
+
+// The same refit with the lower levels kept inside a block: block b takes
+// the kRqChunk leaves [c0, c1) and, for the nodes whose leaf range lies
+// inside them (the node's index lies there too: it is one end of its
+// range), counts arrivals in shared memory and orders the two threads'
+// writes with block-scope fences.  Only the nodes whose range crosses a
+// chunk boundary (a few per cent) take the device-scope atomics.  The
+// block-scope message passing and the device-scope one compose (fences are
+// cumulative), so a node's union reaches whichever block completes its
+// parent.
+constexpr int kRqThreads = 256, kRqChunk = 8 * kRqThreads;
+__global__ void __launch_bounds__(kRqThreads) k_refit_q_local(
+    const SBox *__restrict__ sbox, int64_t M, const TravNode *__restrict__ nodes,
+    const int32_t *__restrict__ nfirst, QBox *__restrict__ nq,
+    const int32_t *__restrict__ parent_int, const int32_t *__restrict__ parent_leaf,
+    uint32_t *__restrict__ flags, QBox *__restrict__ qbox, uint32_t *__restrict__ qlink,
+    const DevCounters *__restrict__ ctr, int64_t T) {
+  __shared__ uint32_t arr[kRqChunk];  // arrivals at the block's own nodes, by index - c0
+  for (int i = threadIdx.x; i < kRqChunk; i += kRqThreads) arr[i] = 0u;
+  __syncthreads();
+  if (M == 1) return;
+  const int64_t c0 = (int64_t)blockIdx.x * kRqChunk;
+  const int64_t c1 = c0 + kRqChunk < M ? c0 + kRqChunk : M;
+  const QFrame fr = scene_frame(ctr, T);
+  for (int k = 0; k < kRqChunk / kRqThreads; ++k) {
+    const int64_t c = c0 + (int64_t)k * kRqThreads + threadIdx.x;
+    if (c >= c1) break;
+    int32_t p = parent_leaf[c];
+    while (p >= 0) {
+      const int4 lk = __ldcg(reinterpret_cast<const int4 *>(nodes + p) + 4);
+      const bool local = nfirst[p] >= c0 && (int64_t)lk.w < c1;
+      if (local) {
+        __threadfence_block();
+        const bool second = atomicAdd(&arr[p - c0], 1u) != 0u;
+        if (!second) break;
+        __threadfence_block();
+      } else if (!arrive_gpu(flags, p)) {
+        break;
+      }
+      refit_q_node(sbox, fr, p, lk, nq, qbox, qlink);
+      const int32_t up = parent_int[p];
+      p = up >= 0 ? (up & ~kRightChildBit) : -1;
+    }
   }
 }
 
@@ -320,17 +379,21 @@ int build_tree(scd_scene *s, const K *keys_sorted, const uint32_t *ids_sorted, i
                                                                s->d_posof.p, Nq, s->N, s->s_nb.p);
     note_launch();
   }
+  // the nodes' first leaves: the cells' roots, and the block-local refit
+  const bool want_first = cells || (compact && !wide);
+  if (want_first && !s->d_first.ensure(M > 1 ? M - 1 : 1, st)) return SCD_ERR_OOM;
   if (M > 1) {
     k_karras<K><<<(unsigned)((M - 1 + bs - 1) / bs), bs, 0, st>>>(
         leafkey, M, s->d_nodes.p, s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p,
-        cells ? s->d_first.p : nullptr);
+        want_first ? s->d_first.p : nullptr);
     note_launch();
   }
   static_assert(sizeof(QBox) == sizeof(float4), "the quantised node boxes use the float ones' buffer");
   if (compact && !wide) {
-    k_refit_q<<<(unsigned)((M + bs - 1) / bs), bs, 0, st>>>(
-        s->s_box.p, M, s->d_nodes.p, reinterpret_cast<QBox *>(s->d_nlo.p), s->d_parent_int.p,
-        s->d_parent_leaf.p, s->d_flags.p, s->d_qbox.p, s->d_qlink.p, s->d_ctr.p, s->T);
+    k_refit_q_local<<<(unsigned)((M + kRqChunk - 1) / kRqChunk), kRqThreads, 0, st>>>(
+        s->s_box.p, M, s->d_nodes.p, s->d_first.p, reinterpret_cast<QBox *>(s->d_nlo.p),
+        s->d_parent_int.p, s->d_parent_leaf.p, s->d_flags.p, s->d_qbox.p, s->d_qlink.p,
+        s->d_ctr.p, s->T);
   } else {
     (wide ? k_refit<true> : k_refit<false>)<<<(unsigned)((M + bs - 1) / bs), bs, 0, st>>>(
         s->s_box.p, Nq, L, M, s->d_leaflo.p, s->d_leafhi.p, s->d_nodes.p, s->d_nlo.p,

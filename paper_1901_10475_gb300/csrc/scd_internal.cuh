@@ -393,7 +393,7 @@ int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, DevBuf<int64_
 
 // the scene (opaque in the ABI)
 namespace scd {
-constexpr int kStreamBuckets = 8;  // buckets of a canonical list streamed to the host
+constexpr int kStreamBuckets = 16;  // buckets of a canonical list streamed to the host
 }
 
 struct scd_scene {
