@@ -32,33 +32,50 @@ __device__ __forceinline__ int64_t sort_count(int64_t n, const unsigned long lon
   return v < (unsigned long long)n ? (int64_t)v : n;
 }
 
-template <class K>
+// kOpen: also count, per digit, the keys whose low tmask bits are all ones
+// (open run starts; holes too, which sort last) into ocounts
+template <class K, bool kOpen = false>
 __global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const K *__restrict__ keys, int64_t n,
                                                            const unsigned long long *__restrict__ d_n,
                                                            int shift, uint32_t *__restrict__ counts,
-                                                           int64_t nblk) {
+                                                           int64_t nblk,
+                                                           uint32_t *__restrict__ ocounts = nullptr,
+                                                           unsigned long long tmask = 0) {
   n = sort_count(n, d_n);
   __shared__ uint32_t wh[kRsWarps][256];
+  __shared__ uint32_t wo[kOpen ? kRsWarps : 1][256];
   int w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&wh[0][0])[i] = 0;
+  if (kOpen)
+    for (int i = threadIdx.x; i < kRsWarps * 256; i += kRsThreads) (&wo[0][0])[i] = 0;
   __syncthreads();
   int64_t base = (int64_t)blockIdx.x * kRsTile;
   // all loads first, so that every item's load is in flight together
   uint32_t dig[kRsItems];
+  bool op[kRsItems];
 #pragma unroll
   for (int k = 0; k < kRsItems; ++k) {
     int64_t idx = base + (int64_t)k * kRsThreads + threadIdx.x;
-    dig[k] = idx < n ? digit_of(keys[idx], shift) : 256u;
+    const K key = idx < n ? keys[idx] : (K)0;
+    dig[k] = idx < n ? digit_of(key, shift) : 256u;
+    op[k] = kOpen && ((unsigned long long)key & tmask) == tmask;
   }
 #pragma unroll
   for (int k = 0; k < kRsItems; ++k)
-    if (dig[k] < 256u) atomicAdd(&wh[w][dig[k]], 1u);
+    if (dig[k] < 256u) {
+      atomicAdd(&wh[w][dig[k]], 1u);
+      if (kOpen && op[k]) atomicAdd(&wo[w][dig[k]], 1u);
+    }
   __syncthreads();
   for (int d = threadIdx.x; d < 256; d += kRsThreads) {
-    uint32_t s = 0;
+    uint32_t s = 0, o = 0;
 #pragma unroll
-    for (int q = 0; q < kRsWarps; ++q) s += wh[q][d];
+    for (int q = 0; q < kRsWarps; ++q) {
+      s += wh[q][d];
+      if (kOpen) o += wo[q][d];
+    }
     counts[(int64_t)d * nblk + blockIdx.x] = s;
+    if (kOpen) ocounts[(int64_t)d * nblk + blockIdx.x] = o;
   }
 }
 
@@ -181,12 +198,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // read with plain loads.  Items of a tile are warp-striped: warp w holds
 // tile items [w*32*I, (w+1)*32*I), item k of lane l at w*32*I + k*32 + l,
 // so (k, lane) order is input order and ranks are stable.
-template <class K, bool kVals>
+// kPairs (the last pass of the packed run starts' sort): instead of the
+// keys, the decoded pairs of the records go to their sorted positions, each
+// open start with the last tick of the end whose rank among the ends equals
+// its own rank among the open starts (from the open counts per digit and
+// tile, ocounts / ototals, and an in-tile prefix).
+template <class K, bool kVals, bool kPairs = false>
 __global__ void __launch_bounds__(kRsThreads, 4) k_rs_downsweep(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t n, const unsigned long long *__restrict__ d_n, int shift,
     const uint32_t *__restrict__ counts, const uint32_t *__restrict__ totals, int64_t nblk,
-    unsigned int *err, int even = 0) {
+    unsigned int *err, int even = 0, const uint32_t *__restrict__ ocounts = nullptr,
+    const uint32_t *__restrict__ ototals = nullptr, PairEmit pe = PairEmit{}) {
   n = sort_count(n, d_n);
   const int64_t ntiles = (n + kRsTile - 1) / kRsTile;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -200,6 +223,10 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_downsweep(
   __shared__ uint32_t gdig[256];   // first global position of each digit
   __shared__ uint32_t gbase[256];  // global position of the tile's first item of each digit,
                                    // less the digit's first tile position (mod 2^32)
+  // kPairs: open starts before the digit's first open start (ordered), and
+  // the open starts of the tile's staged items before each digit's run
+  __shared__ uint32_t odig[kPairs ? 256 : 1], obase[kPairs ? 256 : 1];
+  __shared__ uint16_t opre[kPairs ? kRsTile : 1];  // open starts before each staged item
 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -215,6 +242,11 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_downsweep(
 
   // (even: every digit's range rounded up to an even length)
   gdig[d] = digit_scan_excl(even ? (totals[d] + 1u) & ~1u : totals[d], scanbuf);
+  if constexpr (kPairs) odig[d] = digit_scan_excl(ototals[d], scanbuf);
+  const unsigned long long tmask = kPairs ? (1ull << pe.tb) - 1ull : 0ull;
+  const int64_t nvalid = kPairs ? sort_count(pe.n, pe.d_n) : 0;
+  const unsigned long long n_ends =
+      kPairs ? (pe.d_ne && *pe.d_ne < pe.n_ends ? *pe.d_ne : pe.n_ends) : 0ull;
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -235,6 +267,7 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_downsweep(
     uint32_t *vb = b ? vbuf1 : vbuf0;
     for (int i = lane; i < 256; i += 32) wcnt[w][i] = 0;
     gbase[d] = gdig[d] + counts[(int64_t)d * nblk + tile];
+    if constexpr (kPairs) obase[d] = odig[d] + ocounts[(int64_t)d * nblk + tile];
     bool ok = true;
     if (full) {
       ok = mbar_wait(&bar[b], b ? parity1 : parity0);
@@ -314,12 +347,62 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_downsweep(
 
     // (e) each digit's run goes to consecutive global positions
     const int cnt = n - base < kRsTile ? (int)(n - base) : kRsTile;
-    for (int r = threadIdx.x; r < cnt; r += kRsThreads) {
-      K kk = kb[r];
-      uint32_t dg = digit_of(kk, shift);
-      uint32_t pos = gbase[dg] + (uint32_t)r;
-      kout[pos] = kk;
-      if (kVals) vout[pos] = vb[r];
+    if constexpr (kPairs) {
+      // the open starts before every staged item: per thread over kRsItems
+      // consecutive items, then across the threads
+      const int r0 = threadIdx.x * kRsItems;
+      uint32_t mine = 0;
+#pragma unroll
+      for (int k = 0; k < kRsItems; ++k)
+        if (r0 + k < cnt) mine += ((unsigned long long)kb[r0 + k] & tmask) == tmask;
+      uint32_t run = digit_scan_excl(mine, scanbuf);
+#pragma unroll
+      for (int k = 0; k < kRsItems; ++k)
+        if (r0 + k < cnt) {
+          opre[r0 + k] = (uint16_t)run;
+          run += ((unsigned long long)kb[r0 + k] & tmask) == tmask;
+        }
+      __syncthreads();
+      // then the pairs, warp-contiguous as the keys would be
+      bool bad = false;
+      const unsigned long long omask = (1ull << pe.ob) - 1ull;
+      for (int r = threadIdx.x; r < cnt; r += kRsThreads) {
+        const unsigned long long kk = (unsigned long long)kb[r];
+        const uint32_t dg = digit_of((K)kk, shift);
+        const int64_t pos = (int64_t)(uint32_t)(gbase[dg] + (uint32_t)r);
+        if (pos >= nvalid) continue;
+        const bool open = (kk & tmask) == tmask;
+        // open starts before this one in the final order
+        const unsigned long long rank =
+            (unsigned long long)obase[dg] + (uint32_t)(opre[r] - opre[wcnt[0][dg]]);
+        const unsigned long long key = kk >> pe.tb;  // (i, j, first tick)
+        scd_pair q;
+        q.i = (uint32_t)(key >> (pe.ob + pe.tb));
+        q.j = (uint32_t)((key >> pe.tb) & omask);
+        q.tlo = (int32_t)(key & tmask);
+        q.thi = (int32_t)(kk & tmask);
+        if (open) {
+          if (rank < n_ends) {
+            const unsigned long long ek = __ldg(pe.ends + rank);
+            q.thi = (int32_t)(ek & tmask);
+            bad |= (ek >> pe.tb) != (key >> pe.tb) || q.thi <= q.tlo;
+          } else {
+            bad = true;
+          }
+        }
+        pe.out[pos] = q;
+        // the last record: every end taken by exactly one open start
+        if (pos == nvalid - 1 && rank + (open ? 1u : 0u) != n_ends) bad = true;
+      }
+      if (bad) atomicOr(pe.flags, (unsigned)ERR_ZIP);
+    } else {
+      for (int r = threadIdx.x; r < cnt; r += kRsThreads) {
+        K kk = kb[r];
+        uint32_t dg = digit_of(kk, shift);
+        uint32_t pos = gbase[dg] + (uint32_t)r;
+        kout[pos] = kk;
+        if (kVals) vout[pos] = vb[r];
+      }
     }
     __syncthreads();  // the buffer is read out: the copy of the tile after next may land
     if (threadIdx.x == 0) {
@@ -331,8 +414,9 @@ __global__ void __launch_bounds__(kRsThreads, 4) k_rs_downsweep(
 
 template <class K>
 static int rs_impl(K *keys, uint32_t *vals, int64_t n, const unsigned long long *d_n, int lo,
-                   int bits, SortScratch &sc, cudaStream_t st) {
-  if (n <= 1 || bits <= lo) return SCD_OK;
+                   int bits, SortScratch &sc, cudaStream_t st, const PairEmit *pe = nullptr) {
+  if (!pe && (n <= 1 || bits <= lo)) return SCD_OK;
+  if (pe && (n < 1 || bits <= lo || vals || sizeof(K) != 8)) return SCD_ERR_INTERNAL;
   if (n >= (1ll << 32) - 1) return SCD_ERR_CAPACITY;  // positions are 32-bit
   // tiles are copied whole into shared memory: 16-byte aligned arrays
   if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(vals)) & 15)
@@ -368,8 +452,33 @@ static int rs_impl(K *keys, uint32_t *vals, int64_t n, const unsigned long long 
     grid_of[ki][vi] = std::max(1, sms) * std::max(1, per_sm);
   }
   const unsigned grid = (unsigned)std::min<int64_t>(nblk, grid_of[ki][vi]);
+  uint32_t *ocounts = nullptr, *ototals = nullptr;
+  if (pe) {
+    if (!sc.ocounts.ensure((size_t)(256 * nblk + 256), st)) return SCD_ERR_OOM;
+    ocounts = sc.ocounts.p;
+    ototals = sc.ocounts.p + 256 * nblk;
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_rs_downsweep<unsigned long long, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+  }
   int passes = 0;
   for (int shift = lo; shift < bits; shift += 8, ++passes) {
+    if (pe && shift + 8 >= bits) {
+      // the last pass: decoded pairs to their sorted positions
+      const unsigned long long tmask = (1ull << pe->tb) - 1ull;
+      k_rs_upsweep<unsigned long long, true><<<(unsigned)nblk, kRsThreads, 0, st>>>(
+          (const unsigned long long *)ka, n, d_n, shift, counts, nblk, ocounts, tmask);
+      k_rs_scan<<<256, 1024, 0, st>>>(counts, nblk, totals);
+      k_rs_scan<<<256, 1024, 0, st>>>(ocounts, nblk, ototals);
+      k_rs_downsweep<unsigned long long, false, true><<<grid, kRsThreads, smem, st>>>(
+          (const unsigned long long *)ka, nullptr, nullptr, nullptr, n, d_n, shift, counts,
+          totals, nblk, sc.err, 0, ocounts, ototals, *pe);
+      note_launch(4);
+      return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
+    }
     k_rs_upsweep<K><<<(unsigned)nblk, kRsThreads, 0, st>>>(ka, n, d_n, shift, counts, nblk);
     k_rs_scan<<<256, 1024, 0, st>>>(counts, nblk, totals);
     if (vals)
@@ -460,6 +569,11 @@ int sort_reserve(SortScratch &sc, int64_t n, size_t key_bytes, bool vals, cudaSt
   if (vals && !sc.vals_alt.ensure((size_t)n, st)) return SCD_ERR_OOM;
   if (!sc.counts.ensure((size_t)(256 * nblk + 256), st)) return SCD_ERR_OOM;
   return SCD_OK;
+}
+
+int radix_sort_u64_pairs(unsigned long long *keys, int64_t n, const unsigned long long *d_n,
+                         int lo, int bits, SortScratch &sc, const PairEmit &pe, cudaStream_t st) {
+  return rs_impl<unsigned long long>(keys, nullptr, n, d_n, lo, bits, sc, st, &pe);
 }
 
 int radix_sort_u64_dev(unsigned long long *keys, uint32_t *vals, int64_t n_cap,

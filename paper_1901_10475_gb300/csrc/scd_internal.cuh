@@ -333,12 +333,29 @@ struct SortScratch {
   DevBuf<unsigned char> keys_alt;
   DevBuf<uint32_t> vals_alt;
   DevBuf<uint32_t> counts;
+  DevBuf<uint32_t> ocounts;  // open run starts per digit and tile (last pass into pairs)
   unsigned int *err = nullptr;  // device word that receives ERR_SORT (may be null)
   void release(cudaStream_t st) {
     keys_alt.release(st);
     vals_alt.release(st);
     counts.release(st);
+    ocounts.release(st);
   }
+};
+
+// The last pass of the run starts' sort written straight out as pairs: the
+// start keys (i, j, first tick) carry the run's last tick in their low tb
+// bits, all ones for an open run, whose last tick is that of the k-th
+// sorted end for the k-th open start (k counted in the final order).
+struct PairEmit {
+  int ob, tb;
+  const unsigned long long *ends;     // the sorted ends of the open runs
+  unsigned long long n_ends;          // their count (a capacity when d_ne is set)
+  const unsigned long long *d_ne;
+  scd_pair *out;
+  int64_t n;                          // starts that are records (the rest are holes)
+  const unsigned long long *d_n;
+  unsigned int *flags;                // receives ERR_ZIP
 };
 
 // Sort (key, value) pairs by the low `bits` bits of the key, LSD, 8-bit
@@ -355,6 +372,13 @@ int radix_sort_u64(unsigned long long *keys, uint32_t *vals, int64_t n, int lo, 
 int sort_reserve(SortScratch &sc, int64_t n, size_t key_bytes, bool vals, cudaStream_t st);
 // the same with the element count read on the device (min(*d_n, n_cap)), for
 // sorts inside a captured graph; grids are sized for n_cap
+// Sort the packed run starts keys[0, n) (a capacity with d_n) by bits
+// [lo, bits) and write the sorted records as pairs into pe.out: the passes
+// before the last as radix_sort_u64, the last one scattering decoded pairs
+// (each open start zipped with its end) instead of keys.  The keys are left
+// in an unspecified order.
+int radix_sort_u64_pairs(unsigned long long *keys, int64_t n, const unsigned long long *d_n,
+                         int lo, int bits, SortScratch &sc, const PairEmit &pe, cudaStream_t st);
 int radix_sort_u64_dev(unsigned long long *keys, uint32_t *vals, int64_t n_cap,
                        const unsigned long long *d_n, int lo, int bits, SortScratch &sc,
                        cudaStream_t st);

@@ -937,6 +937,22 @@ static UnpackArgs unpack_args(scd_scene *s, int raw_mode, int obj_bits, int t_bi
   return a;
 }
 
+static PairEmit pair_emit(scd_scene *s, int obj_bits, int t_bits, const unsigned long long *ends,
+                          unsigned long long n_ends, const unsigned long long *d_ne,
+                          scd_pair *out, int64_t n, const unsigned long long *d_n) {
+  PairEmit pe;
+  pe.ob = obj_bits;
+  pe.tb = t_bits;
+  pe.ends = ends;
+  pe.n_ends = n_ends;
+  pe.d_ne = d_ne;
+  pe.out = out;
+  pe.n = n;
+  pe.d_n = d_n;
+  pe.flags = &s->d_ctr.p->trav_flags;
+  return pe;
+}
+
 // k_open_count, the prefix over the tiles, k_unpack
 static int unpack(scd_scene *s, UnpackArgs a, cudaStream_t st) {
   int64_t tiles = (a.n + kUpTile - 1) / kUpTile;
@@ -983,7 +999,9 @@ int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits) {
 // bits of i) splits both into digit ranges (starting 16-byte aligned); runs
 // of whole digits with about equal numbers of starts form the buckets, and
 // each bucket is sorted by the whole key, unpacked into its place in the
-// output and copied out on a second stream.  A pair's starts and ends share
+// output and copied out on a second stream (the bucket's last sort pass
+// writes the pairs themselves: no unpack pass per bucket; for the whole
+// list on the device the separate unpack measured faster).  A pair's starts and ends share
 // their i, so each bucket zips its own open starts with its own ends.  The
 // output equals canonicalize's; one more pass over the records, hidden
 // under the copies.
@@ -1042,15 +1060,15 @@ int canonicalize_streamed(scd_scene *s, int obj_bits, int t_bits, scd_pair *host
     }
     const int64_t slots = ps[d1] - ps[d0], eslots = pe[d1] - pe[d0];
     unsigned long long *ks = s->d_part.p + ps[d0], *ke = s->d_parte.p + pe[d0];
-    TRY_(radix_sort_u64(ks, nullptr, slots, lo, bits + lo, s->sort_sc, st));
-    if (me > 0) TRY_(radix_sort_u64(ke, nullptr, eslots, bits, s->sort_sc, st));
-    UnpackArgs u = a;
-    u.starts = ks;
-    u.ends = ke;
-    u.n = m;
-    u.n_ends = (unsigned long long)me;
-    u.out = s->d_out.p + out_at;
-    TRY_(unpack(s, u, st));
+    if (m > 0) {
+      if (me > 0) TRY_(radix_sort_u64(ke, nullptr, eslots, bits, s->sort_sc, st));
+      TRY_(radix_sort_u64_pairs(ks, slots, nullptr, lo, bits + lo, s->sort_sc,
+                                pair_emit(s, obj_bits, t_bits, ke, (unsigned long long)me,
+                                          nullptr, s->d_out.p + out_at, m, nullptr),
+                                st));
+    } else if (me > 0) {
+      return SCD_ERR_INTERNAL;  // ends without starts
+    }
     if (m > 0) {
       if (cudaEventRecord(s->cev[b], st) != cudaSuccess ||
           cudaStreamWaitEvent(s->cstream, s->cev[b], 0) != cudaSuccess ||
