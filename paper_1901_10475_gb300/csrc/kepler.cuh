@@ -107,31 +107,39 @@ __device__ __forceinline__ double reduce_2pi(double M) {
 // Kepler's equation, mixed precision: Newton in FP32 to about 3e-7 rad (at
 // most 12 steps: by perigee at e near 1 the FP32 residual cancels and stalls
 // near 1e-5 rad), then FP64 Newton steps.  Each FP64 step squares the error
-// (times |f''/2f'| = e|sin E| / 2(1 - e cos E), at most 1.5 for e <= 0.75),
-// so one step usually suffices: below 2e-13 rad, i.e. below 1e-8 km of
-// position at GEO distance.  Steps continue while the estimated error left
-// exceeds tol (per object, 1e-7 km / a) or the last correction exceeds 1e-5
-// rad; after kFp64Steps without that, iters reports non-convergence.
+// (times |f''/2f'| = e|sin E| / 2(1 - e cos E), at most e / 2(1 - e): 1.5 for
+// e <= 0.75), so one step usually suffices: below 2e-13 rad, i.e. below
+// 1e-8 km of position at GEO distance.  Steps continue while that bound on
+// the error left exceeds a quarter of the object's tolerance (1e-7 km / a),
+// i.e. while the last correction's square exceeds the object's dmax2, or the
+// correction exceeds 1e-5 rad; both compared in FP32 (the test needs no FP64
+// arithmetic); after kFp64Steps without that, iters reports non-convergence.
 // Returns E with sin E and cos E, corrected to second order in the last step
 // (third-order error below 2e-16), so the caller needs no further sincos.
 constexpr int kFp32Steps = 12, kFp64Steps = 8;
 
 // The rare further FP64 steps: take the pending correction d, then step until
 // the test passes; on return (Ed, s, c, d) describe the last step.
-static __device__ __noinline__ void kepler_more_fp64(double M, double e, double tol, double &Ed, double &s,
-                                              double &c, double &d, int &iters) {
+__device__ __forceinline__ bool newton_more(double d, float dmax2) {
+  const float df = (float)d;
+  return df * df > dmax2 || fabsf(df) > 1e-5f;
+}
+
+static __device__ __noinline__ void kepler_more_fp64(double M, double e, float dmax2, double &Ed,
+                                                     double &s, double &c, double &d,
+                                                     int &iters) {
   for (int step = 1; step < kFp64Steps; ++step) {
     Ed -= d;
     sincos_tab(Ed, s, c);
     const double fp = 1.0 - e * c;
     d = div_newton(Ed - e * s - M, fp);
     iters += 1;
-    if (!(2.0 * fabs(e * s) * d * d > tol * fp || fabs(d) > 1e-5)) return;
+    if (!newton_more(d, dmax2)) return;
   }
   iters = kKeplerMaxIter;  // no convergence
 }
 
-__device__ __forceinline__ double kepler_E_sc(double M, double e, double tol, double &sE,
+__device__ __forceinline__ double kepler_E_sc(double M, double e, float dmax2, double &sE,
                                               double &cE, int &iters) {
   if (e == 0.0) {
     sincos_tab(M, sE, cE);
@@ -154,10 +162,7 @@ __device__ __forceinline__ double kepler_E_sc(double M, double e, double tol, do
   double fp = 1.0 - e * c;
   double d = div_newton(Ed - e * s - M, fp);
   iters = it + 1;
-  // error left after this step (with a factor 4 of safety) above tol,
-  // compared without a second FP64 division: 2 |e s| d^2 / fp > tol
-  if (2.0 * fabs(e * s) * d * d > tol * fp || fabs(d) > 1e-5)
-    kepler_more_fp64(M, e, tol, Ed, s, c, d, iters);
+  if (newton_more(d, dmax2)) kepler_more_fp64(M, e, dmax2, Ed, s, c, d, iters);
   // sin(E - d), cos(E - d) to second order in d
   const double h = 0.5 * d * d;
   sE = s - d * c - h * s;
@@ -170,26 +175,41 @@ __device__ __forceinline__ void position_at(const ObjParams &p, double t, double
                                             int &iters) {
   double M = reduce_2pi(p.M0 + p.n * t);
   double s, c;
-  kepler_E_sc(M, p.e, p.tolE, s, c, iters);
+  kepler_E_sc(M, p.e, p.dmax2, s, c, iters);
   double ce = c - p.e;
 #pragma unroll
   for (int k = 0; k < 3; ++k) out[k] = fma(p.A[k], ce, p.B[k] * s);
 }
 
-// exact range of cos over [x0, x1] (x1 >= x0) from the end values c0 =
-// cos x0, c1 = cos x1: widened to 1 where a multiple of 2 pi lies inside, to
-// -1 where an odd multiple of pi does
-__device__ __forceinline__ void cos_range(double x0, double x1, double c0, double c1, double &lo,
-                                          double &hi) {
-  lo = fmin(c0, c1);
-  hi = fmax(c0, c1);
+// exact ranges of cos and sin over [x0, x1] (x1 >= x0) from the end values
+// c0 = cos x0, c1 = cos x1, s0 = sin x0, s1 = sin x1: each widened to its
+// extremum wherever a multiple m of a quarter turn lies inside (m = 0 mod 4:
+// cos = 1, 1: sin = 1, 2: cos = -1, 3: sin = -1); the whole range once the
+// interval spans a full turn.  The multiples inside are the integers from
+// ceil(x0 / (pi/2)) to floor(x1 / (pi/2)): six FP64 operations for both
+// ranges, the rest integer work (the multiples are at most four).
+__device__ __forceinline__ void cos_sin_range(double x0, double x1, double c0, double c1,
+                                              double s0, double s1, double &clo, double &chi,
+                                              double &slo, double &shi) {
+  clo = fmin(c0, c1);
+  chi = fmax(c0, c1);
+  slo = fmin(s0, s1);
+  shi = fmax(s0, s1);
   if (x1 - x0 >= kTwoPi) {
-    lo = -1.0;
-    hi = 1.0;
+    clo = slo = -1.0;
+    chi = shi = 1.0;
     return;
   }
-  if (ceil(x0 * (1.0 / kTwoPi)) * kTwoPi <= x1) hi = 1.0;
-  if (ceil((x0 - kPi) * (1.0 / kTwoPi)) * kTwoPi + kPi <= x1) lo = -1.0;
+  constexpr double kQuarter = 2.0 / kPi;
+  const long long m0 = (long long)ceil(x0 * kQuarter), m1 = (long long)floor(x1 * kQuarter);
+  for (long long m = m0; m <= m1; ++m) {
+    switch ((int)(m & 3)) {
+      case 0: chi = 1.0; break;
+      case 1: shi = 1.0; break;
+      case 2: clo = -1.0; break;
+      default: slo = -1.0; break;
+    }
+  }
 }
 
 // The interval occupancy box (Def 7) of one object over the ticks [tlo, thi]
@@ -224,20 +244,21 @@ __device__ __forceinline__ void segment_box(const ObjParams &p, int mode, int64_
   // (E within 1e-7 km / a: far inside the 1e-6 km margin)
   int i0 = 0, i1 = 0;
   double s0, c0, s1, c1;
-  double E0 = kepler_E_sc(Mr0, p.e, p.tolE, s0, c0, i0);
-  double E1 = kepler_E_sc(Mr1, p.e, p.tolE, s1, c1, i1);
+  double E0 = kepler_E_sc(Mr0, p.e, p.dmax2, s0, c0, i0);
+  double E1 = kepler_E_sc(Mr1, p.e, p.dmax2, s1, c1, i1);
   iters = max(i0, i1);
   double clo, chi, slo, shi;
-  cos_range(E0, E1, c0, c1, clo, chi);
-  // sin E = cos(E - pi/2)
-  cos_range(E0 - 0.5 * kPi, E1 - 0.5 * kPi, s0, s1, slo, shi);
-  double w = p.r + kEpsKm;
+  cos_sin_range(E0, E1, c0, c1, s0, s1, clo, chi, slo, shi);
+  const double w = p.r + kEpsKm, cl = clo - p.e, ch = chi - p.e;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    double u0 = p.A[q] * (clo - p.e), u1 = p.A[q] * (chi - p.e);
-    double v0 = p.B[q] * slo, v1 = p.B[q] * shi;
-    lo[q] = fmin(u0, u1) + fmin(v0, v1) - w;
-    hi[q] = fmax(u0, u1) + fmax(v0, v1) + w;
+    // interval products by the coefficient's sign (rounding is monotone, so
+    // these are the two products' minimum and maximum, bit for bit)
+    const bool ap = __double_as_longlong(p.A[q]) >= 0, bp = __double_as_longlong(p.B[q]) >= 0;
+    const double ulo = __dmul_rn(p.A[q], ap ? cl : ch), uhi = __dmul_rn(p.A[q], ap ? ch : cl);
+    const double vlo = __dmul_rn(p.B[q], bp ? slo : shi), vhi = __dmul_rn(p.B[q], bp ? shi : slo);
+    lo[q] = __dsub_rn(__dadd_rn(ulo, vlo), w);
+    hi[q] = __dadd_rn(__dadd_rn(uhi, vhi), w);
   }
 }
 

@@ -42,7 +42,12 @@ struct __align__(16) ObjParams {
   double r;      // radius [km]
   double P;      // period [s]
   double tolE;   // eccentric-anomaly accuracy of the Kepler solve [rad]: 1e-7 km / a
-  double pad;
+  // the largest squared last Newton correction d that leaves the solve within
+  // tolE / 4 for any E: Newton's error after the step, e |sin E| d^2 /
+  // (2 (1 - e cos E)), is at most e d^2 / (2 (1 - e)); so tolE (1 - e) / (2 e)
+  // (infinite for e = 0)
+  float dmax2;
+  float pad;
 };
 
 // Device-side counters of one scene, read back with one copy.  The first
