@@ -14,11 +14,12 @@ namespace scd {
 // FP64 sine and cosine of the eccentric anomaly by table and Taylor series.
 // x = k (2 pi / 256) + r with |r| <= pi / 256; sin x and cos x from the
 // table's sin and cos of k (2 pi / 256) and the Taylor series of sin r (to
-// r^7) and cos r (to r^8), whose truncation errors are below 2e-23.  The
-// table is built at compile time: each entry by the Taylor series of its
-// angle within a quarter turn (16 terms), then turned by whole quarters.
-// Checked on the host against long-double sinl / cosl: table entries within
-// 2.6e-16, sin and cos over [-4, 4] within 4.2e-16.  The argument reduction
+// r^5) and cos r (to r^6), whose truncation errors are below 1e-17 and
+// 1e-20.  The table is built at compile time: each entry by the Taylor
+// series of its angle within a quarter turn (16 terms), then turned by whole
+// quarters.  Checked on the host against long-double sinl / cosl (the same
+// operations, k picked in FP32): table entries within 2.6e-16, sin and cos
+// over [-4, 4] within 3.7e-16.  The argument reduction
 // takes 2 pi as a double-double (its double and the remainder 2.449e-16),
 // each product subtracted with one rounding (fma).  One table load and a
 // dozen FP64 multiply-adds, in place of a general sincos, in the Kepler
@@ -61,35 +62,34 @@ constexpr SinCosTab make_sincos_tab() {
 }
 static __device__ const SinCosTab g_sincos_tab = make_sincos_tab();
 
-__device__ __forceinline__ void sincos_tab(double x, double &s, double &c) {
+// xf: x in FP32 (or any float within a few ulp of it), from which the table
+// step k is picked in FP32: near a half step the two roundings may pick
+// neighbouring k, either of which leaves |r| within half a step and a hair
+__device__ __forceinline__ void sincos_tab(double x, float xf, double &s, double &c) {
   constexpr double kStepHi = kTwoPi / kSinTab;                 // exact: a power-of-2 division
   constexpr double kStepLo = 2.4492935982947064e-16 / kSinTab;  // 2 pi - fl(2 pi), divided
-  const double k = rint(x * (kSinTab / kTwoPi));
+  const float kf = rintf(xf * (float)(kSinTab / kTwoPi));
+  const double k = (double)kf;
   double r = fma(-k, kStepHi, x);
   r = fma(-k, kStepLo, r);
-  const int idx = ((int)k) & (kSinTab - 1);
+  const int idx = ((int)kf) & (kSinTab - 1);
   const double sk = __ldg(&g_sincos_tab.v[2 * idx]), ck = __ldg(&g_sincos_tab.v[2 * idx + 1]);
   const double r2 = r * r;
-  const double sr =
-      r * fma(r2, fma(r2, fma(r2, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), 1.0);
-  const double cr = fma(
-      r2, fma(r2, fma(r2, fma(r2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5), 1.0);
+  // |r| <= pi / 256 (and a hair): the first omitted terms, r^7 / 7! and
+  // r^8 / 8!, are below 1e-17 and 1e-20
+  const double sr = r * fma(r2, fma(r2, 1.0 / 120.0, -1.0 / 6.0), 1.0);
+  const double cr = fma(r2, fma(r2, fma(r2, -1.0 / 720.0, 1.0 / 24.0), -0.5), 1.0);
   s = fma(sk, cr, ck * sr);
   c = fma(ck, cr, -(sk * sr));
 }
 
-// num / den for the Newton step's denominator 1 - e cos E (in [1 - e, 1 + e],
-// e < 1): the single-precision reciprocal estimate of PTX rcp.approx (within
-// 2^-22 with the rounding of den to FP32) refined by one Newton-Raphson step
-// for 1 / den, r <- r + r (1 - den r), which squares its relative error (to
-// about 2^-44).  The quotient is a Newton correction, so an error of 1e-13 of
-// it is far below the solve's tolerance.
-__device__ __forceinline__ double div_newton(double num, double den) {
-  float rf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)den));
-  double r = (double)rf;
-  r = fma(r, fma(-den, r, 1.0), r);
-  return num * r;
+// The Newton correction d = (E - e sin E - M) / (1 - e cos E): the residual
+// in FP64 (it cancels), the quotient in FP32 (d is a correction of at most
+// 1e-5 rad, so its relative error of 1e-7 leaves E within 1e-12 rad)
+__device__ __forceinline__ float newton_step(double Ed, double s, double c, double M, double e) {
+  const double f = fma(-e, s, Ed - M);
+  const double fp = fma(-e, c, 1.0);
+  return (float)f / (float)fp;
 }
 
 // ---------------------------------------------------------------------------
@@ -120,33 +120,32 @@ constexpr int kFp32Steps = 12, kFp64Steps = 8;
 
 // The rare further FP64 steps: take the pending correction d, then step until
 // the test passes; on return (Ed, s, c, d) describe the last step.
-__device__ __forceinline__ bool newton_more(double d, float dmax2) {
-  const float df = (float)d;
-  return df * df > dmax2 || fabsf(df) > 1e-5f;
+__device__ __forceinline__ bool newton_more(float d, float dmax2) {
+  return d * d > dmax2 || fabsf(d) > 1e-5f;
 }
 
 static __device__ __noinline__ void kepler_more_fp64(double M, double e, float dmax2, double &Ed,
-                                                     double &s, double &c, double &d,
+                                                     double &s, double &c, float &d,
                                                      int &iters) {
   for (int step = 1; step < kFp64Steps; ++step) {
-    Ed -= d;
-    sincos_tab(Ed, s, c);
-    const double fp = 1.0 - e * c;
-    d = div_newton(Ed - e * s - M, fp);
+    Ed -= (double)d;
+    sincos_tab(Ed, (float)Ed, s, c);
+    d = newton_step(Ed, s, c, M, e);
     iters += 1;
     if (!newton_more(d, dmax2)) return;
   }
   iters = kKeplerMaxIter;  // no convergence
 }
 
-__device__ __forceinline__ double kepler_E_sc(double M, double e, float dmax2, double &sE,
-                                              double &cE, int &iters) {
+// ef: e in FP32 (precomputed per object)
+__device__ __forceinline__ double kepler_E_sc(double M, double e, float ef, float dmax2,
+                                              double &sE, double &cE, int &iters) {
+  const float Mf = (float)M;
   if (e == 0.0) {
-    sincos_tab(M, sE, cE);
+    sincos_tab(M, Mf, sE, cE);
     iters = 0;
     return M;
   }
-  const float Mf = (float)M, ef = (float)e;
   float E = (ef <= 0.5f) ? Mf + ef * sinf(Mf)
                          : Mf + 0.85f * ef * (sinf(Mf) >= 0.f ? 1.f : -1.f);
   int it = 0;
@@ -158,12 +157,12 @@ __device__ __forceinline__ double kepler_E_sc(double M, double e, float dmax2, d
     if (fabsf(d) <= 1e-6f) break;
   }
   double Ed = (double)E, s, c;
-  sincos_tab(Ed, s, c);
-  double fp = 1.0 - e * c;
-  double d = div_newton(Ed - e * s - M, fp);
+  sincos_tab(Ed, E, s, c);
+  float df = newton_step(Ed, s, c, M, e);
   iters = it + 1;
-  if (newton_more(d, dmax2)) kepler_more_fp64(M, e, dmax2, Ed, s, c, d, iters);
+  if (newton_more(df, dmax2)) kepler_more_fp64(M, e, dmax2, Ed, s, c, df, iters);
   // sin(E - d), cos(E - d) to second order in d
+  const double d = (double)df;
   const double h = 0.5 * d * d;
   sE = s - d * c - h * s;
   cE = c + d * s - h * c;
@@ -175,7 +174,7 @@ __device__ __forceinline__ void position_at(const ObjParams &p, double t, double
                                             int &iters) {
   double M = reduce_2pi(p.M0 + p.n * t);
   double s, c;
-  kepler_E_sc(M, p.e, p.dmax2, s, c, iters);
+  kepler_E_sc(M, p.e, p.ef, p.dmax2, s, c, iters);
   double ce = c - p.e;
 #pragma unroll
   for (int k = 0; k < 3; ++k) out[k] = fma(p.A[k], ce, p.B[k] * s);
@@ -244,8 +243,8 @@ __device__ __forceinline__ void segment_box(const ObjParams &p, int mode, int64_
   // (E within 1e-7 km / a: far inside the 1e-6 km margin)
   int i0 = 0, i1 = 0;
   double s0, c0, s1, c1;
-  double E0 = kepler_E_sc(Mr0, p.e, p.dmax2, s0, c0, i0);
-  double E1 = kepler_E_sc(Mr1, p.e, p.dmax2, s1, c1, i1);
+  double E0 = kepler_E_sc(Mr0, p.e, p.ef, p.dmax2, s0, c0, i0);
+  double E1 = kepler_E_sc(Mr1, p.e, p.ef, p.dmax2, s1, c1, i1);
   iters = max(i0, i1);
   double clo, chi, slo, shi;
   cos_sin_range(E0, E1, c0, c1, s0, s1, clo, chi, slo, shi);

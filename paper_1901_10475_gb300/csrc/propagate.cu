@@ -90,7 +90,7 @@ __global__ void k_prepare_objects(const scd_element *__restrict__ el, int64_t n,
   p.P = P;
   p.tolE = 1e-7 / a;
   p.dmax2 = e > 0.0 ? (float)(p.tolE * (1.0 - e) / (2.0 * e)) : INFINITY;
-  p.pad = 0.0f;
+  p.ef = (float)e;
   par[i] = p;
   kout[i] = (int32_t)k;
   segcnt[i] = (sa.T + k) / k;  // ceil((T+1)/k)
@@ -253,7 +253,7 @@ __global__ void k_prepare_params_only(const scd_element *__restrict__ el, int64_
   p.P = 0;
   p.tolE = 1e-7 / a;
   p.dmax2 = e > 0.0 ? (float)(p.tolE * (1.0 - e) / (2.0 * e)) : INFINITY;
-  p.pad = 0.0f;
+  p.ef = (float)e;
   par[i] = p;
 }
 

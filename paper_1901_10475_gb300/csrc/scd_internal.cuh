@@ -47,7 +47,7 @@ struct __align__(16) ObjParams {
   // (2 (1 - e cos E)), is at most e d^2 / (2 (1 - e)); so tolE (1 - e) / (2 e)
   // (infinite for e = 0)
   float dmax2;
-  float pad;
+  float ef;      // e in FP32 (the Kepler solve's FP32 steps)
 };
 
 // Device-side counters of one scene, read back with one copy.  The first
