@@ -151,7 +151,8 @@ typedef struct {
                          line: one traversal step descends two levels)     */
   float split_km;     /* 0: off.  Otherwise boxes whose largest spatial side
                          exceeds |split_km| km are sorted apart from the
-                         others (one more key bit above the Morton key), so
+                         others (one key bit above the Morton key, which
+                         with 12-bit axes gives up its finest time bit), so
                          each group gets its own subtree and the large boxes
                          do not widen the nodes of the small ones; < 0: the
                          large boxes first (default -1000: each pair of a

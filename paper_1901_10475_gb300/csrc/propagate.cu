@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) k_build_boxes(BoxArgs a) {
   // 4D Morton key of the box centre in the scene's bounding cube
   const float R = (float)__longlong_as_double((long long)a.ctr->extent_bits);
   unsigned long long key = box_morton(L, H, R, a.T1f, a.bits, a.time_scale, a.space_warp);
-  key |= (unsigned long long)split_bit(L, H, a.split_km) << (4 * a.bits);
+  key = sort_key(key, split_bit(L, H, a.split_km), a.bits, a.split_km != 0.0f);
   if (a.key64) a.key64[b] = key;
   else a.key32[b] = (uint32_t)key;
 }

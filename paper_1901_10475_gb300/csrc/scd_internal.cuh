@@ -250,6 +250,21 @@ __device__ __forceinline__ uint32_t split_bit(float4 L, float4 H, float split_km
 inline float split_of(const scd_tuning &t) {
   return t.morton_bits == 10 || t.morton_bits == 12 ? t.split_km : 0.0f;
 }
+// The sort key of a box: its Morton key with the size group's bit above it.
+// With 12-bit axes the group bit takes the place of the key's lowest bit
+// (the finest time bit), so that the key stays 48 bits (6 sort passes, not
+// 7; measured: node tests +0.25%, the screen 0.15 ms shorter); with 10-bit
+// axes that bit is worth more than the pass (traversal +12%).
+__host__ __device__ inline unsigned long long sort_key(unsigned long long morton, uint32_t group,
+                                                       int bits, bool split) {
+  if (!split) return morton;
+  if (bits >= 12) return (morton >> 1) | (unsigned long long)group << (4 * bits - 1);
+  return morton | (unsigned long long)group << (4 * bits);
+}
+inline int sort_key_bits(const scd_tuning &t) {
+  const bool split = split_of(t) != 0.0f;
+  return 4 * t.morton_bits + (split && t.morton_bits < 12 ? 1 : 0);
+}
 
 // Refinement rounds: flags of an interval (it met a box of another object;
 // that box was longer than one tick), a tick candidate t (24 bits) | i (20)

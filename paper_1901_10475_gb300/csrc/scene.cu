@@ -370,7 +370,7 @@ static int find_eager(scd_scene *s, const scd_decomp *d, int dkind, int raw_mode
   int64_t M = 0;
   if (dkind == SCD_DECOMP_NONE) {
     // A5: sort box ids along the Morton curve
-    int kb = 4 * s->tune.morton_bits + (split_of(s->tune) != 0.0f);
+    int kb = sort_key_bits(s->tune);
     if (s->tune.morton_bits > 8) {
       TRY(radix_sort_u64(s->d_key64.p, s->d_id.p, N, kb, s->sort_sc, st));
     } else {
@@ -450,7 +450,7 @@ static int enqueue_find(scd_scene *s, const scd_decomp *d, int dkind, int ob, in
   int64_t M = 0;
   if (s->events_ready) cudaEventRecord(s->ev[2], st);
   if (dkind == SCD_DECOMP_NONE) {
-    int kb = 4 * s->tune.morton_bits + (split_of(s->tune) != 0.0f);
+    int kb = sort_key_bits(s->tune);
     if (s->tune.morton_bits > 8) {
       TRY(radix_sort_u64(s->d_key64.p, s->d_id.p, s->N, kb, s->sort_sc, st));
     } else {
