@@ -274,8 +274,8 @@ SCD_API int scd_narrow_phase(scd_scene *s, const scd_pair *d_pairs, int64_t n_pa
 
 /* Adaptive refinement: the interval growing and halving of Alg 5 and Alg 6
  * as data-parallel rounds over all of the scene's objects.  Every object
- * starts with [0, T]; each round builds the 4D box (Def 8; SPEED boxes,
- * whatever the scene's box mode) of every active interval; an interval
+ * starts with [0, T]; each round builds the 4D box (Def 8, in the scene's
+ * box mode: SPEED or INTERVAL) of every active interval; an interval
  * whose box meets no other object's box is proven collision-free and
  * dropped, one that meets another is halved (ticks [t0, mid], [mid+1, t1]),
  * a single tick that still meets a longer interval waits; two single-tick
@@ -290,9 +290,12 @@ SCD_API int scd_narrow_phase(scd_scene *s, const scd_pair *d_pairs, int64_t n_pa
  *   rounds       (or NULL): the rounds taken, at most ceil(log2(T+1)) + 2.
  * Needs scd_build_boxes (the per-object constants): else SCD_ERR_STATE.
  * Batches of scenes: SCD_ERR_INVALID_ARG.  n > 2^20: SCD_ERR_CAPACITY.
- * Meeting boxes are found by a sort on the lower x face and a sweep, work
- * that grows with the boxes each box's x range covers: meant for
- * populations up to some thousands of objects.  Synchronous. */
+ * Meeting boxes are found per round by a Morton sort of the round's boxes,
+ * a radix tree and the persistent traversal; all rounds are queued at once
+ * with their sizes on the device.  The scene keeps the rounds' buffers (the
+ * capacities that sufficed) and, after the first call of a shape, the
+ * rounds' queue as a captured CUDA graph that later calls replay; both are
+ * freed with the scene.  Synchronous. */
 SCD_API int scd_refine_witnesses(scd_scene *s, scd_witness *host_out, int64_t cap,
                                  int64_t *n_out, int64_t *round_boxes, int *rounds);
 

@@ -42,6 +42,8 @@
 #include <algorithm>
 
 #include "kepler.cuh"
+#include <cstring>
+
 #include "scd_internal.cuh"
 
 namespace scd {
@@ -307,7 +309,9 @@ struct RfBuffers {
   DevBuf<float4> tlo, thi;  // trace (scd_refine_trace): every round's boxes
   DevBuf<uint32_t> tobj;
   int64_t tcap = 0;
-  SortScratch sc;
+  // the rounds' sort scratch (inside a captured graph: sized only by size())
+  // and the scratch of the sorts after the rounds
+  SortScratch sc, sc_post;
   explicit RfBuffers(cudaStream_t s) : st(s) {}
   ~RfBuffers() {
     for (int b = 0; b < 2; ++b) {
@@ -322,6 +326,7 @@ struct RfBuffers {
     qbox.release(st); ctr.release(st); sort_err.release(st); pairs.release(st);
     wit.release(st); span.release(st); tlo.release(st); thi.release(st); tobj.release(st);
     sc.release(st);
+    sc_post.release(st);
   }
   // every per-interval buffer for `cap` intervals a round, and `ccap`
   // candidates
@@ -353,9 +358,8 @@ static int rf_read_state(RfBuffers &B, unsigned long long h[RF_WORDS]) {
 // (levels >= 0): level l = 0 .. levels in units of T_s / 2^l, spans at the
 // last.  On return h holds the state words and round_counts the intervals
 // of every round; the caller checks capacity, candidates and the stack.
-static int rf_rounds(scd_scene *s, RfBuffers &B, int64_t cap, int64_t ccap, int deep,
-                     int rounds, int levels, unsigned long long h[RF_WORDS],
-                     unsigned long long *round_counts, unsigned int &trav_flags) {
+static int rf_queue(scd_scene *s, RfBuffers &B, int64_t cap, int64_t ccap, int deep,
+                    int rounds, int levels) {
   cudaStream_t st = B.st;
   const int64_t n = s->n;
   if (cudaMemsetAsync(B.state.p, 0, sizeof(unsigned long long) * RF_WORDS, st) != cudaSuccess ||
@@ -424,12 +428,119 @@ static int rf_rounds(scd_scene *s, RfBuffers &B, int64_t cap, int64_t ccap, int 
     note_launch(2);
     cur = nx;
   }
+  return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
+}
+
+// the rounds' sizes, the traversal flags and the state words, after the queue
+static int rf_collect(RfBuffers &B, unsigned long long h[RF_WORDS],
+                      unsigned long long *round_counts, unsigned int &trav_flags) {
   if (cudaMemcpyAsync(round_counts, B.rounds.p, sizeof(unsigned long long) * kRfMaxRounds,
-                      cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                      cudaMemcpyDeviceToHost, B.st) != cudaSuccess ||
       cudaMemcpyAsync(&trav_flags, &B.ctr.p->trav_flags, sizeof(unsigned int),
-                      cudaMemcpyDeviceToHost, st) != cudaSuccess)
+                      cudaMemcpyDeviceToHost, B.st) != cudaSuccess)
     return SCD_ERR_CUDA;
   return rf_read_state(B, h);
+}
+
+// The rounds' queue captured as one CUDA graph, replayed while the call's
+// shape (sizes, capacities, rounds) and the scene's buffers stay the same:
+// the small cases are launch-bound (about 30 launches a round).  The
+// buffers live with the scene so that the graph's pointers stay valid.
+struct RfCache {
+  RfBuffers B;
+  cudaStream_t gst = nullptr;
+  cudaEvent_t in = nullptr, out = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t key[10] = {};
+  unsigned long long nlaunch = 0;  // kernels in the graph
+  explicit RfCache(cudaStream_t st) : B(st) {}
+  ~RfCache() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (gst) {
+      cudaStreamSynchronize(gst);
+      cudaStreamDestroy(gst);
+    }
+    if (in) cudaEventDestroy(in);
+    if (out) cudaEventDestroy(out);
+  }
+};
+
+static void rf_key(const scd_scene *s, const RfBuffers &B, int64_t cap, int64_t ccap, int deep,
+                   int rounds, int levels, int64_t k[10]) {
+  k[0] = cap;
+  k[1] = ccap;
+  k[2] = deep;
+  k[3] = rounds;
+  k[4] = levels;
+  k[5] = s->n;
+  k[6] = s->T;
+  k[7] = s->box_mode * 1000000 + (int64_t)(split_of(s->tune) * 10.0f);
+  k[8] = (int64_t)reinterpret_cast<uintptr_t>(B.obj[0].p) ^ (int64_t)reinterpret_cast<uintptr_t>(s->d_par.p);
+  int64_t tb;
+  memcpy(&tb, &s->tick_s, sizeof(tb));
+  k[9] = tb;
+}
+
+// queue the rounds: by the cached graph when its shape matches, else
+// eagerly
+static int rf_rounds(scd_scene *s, RfBuffers &B, RfCache *gc, int64_t cap, int64_t ccap,
+                     int deep, int rounds, int levels, unsigned long long h[RF_WORDS],
+                     unsigned long long *round_counts, unsigned int &trav_flags) {
+  int64_t k[10];
+  rf_key(s, B, cap, ccap, deep, rounds, levels, k);
+  if (gc && gc->exec && memcmp(k, gc->key, sizeof(k)) == 0) {
+    if (cudaEventRecord(gc->in, B.st) != cudaSuccess ||
+        cudaStreamWaitEvent(gc->gst, gc->in, 0) != cudaSuccess ||
+        cudaGraphLaunch(gc->exec, gc->gst) != cudaSuccess ||
+        cudaEventRecord(gc->out, gc->gst) != cudaSuccess ||
+        cudaStreamWaitEvent(B.st, gc->out, 0) != cudaSuccess)
+      return SCD_ERR_CUDA;
+    note_launch(gc->nlaunch);
+  } else {
+    int rc = rf_queue(s, B, cap, ccap, deep, rounds, levels);
+    if (rc != SCD_OK) return rc;
+  }
+  return rf_collect(B, h, round_counts, trav_flags);
+}
+
+// capture the queue of a shape that has just run eagerly (nothing is
+// allocated while capturing: every buffer is sized); without a graph the
+// calls stay eager
+static void rf_capture(scd_scene *s, RfCache &gc, int64_t cap, int64_t ccap, int deep,
+                       int rounds, int levels) {
+  if (!gc.gst) {
+    if (cudaStreamCreateWithFlags(&gc.gst, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&gc.in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&gc.out, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+  }
+  if (gc.exec) {
+    cudaGraphExecDestroy(gc.exec);
+    gc.exec = nullptr;
+  }
+  if (cudaStreamSynchronize(gc.B.st) != cudaSuccess) return;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(gc.gst, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const cudaStream_t st = gc.B.st;
+  gc.B.st = gc.gst;
+  const unsigned long long mark = launch_count();
+  const int rc = rf_queue(s, gc.B, cap, ccap, deep, rounds, levels);
+  const cudaError_t e = cudaStreamEndCapture(gc.gst, &g);
+  gc.B.st = st;
+  gc.nlaunch = launch_count() - mark;
+  if (rc == SCD_OK && e == cudaSuccess && g &&
+      cudaGraphInstantiate(&gc.exec, g, 0) == cudaSuccess) {
+    rf_key(s, gc.B, cap, ccap, deep, rounds, levels, gc.key);
+  } else {
+    gc.exec = nullptr;
+    cudaGetLastError();
+  }
+  if (g) cudaGraphDestroy(g);
 }
 
 }  // namespace scd
@@ -438,20 +549,21 @@ namespace scd {
 // Queue the rounds, and again with more room while a round's intervals, the
 // candidates or a traversal stack did not fit.  The capacities that sufficed
 // stay on the scene for its next call.
-static int rf_run(scd_scene *s, RfBuffers &B, int rounds, int levels,
+static int rf_run(scd_scene *s, RfBuffers &B, RfCache *gc, int rounds, int levels,
                   unsigned long long h[RF_WORDS], unsigned long long *round_counts) {
   cudaStream_t st = B.st;
   if (!B.state.ensure(RF_WORDS, st) || !B.sort_err.ensure(1, st) ||
       !B.rounds.ensure(kRfMaxRounds, st) || !B.ctr.ensure(1, st))
     return SCD_ERR_OOM;
   B.sc.err = B.sort_err.p;
+  B.sc_post.err = B.sort_err.p;
   int64_t cap = std::max<int64_t>(s->rf_cap, std::max<int64_t>(4 * s->n, 1 << 16));
   int64_t ccap = std::max<int64_t>(s->rf_ccap, 1 << 16);
   int deep = s->rf_deep;
   for (int attempt = 0; attempt < 8; ++attempt) {
     if (!B.size(cap, ccap)) return SCD_ERR_OOM;
     unsigned int tf = 0;
-    int rc = rf_rounds(s, B, cap, ccap, deep, rounds, levels, h, round_counts, tf);
+    int rc = rf_rounds(s, B, gc, cap, ccap, deep, rounds, levels, h, round_counts, tf);
     if (rc != SCD_OK) return rc;
     bool again = false;
     if (h[RF_OVER] > (unsigned long long)cap) {
@@ -471,10 +583,28 @@ static int rf_run(scd_scene *s, RfBuffers &B, int rounds, int levels,
       s->rf_cap = cap;
       s->rf_ccap = ccap;
       s->rf_deep = deep;
+      if (gc) {
+        int64_t k[10];
+        rf_key(s, B, cap, ccap, deep, rounds, levels, k);
+        if (!gc->exec || memcmp(k, gc->key, sizeof(k)) != 0)
+          rf_capture(s, *gc, cap, ccap, deep, rounds, levels);
+      }
       return SCD_OK;
     }
   }
   return SCD_ERR_CAPACITY;
+}
+
+// the scene's refinement buffers and graph, made on first use
+static RfCache &rf_cache(scd_scene *s) {
+  if (!s->rf) s->rf = new RfCache(s->stream);
+  s->rf->B.st = s->stream;
+  return *s->rf;
+}
+
+void rf_release(scd_scene *s) {
+  delete s->rf;
+  s->rf = nullptr;
 }
 
 static int rf_check_scene(const scd_scene *s) {
@@ -494,13 +624,14 @@ extern "C" SCD_API int scd_refine_witnesses(scd_scene *s, scd_witness *host_out,
   if (int rc = rf_check_scene(s)) return rc;
   const unsigned long long mark = launch_count();
   cudaStream_t st = s->stream;
-  RfBuffers B(st);
+  RfCache &gc = rf_cache(s);
+  RfBuffers &B = gc.B;
   // the halvings of [0, T] down to single ticks, one round to decide them
   // and one for single ticks that wait for a longer interval
   int nr = 2;
   while ((1ll << (nr - 2)) < s->T + 1) ++nr;
   unsigned long long h[RF_WORDS], rc_[kRfMaxRounds];
-  int rc = rf_run(s, B, nr, -1, h, rc_);
+  int rc = rf_run(s, B, &gc, nr, -1, h, rc_);
   if (rc != SCD_OK) return rc;
   int r = 0;
   while (r < nr && rc_[r] > 0) {
@@ -514,7 +645,7 @@ extern "C" SCD_API int scd_refine_witnesses(scd_scene *s, scd_witness *host_out,
   // distinct tick candidates, then Alg 1's test at each tick
   int64_t nw = 0;
   if (ncand > 0) {
-    int rc2 = radix_sort_u64(B.cand.p, nullptr, ncand, 64, B.sc, st);
+    int rc2 = radix_sort_u64(B.cand.p, nullptr, ncand, 64, B.sc_post, st);
     if (rc2 != SCD_OK) return rc2;
     if (!B.pairs.ensure(ncand, st) || !B.first.ensure(ncand, st)) return SCD_ERR_OOM;
     k_rf_unique<<<grid_of(ncand), kRfThreads, 0, st>>>(B.cand.p, ncand, B.pairs.p, B.state.p);
@@ -530,7 +661,7 @@ extern "C" SCD_API int scd_refine_witnesses(scd_scene *s, scd_witness *host_out,
     if ((rc2 = rf_read_state(B, h)) != SCD_OK) return rc2;
     nw = (int64_t)h[RF_NWIT];
     if (nw > 0) {
-      if ((rc2 = radix_sort_u64(B.wkey.p, nullptr, nw, 64, B.sc, st)) != SCD_OK) return rc2;
+      if ((rc2 = radix_sort_u64(B.wkey.p, nullptr, nw, 64, B.sc_post, st)) != SCD_OK) return rc2;
       if (!B.wit.ensure(nw, st)) return SCD_ERR_OOM;
       k_rf_decode<<<grid_of(nw), kRfThreads, 0, st>>>(B.wkey.p, nw, B.wit.p);
       note_launch();
@@ -570,9 +701,10 @@ extern "C" SCD_API int scd_refine_continuous(scd_scene *s, double eps_s, scd_spa
   if (L > kRfMaxLevels) return SCD_ERR_CAPACITY;  // eps_s below T / 2^22
   const unsigned long long mark = launch_count();
   cudaStream_t st = s->stream;
-  RfBuffers B(st);
+  RfCache &gc = rf_cache(s);
+  RfBuffers &B = gc.B;
   unsigned long long h[RF_WORDS], rc_[kRfMaxRounds];
-  int rc = rf_run(s, B, 0, L, h, rc_);
+  int rc = rf_run(s, B, &gc, 0, L, h, rc_);
   if (rc != SCD_OK) return rc;
   int r = 0;
   while (r <= L && rc_[r] > 0) {
@@ -584,14 +716,14 @@ extern "C" SCD_API int scd_refine_continuous(scd_scene *s, double eps_s, scd_spa
   const int64_t ncand = (int64_t)h[RF_NCAND];
   int64_t nu = 0;
   if (ncand > 0) {  // spans of the finest level: distinct, in (i, j, t0, t1) order
-    int rc2 = radix_sort_u64(B.cand.p, nullptr, ncand, 64, B.sc, st);
+    int rc2 = radix_sort_u64(B.cand.p, nullptr, ncand, 64, B.sc_post, st);
     if (rc2 != SCD_OK) return rc2;
     if (!B.wkey.ensure(ncand, st)) return SCD_ERR_OOM;
     k_rf_distinct<<<grid_of(ncand), kRfThreads, 0, st>>>(B.cand.p, ncand, B.wkey.p, B.state.p);
     note_launch();
     if ((rc2 = rf_read_state(B, h)) != SCD_OK) return rc2;
     nu = (int64_t)h[RF_NUNIQ];
-    if ((rc2 = radix_sort_u64(B.wkey.p, nullptr, nu, 64, B.sc, st)) != SCD_OK) return rc2;
+    if ((rc2 = radix_sort_u64(B.wkey.p, nullptr, nu, 64, B.sc_post, st)) != SCD_OK) return rc2;
     if (!B.span.ensure(nu, st)) return SCD_ERR_OOM;
     k_rf_span_decode<<<grid_of(nu), kRfThreads, 0, st>>>(B.wkey.p, nu, ldexp(T_s, -L), B.span.p);
     note_launch();
@@ -634,7 +766,7 @@ extern "C" SCD_API int scd_refine_trace(scd_scene *s, double eps_s, float *lo4, 
       !B.tobj.ensure((size_t)B.tcap, st))
     return SCD_ERR_OOM;
   unsigned long long h[RF_WORDS], rc_[kRfMaxRounds];
-  int rc = rf_run(s, B, nr, L, h, rc_);
+  int rc = rf_run(s, B, nullptr, nr, L, h, rc_);
   if (rc != SCD_OK) return rc;
   const int nrounds = L >= 0 ? L + 1 : nr;
   int r = 0;

@@ -438,6 +438,7 @@ int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, DevBuf<int64_
 // the scene (opaque in the ABI)
 namespace scd {
 constexpr int kStreamBuckets = 16;  // buckets of a canonical list streamed to the host
+struct RfCache;  // the refinement's buffers and captured rounds (refine.cu)
 }
 
 struct scd_scene {
@@ -517,6 +518,7 @@ struct scd_scene {
   scd_pair *host_dst = nullptr;
   int64_t host_cap = 0;
   bool host_done = false;
+  scd::RfCache *rf = nullptr;  // the adaptive refinement's buffers and graph
   cudaStream_t cstream = nullptr;
   cudaEvent_t cev[scd::kStreamBuckets] = {};
   scd::DevBuf<unsigned long long> d_part, d_parte;  // the records split by their top digit
@@ -591,6 +593,8 @@ int traverse_round(const QBox *qbox, const uint32_t *qlink, const SBox *sbox,
 int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits);
 // canonical list with every count read on the device (graph capture)
 int canonicalize_dev(scd_scene *s, int obj_bits, int t_bits);
+// the refinement's buffers and graph kept by the scene, freed with it
+void rf_release(scd_scene *s);
 // canonical list streamed into host memory bucket by bucket (run starts
 // packed with their last tick); SCD_ERR_STATE when the records do not allow
 // it; the copies are left running on the scene's copy stream

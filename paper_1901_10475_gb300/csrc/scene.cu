@@ -773,6 +773,7 @@ extern "C" SCD_API void scd_scene_destroy(scd_scene *s) {
   s->d_objT.release(st); s->d_objscene.release(st); s->d_sceneoff.release(st);
   s->d_pairoff.release(st);
   s->d_part.release(st); s->d_parte.release(st);
+  rf_release(s);
   if (s->events_ready)
     for (int k = 0; k < 8; ++k) cudaEventDestroy(s->ev[k]);
   if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);

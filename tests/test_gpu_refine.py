@@ -238,3 +238,31 @@ def test_every_continuous_round_follows_from_its_own_boxes(scd):
     want = sorted({(int(c["i"]), int(c["j"]), c["tlo"] * unit, c["thi"] * unit) for c in cells})
     assert sorted(map(tuple, spans.tolist())) == want
     sc.close()
+
+
+def test_repeated_calls_replay_the_same_rounds(scd):
+    """The second and later calls on a scene replay its captured rounds: the
+    same witnesses and round sizes; after new elements (same count) the
+    results are those of a fresh scene; the continuous variant in between
+    (another shape of rounds) changes nothing."""
+    els = P.uniform_leo(512)
+    els[511] = els[7]
+    sc = _scene(scd, els, 6000.0)
+    w1, rb1 = sc.refine_witnesses()
+    for _ in range(3):
+        w, rb = sc.refine_witnesses()
+        assert _tuples(w) == _tuples(w1) and rb.tolist() == rb1.tolist()
+    spans, _ = sc.refine_continuous(1.0)
+    w, rb = sc.refine_witnesses()
+    assert _tuples(w) == _tuples(w1) and rb.tolist() == rb1.tolist()
+    els2 = P.uniform_leo(512, seed=77)
+    els2[100] = els2[200]
+    sc.set_elements(els2)
+    sc.build_boxes()
+    w2, rb2 = sc.refine_witnesses()
+    fresh = _scene(scd, els2, 6000.0)
+    w3, rb3 = fresh.refine_witnesses()
+    assert _tuples(w2) == _tuples(w3) and rb2.tolist() == rb3.tolist()
+    assert len(w2) > 0
+    sc.close()
+    fresh.close()
