@@ -1049,8 +1049,10 @@ int canonicalize_streamed(scd_scene *s, int obj_bits, int t_bits, scd_pair *host
   int64_t out_at = 0;
   int d0 = 0;
   for (int b = 0; b < kStreamBuckets && d0 < 256; ++b) {
-    // whole digits up to about an equal share of the starts still left
-    const int64_t share = (n - out_at + (kStreamBuckets - b) - 1) / (kStreamBuckets - b);
+    // whole digits up to about an equal share of the starts still left; the
+    // first bucket small, so that the copies (the slower stream) start early
+    const int64_t share = b == 0 ? (n + 63) / 64
+                                 : (n - out_at + (kStreamBuckets - b) - 1) / (kStreamBuckets - b);
     int d1 = d0;
     int64_t m = 0, me = 0;
     while (d1 < 256 && (m < share || b == kStreamBuckets - 1)) {
