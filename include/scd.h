@@ -314,7 +314,8 @@ typedef struct {
  * the first length <= eps_s; every pair of meeting boxes at that level is
  * one span, the intersection of the two intervals (an instant where two
  * consecutive intervals meet).  No time step: a collision at any real time
- * lies in a span.  SPEED boxes.  Spans sorted by (i, j, t0, t1), each once.
+ * lies in a span.  Boxes in the scene's box mode.  Spans sorted by (i, j,
+ * t0, t1), each once.  Buffers and graph shared with scd_refine_witnesses.
  *   host_out, cap, n_out, round_boxes, rounds: as scd_refine_witnesses.
  * eps_s <= 0: SCD_ERR_INVALID_ARG; eps_s below T tick_s / 2^22:
  * SCD_ERR_CAPACITY.  Needs scd_build_boxes.  Synchronous. */
