@@ -592,6 +592,9 @@ extern "C" SCD_API int scd_find_pairs(scd_scene *s, const scd_decomp *d, scd_pai
   s->host_cap = cap;
   s->host_done = false;
   int rc = find_pairs_impl(s, d, 0);
+  // no copy into host_out may still run once the call returns, whatever
+  // the path (an error after some buckets were queued included)
+  if (s->cstream) cudaStreamSynchronize(s->cstream);
   const bool streamed = s->host_done;
   s->host_dst = nullptr;
   s->host_cap = 0;
