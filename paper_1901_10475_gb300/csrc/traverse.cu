@@ -325,7 +325,11 @@ __global__ void __launch_bounds__(256) k_traverse(TravArgs a) {
 // measured the same on the 24 h catalog screen (21.9, 21.9, 22.0 ms)
 constexpr int kT2Threads = 128;
 constexpr int kT2Warps = kT2Threads / 32;
-constexpr int kHitCap = 256;  // per warp; drained when fewer than 64 slots remain
+// candidate pairs buffered per warp, drained when fewer than one step's
+// worth (128) of slots remain: fewer, longer drains.  Measured on the 24 h
+// catalog screen: 256 18.70 ms, 384 18.39, 448 18.32, 512 18.56 (a larger
+// shared-memory carve-out takes L1), 768 34.9 (fewer resident blocks)
+constexpr int kHitCap = 448;
 // queries claimed per warp atomic; small, so that the queries in flight stay
 // a narrow window of the Morton order and their nodes stay in L2
 // (64 per claim: +4% traversal time, 128: +17%)
