@@ -911,18 +911,31 @@ static int cmp_witness_alg1(const void *x, const void *y) {
   return 0;
 }
 
+int64_t or_refine_start_ticks(const double *el, int64_t T, double tick_s) {
+  const double q = floor(or_period(el) / (64.0 * tick_s));
+  int64_t L = 1;
+  while ((double)(2 * L) <= q) L *= 2;
+  return L > T ? T + 1 : L;
+}
+
 int64_t or_refine_discrete(const double *els, int64_t n, int64_t T, double tick_s, int mode,
-                           or_witness *out, int64_t cap, int64_t *round_boxes, int *rounds,
-                           int64_t *n_tick_candidates) {
-  int64_t m = n, scap = 0, ncap = 0, ccap = 0, nc = 0;
-  or_seg *S = (or_seg *)grow(NULL, &scap, n > 0 ? n : 1, sizeof(or_seg));
+                           int start, or_witness *out, int64_t cap, int64_t *round_boxes,
+                           int *rounds, int64_t *n_tick_candidates) {
+  int64_t m = 0, scap = 0, ncap = 0, ccap = 0, nc = 0;
+  or_seg *S = NULL;
   or_seg *next = NULL;
   or_witness *cand = NULL;
   for (int64_t i = 0; i < n; ++i) {
-    S[i].obj = i;
-    S[i].t0 = 0;
-    S[i].t1 = T;
+    const int64_t L = start ? or_refine_start_ticks(els + 7 * i, T, tick_s) : T + 1;
+    for (int64_t t0 = 0; t0 <= T; t0 += L) {
+      S = (or_seg *)grow(S, &scap, m + 1, sizeof(or_seg));
+      S[m].obj = i;
+      S[m].t0 = t0;
+      S[m].t1 = t0 + L - 1 < T ? t0 + L - 1 : T;
+      ++m;
+    }
   }
+  if (!S) S = (or_seg *)grow(NULL, &scap, 1, sizeof(or_seg));
   int r = 0;
   while (m > 0 && r < 64) {
     if (round_boxes) round_boxes[r] = m;
