@@ -83,18 +83,19 @@ WORKLOADS = {
     "refine512": {
         "metric": "ms per adaptive-refinement solve at n=512, 6000 s (every collision witness)",
         "desc": ("n=512 uniform LEO (a 6678-8378 km, e < 0.01, i 0-100 deg), r = 2.5 km, 6000 s "
-                 "at 1 s ticks: Alg 5-6 as data-parallel rounds from [0, T] (per round the "
-                 "boxes of all active intervals, their Morton sort, a radix tree and the "
-                 "persistent traversal; all rounds queued without host reads), tick candidates "
-                 "decided by the narrow phase; against the fixed 10-tick screen plus the narrow "
-                 "phase on the same population")},
+                 "at 1 s ticks: Alg 5-6 as data-parallel rounds from period-bounded first "
+                 "intervals (per round the boxes of all active intervals, their Morton sort, a "
+                 "radix tree and the persistent traversal; all rounds queued without host "
+                 "reads), tick candidates decided by the narrow phase; against the fixed "
+                 "10-tick screen plus the narrow phase on the same population")},
     "refine24h": {
         "metric": "ms per 24h adaptive-refinement solve at n=16848 (every collision witness)",
         "desc": ("the n=16848 mixture, 24 h at 1 s ticks: Alg 5-6 as data-parallel rounds from "
-                 "[0, T] (per round the boxes of all active intervals, their Morton sort, a "
-                 "radix tree and the persistent traversal; all rounds queued without host "
-                 "reads), tick candidates decided by the narrow phase; against the fixed "
-                 "P/100 screen plus the narrow phase on the same population")},
+                 "period-bounded first intervals (per round the boxes of all active "
+                 "intervals, their Morton sort, a radix tree and the persistent traversal; all "
+                 "rounds queued without host reads), tick candidates decided by the narrow "
+                 "phase; against the fixed P/100 screen plus the narrow phase on the same "
+                 "population")},
     "batch64": {
         "metric": "scenes per second, 64 scenes, ~1.2M objects, horizons 6-72 h",
         "desc": ("64 independent catalog-shaped scenes, sizes log-uniform 1e3-6e4 (total "

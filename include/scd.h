@@ -275,8 +275,11 @@ SCD_API int scd_narrow_phase(scd_scene *s, const scd_pair *d_pairs, int64_t n_pa
                              int32_t *d_first, uint32_t *d_count, scd_witness *earliest);
 
 /* Adaptive refinement: the interval growing and halving of Alg 5 and Alg 6
- * as data-parallel rounds over all of the scene's objects.  Every object
- * starts with [0, T]; each round builds the 4D box (Def 8, in the scene's
+ * as data-parallel rounds over all of the scene's objects.  Object i
+ * starts with its ticks 0..T cut into intervals of L_i ticks (the last one
+ * shorter): L_i is the largest power of two not above
+ * max(1, floor(P_i / (64 tick))), P_i its Kepler period, or T + 1 when that
+ * is longer.  Each round builds the 4D box (Def 8, in the scene's
  * box mode: SPEED or INTERVAL) of every active interval; an interval
  * whose box meets no other object's box is proven collision-free and
  * dropped, one that meets another is halved (ticks [t0, mid], [mid+1, t1]),
@@ -289,7 +292,7 @@ SCD_API int scd_narrow_phase(scd_scene *s, const scd_pair *d_pairs, int64_t n_pa
  *   n_out        the witness count; cap too small: SCD_ERR_BUFFER_TOO_SMALL
  *                with *n_out set and nothing written.
  *   round_boxes  host array of 64 (or NULL): active intervals per round.
- *   rounds       (or NULL): the rounds taken, at most ceil(log2(T+1)) + 2.
+ *   rounds       (or NULL): the rounds taken, at most ceil(log2(max L_i)) + 2.
  * Needs scd_build_boxes (the per-object constants): else SCD_ERR_STATE.
  * Batches of scenes: SCD_ERR_INVALID_ARG.  n > 2^20: SCD_ERR_CAPACITY.
  * Meeting boxes are found per round by a Morton sort of the round's boxes,

@@ -1,8 +1,13 @@
 // refine.cu -- adaptive refinement: the interval growing and halving of
 // Alg 5 and Alg 6 as data-parallel rounds over all objects at once.
 //
-// Every object starts with the whole horizon [0, T] as its interval.  A round
-// builds the 4D box of every active interval (Def 8, in the scene's box
+// Object i starts with its ticks [0, T] cut into intervals of L_i ticks
+// (the last one shorter), L_i the largest power of two not above
+// max(1, floor(P_i / (64 tick))), P_i its period, or the whole horizon when
+// that is longer: Alg 5 grows an interval from one step up to a bound, and a
+// box over more than about a 64th of an orbit meets nearly every other box
+// of a crowded catalog, so the rounds with longer intervals would split
+// nearly everything at full cost and decide nothing.  A round builds the 4D box of every active interval (Def 8, in the scene's box
 // mode), finds the boxes that meet a box of another object, and then
 //   - drops an interval whose box meets none: its object is proven free of
 //     collisions over it (every other object's position at those times lies
@@ -32,8 +37,8 @@
 // (in its refinement mode) flags both intervals of every meeting pair and
 // collects the candidates.  The rounds run without the host: every kernel
 // reads the round's interval count from device memory, and the host queues
-// all rounds at once (at most ceil(log2(T + 1)) + 2 of them, or the levels
-// of the continuous variant) and reads the counts once at the end.  The
+// all rounds at once (ceil(log2(L)) + 2 of them, L the longest first
+// interval, or the levels of the continuous variant) and reads the counts once at the end.  The
 // buffers are sized for a capacity of intervals per round; a round that
 // would exceed it is cut short and flagged, and the call runs again with a
 // larger capacity (kept on the scene for the next call).
@@ -57,7 +62,7 @@ constexpr int64_t kRfMaxObjects = 1ll << 20;
 // count asked for
 enum {
   RF_NCAND = 0, RF_NNEXT = 1, RF_ERR = 2, RF_NUNIQ = 3, RF_NWIT = 4, RF_M = 5, RF_OVER = 6,
-  RF_WORDS = 7
+  RF_LMAX = 7, RF_WORDS = 8
 };
 // the rounds' 4D Morton keys: 10 bits per axis, time weighed 4x against
 // space (24 h catalog rounds 552 -> 522 ms against equal weights; 12-bit axes
@@ -68,6 +73,63 @@ constexpr float kRfTimeScale = 4.0f;
 __device__ __forceinline__ int64_t rf_count(const unsigned long long *state, int64_t cap) {
   const unsigned long long m = state[RF_M];
   return m < (unsigned long long)cap ? (int64_t)m : cap;
+}
+
+// The first interval length of object o in ticks: the largest power of
+// two not above max(1, floor(P / (64 tick))), or T + 1 when longer (a
+// bounded first interval: Alg 5's intervals start at one step and grow up to
+// a bound; the rounds before, in which nearly every box meets every other,
+// are skipped).  The division is rounded as the oracle's.
+__device__ __forceinline__ int32_t rf_start_ticks(const ObjParams &p, int32_t T, double tick_s) {
+  const double q = floor(__ddiv_rn(p.P, 64.0 * tick_s));
+  int64_t L = 1;
+  while (L <= T && (double)(2 * L) <= q) L *= 2;  // past T the answer is T + 1
+  return L > T ? T + 1 : (int32_t)L;
+}
+
+// the object whose run of first intervals holds interval i: the largest o
+// with off[o] <= i
+__device__ __forceinline__ int64_t rf_owner(const int64_t *__restrict__ off, int64_t n,
+                                            int64_t i) {
+  int64_t lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// per object its first round's intervals, and the longest first interval
+__global__ void k_rf_start_count(const ObjParams *__restrict__ par, int64_t n, int32_t T,
+                                 double tick_s, int64_t *__restrict__ cnt,
+                                 unsigned long long *__restrict__ state) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n) return;
+  const int32_t L = rf_start_ticks(par[o], T, tick_s);
+  cnt[o] = ((int64_t)T + L) / L;  // ceil((T + 1) / L)
+  atomicMax(&state[RF_LMAX], (unsigned long long)L);
+}
+
+// The first round's intervals, object-major: [k L, min((k + 1) L - 1, T)];
+// at most cap of them written, the count asked for noted for the retry.
+__global__ void k_rf_init_start(const ObjParams *__restrict__ par, int64_t n, int32_t T,
+                                double tick_s, const int64_t *__restrict__ off, int64_t cap,
+                                uint32_t *obj, int32_t *t0, int32_t *t1,
+                                unsigned long long *state) {
+  const int64_t total = off[n];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    state[RF_M] = (unsigned long long)(total < cap ? total : cap);
+    if (total > cap) atomicMax(&state[RF_OVER], (unsigned long long)total);
+  }
+  if (i >= total || i >= cap) return;
+  const int64_t o = rf_owner(off, n, i);
+  const int32_t L = rf_start_ticks(par[o], T, tick_s);
+  const int64_t a = (i - off[o]) * L;
+  const int64_t b = a + L - 1;
+  obj[i] = (uint32_t)o;
+  t0[i] = (int32_t)a;
+  t1[i] = (int32_t)(b < T ? b : T);
 }
 
 __global__ void k_rf_init(int64_t n, int32_t T, uint32_t *obj, int32_t *t0, int32_t *t1,
@@ -309,6 +371,9 @@ struct RfBuffers {
   DevBuf<float4> tlo, thi;  // trace (scd_refine_trace): every round's boxes
   DevBuf<uint32_t> tobj;
   int64_t tcap = 0;
+  // discrete rounds: per object its first intervals and their offsets
+  DevBuf<int64_t> scnt, soff, stmp;
+  int64_t start_total = 0;
   // the rounds' sort scratch (inside a captured graph: sized only by size())
   // and the scratch of the sorts after the rounds
   SortScratch sc, sc_post;
@@ -325,6 +390,7 @@ struct RfBuffers {
     wkey.release(st); rounds.release(st); sbox.release(st); nodes.release(st); nq.release(st);
     qbox.release(st); ctr.release(st); sort_err.release(st); pairs.release(st);
     wit.release(st); span.release(st); tlo.release(st); thi.release(st); tobj.release(st);
+    scnt.release(st); soff.release(st); stmp.release(st);
     sc.release(st);
     sc_post.release(st);
   }
@@ -353,8 +419,38 @@ static int rf_read_state(RfBuffers &B, unsigned long long h[RF_WORDS]) {
   return SCD_OK;
 }
 
-// The rounds of one call, queued at once.  Discrete: rounds of [0, T] in
-// ticks until nothing is left (at most `rounds` of them).  Continuous
+// The first intervals of the discrete rounds (rf_start_ticks): their counts
+// per object, the offsets, and on the host their total and the number of
+// rounds that halve the longest down to single ticks and decide them.
+static int rf_start(scd_scene *s, RfBuffers &B, int &rounds) {
+  cudaStream_t st = B.st;
+  const int64_t n = s->n;
+  if (!B.scnt.ensure((size_t)n, st) || !B.soff.ensure((size_t)n + 1, st)) return SCD_ERR_OOM;
+  if (cudaMemsetAsync(B.state.p, 0, sizeof(unsigned long long) * RF_WORDS, st) != cudaSuccess)
+    return SCD_ERR_CUDA;
+  if (n > 0) {
+    k_rf_start_count<<<grid_of(n), kRfThreads, 0, st>>>(s->d_par.p, n, (int32_t)s->T, s->tick_s,
+                                                        B.scnt.p, B.state.p);
+    note_launch();
+  }
+  int rc = scan_exclusive_i64(B.scnt.p, B.soff.p, n, B.stmp, st);
+  if (rc != SCD_OK) return rc;
+  int64_t total = 0;
+  unsigned long long lmax = 0;
+  if (cudaMemcpyAsync(&total, B.soff.p + n, sizeof(total), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(&lmax, B.state.p + RF_LMAX, sizeof(lmax), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SCD_ERR_CUDA;
+  B.start_total = total;
+  rounds = 2;
+  while ((1ull << (rounds - 2)) < lmax) ++rounds;
+  return SCD_OK;
+}
+
+// The rounds of one call, queued at once.  Discrete: rounds from the first
+// intervals (rf_start) until nothing is left (at most `rounds` of them).  Continuous
 // (levels >= 0): level l = 0 .. levels in units of T_s / 2^l, spans at the
 // last.  On return h holds the state words and round_counts the intervals
 // of every round; the caller checks capacity, candidates and the stack.
@@ -372,8 +468,13 @@ static int rf_queue(scd_scene *s, RfBuffers &B, int64_t cap, int64_t ccap, int d
     return SCD_ERR_CUDA;
   const bool cont = levels >= 0;
   const double T_s = (double)s->T * s->tick_s;
-  k_rf_init<<<grid_of(n), kRfThreads, 0, st>>>(n, cont ? 1 : (int32_t)s->T, B.obj[0].p,
-                                                B.t0[0].p, B.t1[0].p, B.state.p);
+  if (cont)
+    k_rf_init<<<grid_of(n), kRfThreads, 0, st>>>(n, 1, B.obj[0].p, B.t0[0].p, B.t1[0].p,
+                                                  B.state.p);
+  else
+    k_rf_init_start<<<grid_of(cap), kRfThreads, 0, st>>>(s->d_par.p, n, (int32_t)s->T, s->tick_s,
+                                                          B.soff.p, cap, B.obj[0].p, B.t0[0].p,
+                                                          B.t1[0].p, B.state.p);
   note_launch();
   const float split = split_of(s->tune);
   const int kb = 4 * kRfMortonBits + (split != 0.0f);
@@ -549,7 +650,8 @@ namespace scd {
 // Queue the rounds, and again with more room while a round's intervals, the
 // candidates or a traversal stack did not fit.  The capacities that sufficed
 // stay on the scene for its next call.
-static int rf_run(scd_scene *s, RfBuffers &B, RfCache *gc, int rounds, int levels,
+// Discrete rounds (levels < 0) set `rounds` from their first intervals.
+static int rf_run(scd_scene *s, RfBuffers &B, RfCache *gc, int &rounds, int levels,
                   unsigned long long h[RF_WORDS], unsigned long long *round_counts) {
   cudaStream_t st = B.st;
   if (!B.state.ensure(RF_WORDS, st) || !B.sort_err.ensure(1, st) ||
@@ -558,6 +660,12 @@ static int rf_run(scd_scene *s, RfBuffers &B, RfCache *gc, int rounds, int level
   B.sc.err = B.sort_err.p;
   B.sc_post.err = B.sort_err.p;
   int64_t cap = std::max<int64_t>(s->rf_cap, std::max<int64_t>(4 * s->n, 1 << 16));
+  if (levels < 0) {
+    int rc = rf_start(s, B, rounds);
+    if (rc != SCD_OK) return rc;
+    if (rounds > kRfMaxRounds) return SCD_ERR_INTERNAL;
+    cap = std::max<int64_t>(cap, B.start_total);
+  }
   int64_t ccap = std::max<int64_t>(s->rf_ccap, 1 << 16);
   int deep = s->rf_deep;
   for (int attempt = 0; attempt < 8; ++attempt) {
@@ -626,10 +734,10 @@ extern "C" SCD_API int scd_refine_witnesses(scd_scene *s, scd_witness *host_out,
   cudaStream_t st = s->stream;
   RfCache &gc = rf_cache(s);
   RfBuffers &B = gc.B;
-  // the halvings of [0, T] down to single ticks, one round to decide them
-  // and one for single ticks that wait for a longer interval
-  int nr = 2;
-  while ((1ll << (nr - 2)) < s->T + 1) ++nr;
+  // the halvings of the longest first interval down to single ticks, one
+  // round to decide them and one for single ticks that wait for a longer
+  // interval
+  int nr = 0;
   unsigned long long h[RF_WORDS], rc_[kRfMaxRounds];
   int rc = rf_run(s, B, &gc, nr, -1, h, rc_);
   if (rc != SCD_OK) return rc;
@@ -639,7 +747,7 @@ extern "C" SCD_API int scd_refine_witnesses(scd_scene *s, scd_witness *host_out,
     ++r;
   }
   if (rounds) *rounds = r;
-  if (h[RF_M] > 0) return SCD_ERR_INTERNAL;  // more rounds than the halvings of [0, T] allow
+  if (h[RF_M] > 0) return SCD_ERR_INTERNAL;  // more rounds than the halvings allow
   if (h[RF_ERR]) return SCD_ERR_KEPLER_NOCONV;
   const int64_t ncand = (int64_t)h[RF_NCAND];
   // distinct tick candidates, then Alg 1's test at each tick
@@ -704,7 +812,8 @@ extern "C" SCD_API int scd_refine_continuous(scd_scene *s, double eps_s, scd_spa
   RfCache &gc = rf_cache(s);
   RfBuffers &B = gc.B;
   unsigned long long h[RF_WORDS], rc_[kRfMaxRounds];
-  int rc = rf_run(s, B, &gc, 0, L, h, rc_);
+  int nr = 0;
+  int rc = rf_run(s, B, &gc, nr, L, h, rc_);
   if (rc != SCD_OK) return rc;
   int r = 0;
   while (r <= L && rc_[r] > 0) {
@@ -750,14 +859,12 @@ extern "C" SCD_API int scd_refine_trace(scd_scene *s, double eps_s, float *lo4, 
                                         int64_t *round_boxes, int *rounds) {
   if (!s || !n_out || cap < 0 || (cap > 0 && (!lo4 || !hi4 || !obj))) return SCD_ERR_INVALID_ARG;
   if (int rc = rf_check_scene(s)) return rc;
-  int nr = 2, L = -1;
+  int nr = 0, L = -1;  // discrete rounds: nr from the first intervals
   if (eps_s > 0.0) {
     const double T_s = (double)s->T * s->tick_s;
     L = 0;
     while (L <= kRfMaxLevels && ldexp(T_s, -L) > eps_s) ++L;
     if (L > kRfMaxLevels) return SCD_ERR_CAPACITY;
-  } else {
-    while ((1ll << (nr - 2)) < s->T + 1) ++nr;
   }
   cudaStream_t st = s->stream;
   RfBuffers B(st);

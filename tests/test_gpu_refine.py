@@ -1,5 +1,6 @@
 """Parity of the CUDA adaptive refinement (scd_refine_witnesses, through the
-C ABI) with the oracle: the witness list is exact (Alg 1's test decides every
+C ABI) with the oracle (its rounds starting from period-bounded intervals,
+as the CUDA rounds do): the witness list is exact (Alg 1's test decides every
 tick candidate), so it must equal the oracle's refinement and Alg 1 witness
 for witness, in Alg 1's order.  The rounds' interval counts come from
 overlap tests of FP32 boxes whose centres agree with the oracle's to 1e-7 km,
@@ -41,7 +42,7 @@ def test_small_large_radii_equal_alg1_and_oracle(scd, seed):
     w, rb = sc.refine_witnesses()
     ref = O.alg1_witnesses(els, T, 1.0)
     assert _tuples(w) == _tuples(ref)
-    ow, orb, _ = O.refine_discrete(els, T, 1.0, O.BOX_SPEED)
+    ow, orb, _ = O.refine_discrete(els, T, 1.0, O.BOX_SPEED, start=O.REFINE_START_PERIOD)
     assert len(rb) <= math.ceil(math.log2(T + 1)) + 2
     assert abs(int(rb.sum()) - int(orb.sum())) <= 0.02 * orb.sum()
     sc.close()
@@ -54,7 +55,7 @@ def test_uniform_512_six_thousand_seconds(scd):
     els[511] = els[7]
     sc = _scene(scd, els, 6000.0)
     w, rb = sc.refine_witnesses()
-    ow, orb, _ = O.refine_discrete(els, 6000, 1.0, O.BOX_SPEED)
+    ow, orb, _ = O.refine_discrete(els, 6000, 1.0, O.BOX_SPEED, start=O.REFINE_START_PERIOD)
     assert _tuples(w) == _tuples(ow)
     mine = w[(w["i"] == 7) & (w["j"] == 511)]
     assert mine["t"].tolist() == list(range(6001))
@@ -64,7 +65,8 @@ def test_uniform_512_six_thousand_seconds(scd):
     # same witnesses (both exact), the oracle's rounds with its INTERVAL boxes
     sc2 = _scene(scd, els, 6000.0, mode=1)
     w2, rb2 = sc2.refine_witnesses()
-    ow2, orb2, _ = O.refine_discrete(els, 6000, 1.0, O.BOX_INTERVAL)
+    ow2, orb2, _ = O.refine_discrete(els, 6000, 1.0, O.BOX_INTERVAL,
+                                     start=O.REFINE_START_PERIOD)
     assert _tuples(w2) == _tuples(w) == _tuples(ow2)
     assert len(rb2) == len(orb2)
     assert abs(int(rb2.sum()) - int(orb2.sum())) <= 0.02 * orb2.sum()
@@ -132,7 +134,7 @@ def test_far_apart_orbits_and_errors(scd):
     assert e.value.status == scd.SCD_ERR_STATE
     sc.build_boxes()
     w, rb = sc.refine_witnesses()
-    _, orb, _ = O.refine_discrete(els, 86400, 1.0, O.BOX_SPEED)
+    _, orb, _ = O.refine_discrete(els, 86400, 1.0, O.BOX_SPEED, start=O.REFINE_START_PERIOD)
     assert len(w) == 0 and rb.tolist() == orb.tolist()
     sc.close()
     # a buffer too small reports the count needed and writes nothing
@@ -208,6 +210,12 @@ def test_every_round_follows_from_its_own_boxes(scd, mode):
     tr = scd.scd_refine_trace(sc.handle)
     w, rb = sc.refine_witnesses()
     assert [len(o) for _, _, o in tr] == rb.tolist()
+    # the first round: every object's ticks cut by its own start length
+    first = []
+    for i in range(len(els)):
+        L = O.refine_start_ticks(els[i], 6000, 1.0)
+        first += [(i, a, min(a + L - 1, 6000)) for a in range(0, 6001, L)]
+    assert _round_intervals(*tr[0]) == sorted(first)
     g = np.random.default_rng(mode)
     for r, (lo, hi, obj) in enumerate(tr):
         want = O.refine_round(lo, hi, obj, False)
