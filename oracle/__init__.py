@@ -81,8 +81,8 @@ def lib():
                 "or_raw_cells_tree": (i64, [vp, vp, vp, i64, vp, i64]),
                 "or_alg3": (i32, [vp, i64, i64, d, i32, i64, vp, vp, vp, vp]),
                 "or_narrow_phase": (i64, [vp, i64, vp, i64, d, vp, vp, vp, vp, i64]),
-                "or_refine_discrete": (i64, [vp, i64, i64, d, i32, i32, vp, i64, vp, vp, vp]),
-                "or_refine_start_ticks": (i64, [vp, i64, d]),
+                "or_refine_discrete": (i64, [vp, i64, i64, d, i32, d, vp, i64, vp, vp, vp]),
+                "or_refine_start_ticks": (i64, [vp, i64, d, d]),
                 "or_refine_continuous": (i64, [vp, i64, d, d, i32, vp, i64, vp, vp]),
                 "or_refine_round": (i64, [vp, vp, vp, i64, i32, vp, vp, vp, i64]),
                 "or_radial_range": (None, [vp, vp]),
@@ -435,20 +435,19 @@ def earliest_witness(wit):
 SPAN_DTYPE = np.dtype([("i", "<u4"), ("j", "<u4"), ("t0", "<f8"), ("t1", "<f8")])
 
 
-REFINE_START_HORIZON, REFINE_START_PERIOD = 0, 1
-
-
-def refine_start_ticks(el, T: int, tick_s: float) -> int:
-    """First-interval length of start rule 1 (ticks): the largest power of
-    two not above max(1, floor(P / (64 tick_s))), or T + 1 when longer."""
-    return int(lib().or_refine_start_ticks(_p(_els([el])), int(T), float(tick_s)))
+def refine_start_ticks(el, T: int, tick_s: float, fraction: float) -> int:
+    """First-interval length (ticks) for the start fraction f: the largest
+    power of two not above max(1, floor(P / (f tick_s))), or T + 1 when
+    longer or f = 0."""
+    return int(lib().or_refine_start_ticks(_p(_els([el])), int(T), float(tick_s),
+                                           float(fraction)))
 
 
 def refine_discrete(els, T: int, tick_s: float, mode: int = BOX_SPEED,
-                    start: int = REFINE_START_HORIZON):
+                    start_fraction: float = 0.0):
     """Adaptive refinement in bulk-synchronous rounds (Alg 5-6 taken top-down
-    over all objects, each starting from [0, T] or, start = 1, from intervals
-    of refine_start_ticks): returns (witnesses in Alg 1's order, active
+    over all objects, each starting from [0, T] (start_fraction 0) or from
+    intervals of refine_start_ticks): returns (witnesses in Alg 1's order, active
     intervals per round, distinct tick candidates)."""
     E = _els(els)
     rb = np.zeros(64, np.int64)
@@ -457,8 +456,8 @@ def refine_discrete(els, T: int, tick_s: float, mode: int = BOX_SPEED,
     cap = 1 << 12
     while True:
         out = np.zeros(cap, WITNESS_DTYPE)
-        k = lib().or_refine_discrete(_p(E), len(E), int(T), float(tick_s), int(mode), int(start),
-                                     _p(out), cap,
+        k = lib().or_refine_discrete(_p(E), len(E), int(T), float(tick_s), int(mode),
+                                     float(start_fraction), _p(out), cap,
                                      _p(rb), ctypes.byref(rounds), ctypes.byref(ntc))
         if k <= cap:
             return out[:k].copy(), rb[:rounds.value].copy(), int(ntc.value)

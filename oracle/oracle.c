@@ -881,7 +881,8 @@ done:
 /* ------------------------------------------------------------------------ */
 /* Adaptive refinement in bulk-synchronous rounds: the interval doubling    */
 /* and halving of Alg 5 and Alg 6 taken top-down over all objects at once. */
-/* Every object starts with one interval, the whole horizon.  In a round   */
+/* Every object starts with the whole horizon, or with it cut into        */
+/* intervals of a bounded length (or_refine_start_ticks).  In a round      */
 /* every active interval gets its 4D box (Def 8); a box that meets no box  */
 /* of another object proves its object collision-free over the interval    */
 /* (every other object's position at those times lies in one of this       */
@@ -911,22 +912,23 @@ static int cmp_witness_alg1(const void *x, const void *y) {
   return 0;
 }
 
-int64_t or_refine_start_ticks(const double *el, int64_t T, double tick_s) {
-  const double q = floor(or_period(el) / (64.0 * tick_s));
+int64_t or_refine_start_ticks(const double *el, int64_t T, double tick_s, double fraction) {
+  if (!(fraction > 0.0)) return T + 1;
+  const double q = floor(or_period(el) / (fraction * tick_s));
   int64_t L = 1;
-  while ((double)(2 * L) <= q) L *= 2;
+  while (L <= T && (double)(2 * L) <= q) L *= 2; /* beyond T the length is T + 1 anyway */
   return L > T ? T + 1 : L;
 }
 
 int64_t or_refine_discrete(const double *els, int64_t n, int64_t T, double tick_s, int mode,
-                           int start, or_witness *out, int64_t cap, int64_t *round_boxes,
-                           int *rounds, int64_t *n_tick_candidates) {
+                           double start_fraction, or_witness *out, int64_t cap,
+                           int64_t *round_boxes, int *rounds, int64_t *n_tick_candidates) {
   int64_t m = 0, scap = 0, ncap = 0, ccap = 0, nc = 0;
   or_seg *S = NULL;
   or_seg *next = NULL;
   or_witness *cand = NULL;
   for (int64_t i = 0; i < n; ++i) {
-    const int64_t L = start ? or_refine_start_ticks(els + 7 * i, T, tick_s) : T + 1;
+    const int64_t L = or_refine_start_ticks(els + 7 * i, T, tick_s, start_fraction);
     for (int64_t t0 = 0; t0 <= T; t0 += L) {
       S = (or_seg *)grow(S, &scap, m + 1, sizeof(or_seg));
       S[m].obj = i;

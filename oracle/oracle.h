@@ -148,20 +148,20 @@ typedef struct { uint32_t i, j; double t0, t1; } or_span;
 /* Rounds over all objects' intervals: a box that meets no other object's
  * box is done, one that meets another is halved (ticks [t0, mid],
  * [mid+1, t1]); two single-tick boxes that meet are a tick candidate.  The
- * first round holds [0, T] for every object (start = 0), or (start = 1)
- * object i's ticks cut into intervals of L_i ticks from tick 0 (the last one
- * clipped at T), L_i the largest power of two not above
- * max(1, floor(P_i / (64 tick_s))) (P_i the period, or_period), or [0, T]
- * when L_i > T: a bounded first interval, as Alg 5's intervals start at
- * one step and grow up to a bound.  Returns the witnesses among the tick
+ * first round holds object i's ticks cut into intervals of L_i ticks from
+ * tick 0 (the last one clipped at T), L_i the largest power of two not
+ * above max(1, floor(P_i / (f tick_s))) for the start fraction f > 0 (P_i
+ * the period, or_period), or [0, T] when L_i > T or f = 0: a bounded first
+ * interval, as Alg 5's intervals start at one step and grow up to a bound.
+ * Returns the witnesses among the tick
  * candidates (Alg 1's test at the tick), in Alg 1's order (t, i, j);
  * round_boxes[r] = active intervals of round r (up to 64 rounds), *rounds
  * the rounds taken, *n_tick_candidates the distinct tick candidates. */
 int64_t or_refine_discrete(const double *els, int64_t n, int64_t T, double tick_s, int mode,
-                           int start, or_witness *out, int64_t cap, int64_t *round_boxes,
-                           int *rounds, int64_t *n_tick_candidates);
-/* the first-interval length L_i of start rule 1, in ticks */
-int64_t or_refine_start_ticks(const double *el, int64_t T, double tick_s);
+                           double start_fraction, or_witness *out, int64_t cap,
+                           int64_t *round_boxes, int *rounds, int64_t *n_tick_candidates);
+/* the first-interval length L_i for the start fraction f, in ticks */
+int64_t or_refine_start_ticks(const double *el, int64_t T, double tick_s, double fraction);
 /* The continuous-time variant (Sec. 4.6): closed real intervals halved
  * down to length <= eps_s, halves sharing their endpoint; every meeting
  * pair of boxes at that level as (i < j, intersection of the intervals),

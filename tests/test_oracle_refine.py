@@ -22,7 +22,7 @@ def _key(w):
     return sorted(map(tuple, np.asarray(w).tolist()))
 
 
-@pytest.mark.parametrize("start", [O.REFINE_START_HORIZON, O.REFINE_START_PERIOD])
+@pytest.mark.parametrize("start", [0.0, 64.0, 256.0])
 @pytest.mark.parametrize("mode", [O.BOX_SPEED, O.BOX_INTERVAL])
 @pytest.mark.parametrize("seed", [300, 302, 310, 311])
 def test_discrete_refinement_equals_alg1(mode, seed, start):
@@ -161,28 +161,35 @@ def test_round_step_reproduces_the_refinement(mode):
 
 
 def test_start_lengths_from_the_period():
-    """Start rule 1: the largest power of two of ticks not above P / 64
-    (P = 2 pi sqrt(a^3 / mu)), at least one tick, the whole horizon when
-    longer; worked by hand for a LEO and a GEO orbit."""
+    """The first-interval length for start fraction f: the largest power of
+    two of ticks not above P / (f tick) (P = 2 pi sqrt(a^3 / mu)), at least
+    one tick, the whole horizon when longer or f = 0; worked by hand for a
+    LEO and a GEO orbit."""
     leo = [7000.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0]   # P = 5828.5 s, P / 64 = 91.1
     geo = [42164.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0]  # P = 86164 s, P / 64 = 1346.3
-    assert O.refine_start_ticks(leo, 86400, 1.0) == 64
-    assert O.refine_start_ticks(geo, 86400, 1.0) == 1024
-    assert O.refine_start_ticks(leo, 86400, 0.5) == 128     # P / 32 = 182.1
-    assert O.refine_start_ticks(leo, 86400, 200.0) == 1     # P / 12800 < 1
-    assert O.refine_start_ticks(leo, 50, 1.0) == 51         # longer than [0, 50]
+    assert O.refine_start_ticks(leo, 86400, 1.0, 64) == 64
+    assert O.refine_start_ticks(geo, 86400, 1.0, 64) == 1024
+    assert O.refine_start_ticks(leo, 86400, 0.5, 64) == 128    # P / 32 = 182.1
+    assert O.refine_start_ticks(leo, 86400, 200.0, 64) == 1    # P / 12800 < 1
+    assert O.refine_start_ticks(leo, 50, 1.0, 64) == 51        # longer than [0, 50]
+    assert O.refine_start_ticks(leo, 86400, 1.0, 256) == 16    # P / 256 = 22.8
+    assert O.refine_start_ticks(geo, 86400, 1.0, 128) == 512   # P / 128 = 673.2
+    assert O.refine_start_ticks(leo, 86400, 1.0, 0) == 86401   # the whole horizon
+    assert O.refine_start_ticks(leo, 86400, 1.0, 1e-30) == 86401
     # the first round: ceil(3001 / 64) + ceil(3001 / 1024) intervals
-    _, rb, _ = O.refine_discrete(np.array([leo, geo]), 3000, 1.0, O.BOX_SPEED,
-                                 O.REFINE_START_PERIOD)
+    _, rb, _ = O.refine_discrete(np.array([leo, geo]), 3000, 1.0, O.BOX_SPEED, 64.0)
     assert rb[0] == 47 + 3
+    # and ceil(3001 / 16) + ceil(3001 / 256)
+    _, rb, _ = O.refine_discrete(np.array([leo, geo]), 3000, 1.0, O.BOX_SPEED, 256.0)
+    assert rb[0] == 188 + 12
 
 
 @pytest.mark.parametrize("mode", [O.BOX_SPEED, O.BOX_INTERVAL])
 def test_both_starts_give_the_same_witnesses_on_a_crowded_shell(mode):
     els = P.uniform_leo(24, seed=101, radius_km=300.0)
     T = 400
-    w0, rb0, _ = O.refine_discrete(els, T, 1.0, mode, O.REFINE_START_HORIZON)
-    w1, rb1, _ = O.refine_discrete(els, T, 1.0, mode, O.REFINE_START_PERIOD)
+    w0, rb0, _ = O.refine_discrete(els, T, 1.0, mode, 0.0)
+    w1, rb1, _ = O.refine_discrete(els, T, 1.0, mode, 64.0)
     assert w0.tolist() == w1.tolist() == O.alg1_witnesses(els, T, 1.0).tolist()
     assert len(w1) > 0
     # starting from intervals of 64 ticks skips the rounds in which nearly
