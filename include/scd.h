@@ -161,6 +161,12 @@ typedef struct {
                          screens apply it with 10- or 12-bit Morton axes
                          (ignored with 8 or 16), decomposed screens and
                          batches always.                                   */
+  float refine_start; /* adaptive refinement: the first intervals of object i
+                         are L_i ticks long, L_i the largest power of two
+                         not above max(1, floor(P_i / (refine_start tick))),
+                         P_i its Kepler period; 0: the whole horizon
+                         [0, T].  >= 0 and finite (default 256; 128 in a
+                         scene of INTERVAL boxes)                          */
 } scd_tuning;
 
 typedef struct scd_scene scd_scene;
@@ -192,8 +198,8 @@ SCD_API int scd_set_allocator(void *(*alloc_fn)(size_t bytes, void *stream, void
 /* Create a scene of n objects (Defs 1, 5-6).  elems: host array of n
  * elements, copied.  horizon_s / tick_s must be a whole number of ticks.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).  The scene's
- * tuning starts as scd_default_tuning, with space_warp = 1 and time_scale =
- * 16 for INTERVAL boxes (measured best for them).
+ * tuning starts as scd_default_tuning, with space_warp = 1, time_scale =
+ * 16 and refine_start = 128 for INTERVAL boxes (measured best for them).
  * Errors: INVALID_ARG (n <= 0, a <= 0, e outside [0, 1), radius < 0, a NaN,
  * horizon or tick <= 0 or not commensurate, bad policy), OOM, CUDA. */
 SCD_API int scd_scene_create(const scd_element *elems, int64_t n, double horizon_s,
@@ -278,8 +284,9 @@ SCD_API int scd_narrow_phase(scd_scene *s, const scd_pair *d_pairs, int64_t n_pa
  * as data-parallel rounds over all of the scene's objects.  Object i
  * starts with its ticks 0..T cut into intervals of L_i ticks (the last one
  * shorter): L_i is the largest power of two not above
- * max(1, floor(P_i / (64 tick))), P_i its Kepler period, or T + 1 when that
- * is longer.  Each round builds the 4D box (Def 8, in the scene's
+ * max(1, floor(P_i / (f tick))), P_i its Kepler period and f the scene's
+ * tuning refine_start, or T + 1 when that is longer or f = 0.  Each round
+ * builds the 4D box (Def 8, in the scene's
  * box mode: SPEED or INTERVAL) of every active interval; an interval
  * whose box meets no other object's box is proven collision-free and
  * dropped, one that meets another is halved (ticks [t0, mid], [mid+1, t1]),

@@ -59,7 +59,8 @@ class scd_tuning(ctypes.Structure):
                 ("block_threads", ctypes.c_int), ("morton_bits", ctypes.c_int),
                 ("time_scale", ctypes.c_float), ("use_graph", ctypes.c_int),
                 ("space_warp", ctypes.c_int), ("nodes_per_step", ctypes.c_int),
-                ("node_width", ctypes.c_int), ("split_km", ctypes.c_float)]
+                ("node_width", ctypes.c_int), ("split_km", ctypes.c_float),
+                ("refine_start", ctypes.c_float)]
 
 
 class scd_witness(ctypes.Structure):

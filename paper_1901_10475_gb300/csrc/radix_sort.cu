@@ -42,6 +42,8 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const K *__restrict__
                                                            uint32_t *__restrict__ ocounts = nullptr,
                                                            unsigned long long tmask = 0) {
   n = sort_count(n, d_n);
+  // past a device count: no counts (the scan and the scatter stop there)
+  if (d_n && (int64_t)blockIdx.x * kRsTile >= n) return;
   __shared__ uint32_t wh[kRsWarps][256];
   __shared__ uint32_t wo[kOpen ? kRsWarps : 1][256];
   int w = threadIdx.x >> 5;
@@ -85,9 +87,14 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_upsweep(const K *__restrict__
 // the warp in registers; one block-wide scan of the warp totals per chunk.
 constexpr int kScanItems = 8;
 __global__ void __launch_bounds__(1024) k_rs_scan(uint32_t *__restrict__ counts, int64_t nblk,
-                                                  uint32_t *__restrict__ totals) {
+                                                  uint32_t *__restrict__ totals,
+                                                  const unsigned long long *__restrict__ d_n =
+                                                      nullptr,
+                                                  int64_t n = 0) {
   __shared__ uint32_t ws[32];
-  uint32_t *c = counts + (int64_t)blockIdx.x * nblk;
+  uint32_t *c = counts + (int64_t)blockIdx.x * nblk;  // rows of nblk
+  // with a device count, only the blocks that hold items counted
+  if (d_n) nblk = std::min<int64_t>(nblk, (sort_count(n, d_n) + kRsTile - 1) / kRsTile);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t carry = 0;
   for (int64_t b0 = 0; b0 < nblk; b0 += 1024 * kScanItems) {
@@ -471,8 +478,8 @@ static int rs_impl(K *keys, uint32_t *vals, int64_t n, const unsigned long long 
       const unsigned long long tmask = (1ull << pe->tb) - 1ull;
       k_rs_upsweep<unsigned long long, true><<<(unsigned)nblk, kRsThreads, 0, st>>>(
           (const unsigned long long *)ka, n, d_n, shift, counts, nblk, ocounts, tmask);
-      k_rs_scan<<<256, 1024, 0, st>>>(counts, nblk, totals);
-      k_rs_scan<<<256, 1024, 0, st>>>(ocounts, nblk, ototals);
+      k_rs_scan<<<256, 1024, 0, st>>>(counts, nblk, totals, d_n, n);
+      k_rs_scan<<<256, 1024, 0, st>>>(ocounts, nblk, ototals, d_n, n);
       k_rs_downsweep<unsigned long long, false, true><<<grid, kRsThreads, smem, st>>>(
           (const unsigned long long *)ka, nullptr, nullptr, nullptr, n, d_n, shift, counts,
           totals, nblk, sc.err, 0, ocounts, ototals, *pe);
@@ -480,7 +487,7 @@ static int rs_impl(K *keys, uint32_t *vals, int64_t n, const unsigned long long 
       return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
     }
     k_rs_upsweep<K><<<(unsigned)nblk, kRsThreads, 0, st>>>(ka, n, d_n, shift, counts, nblk);
-    k_rs_scan<<<256, 1024, 0, st>>>(counts, nblk, totals);
+    k_rs_scan<<<256, 1024, 0, st>>>(counts, nblk, totals, d_n, n);
     if (vals)
       k_rs_downsweep<K, true><<<grid, kRsThreads, smem, st>>>(ka, va, kb, vb, n, d_n, shift,
                                                                counts, totals, nblk, sc.err);

@@ -3,12 +3,14 @@
 //
 // Object i starts with its ticks [0, T] cut into intervals of L_i ticks
 // (the last one shorter), L_i the largest power of two not above
-// max(1, floor(P_i / (64 tick))), P_i its period, or the whole horizon when
-// that is longer: Alg 5 grows an interval from one step up to a bound, and a
-// box over more than about a 64th of an orbit meets nearly every other box
-// of a crowded catalog, so the rounds with longer intervals would split
-// nearly everything at full cost and decide nothing.  A round builds the 4D box of every active interval (Def 8, in the scene's box
-// mode), finds the boxes that meet a box of another object, and then
+// max(1, floor(P_i / (f tick))), P_i its period and f the scene's start
+// fraction, or the whole horizon when that is longer or f = 0: Alg 5 grows
+// an interval from one step up to a bound, and a box over more than a few
+// hundredths of an orbit meets nearly every other box of a crowded catalog,
+// so the rounds with longer intervals would halve nearly everything at full
+// cost and decide nothing.  A round builds the 4D box of every active
+// interval (Def 8, in the scene's box mode), finds the boxes that meet a
+// box of another object, and then
 //   - drops an interval whose box meets none: its object is proven free of
 //     collisions over it (every other object's position at those times lies
 //     in one of this round's boxes, or was proven free in an earlier round);
@@ -75,61 +77,55 @@ __device__ __forceinline__ int64_t rf_count(const unsigned long long *state, int
   return m < (unsigned long long)cap ? (int64_t)m : cap;
 }
 
-// The first interval length of object o in ticks: the largest power of
-// two not above max(1, floor(P / (64 tick))), or T + 1 when longer (a
-// bounded first interval: Alg 5's intervals start at one step and grow up to
-// a bound; the rounds before, in which nearly every box meets every other,
-// are skipped).  The division is rounded as the oracle's.
-__device__ __forceinline__ int32_t rf_start_ticks(const ObjParams &p, int32_t T, double tick_s) {
-  const double q = floor(__ddiv_rn(p.P, 64.0 * tick_s));
+// The first interval length of an object in ticks: the largest power of
+// two not above max(1, floor(P / unit)), unit = f tick for the start
+// fraction f, or T + 1 when longer or f = 0 (a bounded first interval:
+// Alg 5's intervals grow from one step up to a bound; the rounds before, in
+// which nearly every box meets another, are skipped).  The division is
+// rounded as the oracle's.
+__device__ __forceinline__ int32_t rf_start_ticks(const ObjParams &p, int32_t T, double unit) {
+  if (!(unit > 0.0)) return T + 1;
+  const double q = floor(__ddiv_rn(p.P, unit));
   int64_t L = 1;
   while (L <= T && (double)(2 * L) <= q) L *= 2;  // past T the answer is T + 1
   return L > T ? T + 1 : (int32_t)L;
 }
 
-// the object whose run of first intervals holds interval i: the largest o
-// with off[o] <= i
-__device__ __forceinline__ int64_t rf_owner(const int64_t *__restrict__ off, int64_t n,
-                                            int64_t i) {
-  int64_t lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if (__ldg(off + mid) <= i) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 // per object its first round's intervals, and the longest first interval
 __global__ void k_rf_start_count(const ObjParams *__restrict__ par, int64_t n, int32_t T,
-                                 double tick_s, int64_t *__restrict__ cnt,
+                                 double unit, int64_t *__restrict__ cnt,
                                  unsigned long long *__restrict__ state) {
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= n) return;
-  const int32_t L = rf_start_ticks(par[o], T, tick_s);
+  const int32_t L = rf_start_ticks(par[o], T, unit);
   cnt[o] = ((int64_t)T + L) / L;  // ceil((T + 1) / L)
   atomicMax(&state[RF_LMAX], (unsigned long long)L);
 }
 
-// The first round's intervals, object-major: [k L, min((k + 1) L - 1, T)];
-// at most cap of them written, the count asked for noted for the retry.
+// The first round's intervals, object-major: [k L, min((k + 1) L - 1, T)],
+// one warp per object; at most cap of them written, the count asked for
+// noted for the retry.
 __global__ void k_rf_init_start(const ObjParams *__restrict__ par, int64_t n, int32_t T,
-                                double tick_s, const int64_t *__restrict__ off, int64_t cap,
+                                double unit, const int64_t *__restrict__ off, int64_t cap,
                                 uint32_t *obj, int32_t *t0, int32_t *t1,
                                 unsigned long long *state) {
   const int64_t total = off[n];
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     state[RF_M] = (unsigned long long)(total < cap ? total : cap);
     if (total > cap) atomicMax(&state[RF_OVER], (unsigned long long)total);
   }
-  if (i >= total || i >= cap) return;
-  const int64_t o = rf_owner(off, n, i);
-  const int32_t L = rf_start_ticks(par[o], T, tick_s);
-  const int64_t a = (i - off[o]) * L;
-  const int64_t b = a + L - 1;
-  obj[i] = (uint32_t)o;
-  t0[i] = (int32_t)a;
-  t1[i] = (int32_t)(b < T ? b : T);
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; o < n; o += nw) {
+    const int64_t L = rf_start_ticks(par[o], T, unit);
+    const int64_t b0 = off[o], c = off[o + 1] - b0;
+    for (int64_t k = lane; k < c && b0 + k < cap; k += 32) {
+      const int64_t a = k * L, b = a + L - 1;
+      obj[b0 + k] = (uint32_t)o;
+      t0[b0 + k] = (int32_t)a;
+      t1[b0 + k] = (int32_t)(b < T ? b : T);
+    }
+  }
 }
 
 __global__ void k_rf_init(int64_t n, int32_t T, uint32_t *obj, int32_t *t0, int32_t *t1,
@@ -160,11 +156,8 @@ struct RfBoxArgs {
   unsigned long long *err;
 };
 
-__global__ void __launch_bounds__(kRfThreads) k_rf_boxes(RfBoxArgs a) {
-  const int64_t M = rf_count(a.state, a.cap);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) *a.round_count = (unsigned long long)M;
-  if (i >= M) return;
+// the box, Morton key and index of interval i
+__device__ __forceinline__ void rf_box(const RfBoxArgs &a, int64_t i) {
   const ObjParams &p = a.par[a.obj[i]];
   const int32_t t0 = a.t0[i], t1 = a.t1[i];
   double lo[3], hi[3];
@@ -190,6 +183,13 @@ __global__ void __launch_bounds__(kRfThreads) k_rf_boxes(RfBoxArgs a) {
   a.idx[i] = (uint32_t)i;
 }
 
+__global__ void __launch_bounds__(kRfThreads) k_rf_boxes(RfBoxArgs a) {
+  const int64_t M = rf_count(a.state, a.cap);
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i0 == 0) *a.round_count = (unsigned long long)M;
+  for (int64_t i = i0; i < M; i += (int64_t)gridDim.x * blockDim.x) rf_box(a, i);
+}
+
 // the sorted boxes (32-byte records) and their objects
 __global__ void __launch_bounds__(kRfThreads) k_rf_gather(const uint32_t *__restrict__ idx,
                                                           const float4 *__restrict__ lo,
@@ -199,12 +199,32 @@ __global__ void __launch_bounds__(kRfThreads) k_rf_gather(const uint32_t *__rest
                                                           const unsigned long long *state,
                                                           SBox *sbox, uint32_t *sobj) {
   const int64_t M = rf_count(state, cap);
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= M) return;
-  const uint32_t i = idx[p];
-  sbox[p].lo = lo[i];
-  sbox[p].hi = hi[i];
-  sobj[p] = obj[i];
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < M;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = idx[p];
+    sbox[p].lo = lo[i];
+    sbox[p].hi = hi[i];
+    sobj[p] = obj[i];
+  }
+}
+
+// Slots for `need` next-round intervals of each lane of a warp: one atomic
+// on the next-round count per warp (the lanes' slots follow one another).
+// Every lane of the warp calls it.
+__device__ __forceinline__ unsigned long long rf_claim(unsigned long long *nnext,
+                                                       uint32_t need) {
+  const int lane = threadIdx.x & 31;
+  uint32_t incl = need;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned long long base = 0;
+  if (lane == 31 && total) base = atomicAdd(nnext, (unsigned long long)total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return base + (incl - need);
 }
 
 // next round's intervals (order is free: appended by atomics); entries past
@@ -217,27 +237,36 @@ __global__ void __launch_bounds__(kRfThreads) k_rf_split(const uint32_t *__restr
                                                          int32_t *nt0, int32_t *nt1,
                                                          unsigned long long *state) {
   const int64_t M = rf_count(state, cap);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
-  const uint32_t f = flags[i];
-  if (!(f & kRfHit)) return;  // proven free of collisions over [t0, t1]
-  const int32_t a0 = t0[i], a1 = t1[i];
-  if (a1 > a0) {
-    const unsigned long long q = atomicAdd(&state[RF_NNEXT], 2ull);
-    if (q + 2 > (unsigned long long)cap) return;
-    const int32_t mid = a0 + (a1 - a0) / 2;
-    nobj[q] = obj[i];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // whole warps walk the intervals (rf_claim needs every lane)
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < M;
+       base += stride) {
+    const int64_t i = base + (threadIdx.x & 31);
+    uint32_t need = 0, o = 0;
+    int32_t a0 = 0, a1 = 0;
+    if (i < M) {
+      const uint32_t f = flags[i];
+      if (f & kRfHit) {  // else proven free of collisions over [t0, t1]
+        a0 = t0[i];
+        a1 = t1[i];
+        o = obj[i];
+        // halved, or a single tick waiting for the longer intervals it meets
+        need = a1 > a0 ? 2u : ((f & kRfHitLong) ? 1u : 0u);
+      }
+    }
+    const unsigned long long q = rf_claim(&state[RF_NNEXT], need);
+    // every slot below the capacity is written, also by the lane whose two
+    // slots straddle it: a round cut short still reads all of its intervals
+    if (need == 0 || q >= (unsigned long long)cap) continue;
+    const int32_t mid = need == 2 ? a0 + (a1 - a0) / 2 : a1;
+    nobj[q] = o;
     nt0[q] = a0;
     nt1[q] = mid;
-    nobj[q + 1] = obj[i];
-    nt0[q + 1] = mid + 1;
-    nt1[q + 1] = a1;
-  } else if (f & kRfHitLong) {  // wait for the longer intervals it meets
-    const unsigned long long q = atomicAdd(&state[RF_NNEXT], 1ull);
-    if (q + 1 > (unsigned long long)cap) return;
-    nobj[q] = obj[i];
-    nt0[q] = a0;
-    nt1[q] = a1;
+    if (need == 2 && q + 1 < (unsigned long long)cap) {
+      nobj[q + 1] = o;
+      nt0[q + 1] = mid + 1;
+      nt1[q + 1] = a1;
+    }
   }
 }
 
@@ -250,17 +279,23 @@ __global__ void __launch_bounds__(kRfThreads) k_rf_split_cont(const uint32_t *__
                                                               int32_t *nt0, int32_t *nt1,
                                                               unsigned long long *state) {
   const int64_t M = rf_count(state, cap);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M || !(flags[i] & kRfHit)) return;
-  const unsigned long long q = atomicAdd(&state[RF_NNEXT], 2ull);
-  if (q + 2 > (unsigned long long)cap) return;
-  const int32_t k = t0[i];
-  nobj[q] = obj[i];
-  nt0[q] = 2 * k;
-  nt1[q] = 2 * k + 1;
-  nobj[q + 1] = obj[i];
-  nt0[q + 1] = 2 * k + 1;
-  nt1[q + 1] = 2 * k + 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < M;
+       base += stride) {
+    const int64_t i = base + (threadIdx.x & 31);
+    const uint32_t need = (i < M && (flags[i] & kRfHit)) ? 2u : 0u;
+    const unsigned long long q = rf_claim(&state[RF_NNEXT], need);
+    if (need == 0 || q >= (unsigned long long)cap) continue;  // (slots below cap all written)
+    const int32_t k = t0[i];
+    nobj[q] = obj[i];
+    nt0[q] = 2 * k;
+    nt1[q] = 2 * k + 1;
+    if (q + 1 < (unsigned long long)cap) {
+      nobj[q + 1] = obj[i];
+      nt0[q + 1] = 2 * k + 1;
+      nt1[q + 1] = 2 * k + 2;
+    }
+  }
 }
 
 // a copy of round r's boxes and objects after those of the rounds before it
@@ -274,14 +309,15 @@ __global__ void __launch_bounds__(kRfThreads) k_rf_trace(const float4 *__restric
                                                          float4 *tlo, float4 *thi,
                                                          uint32_t *tobj, int64_t tcap) {
   const int64_t M = rf_count(state, cap);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= M) return;
   unsigned long long off = 0;
   for (int q = 0; q < r; ++q) off += rounds[q];
   if (off + (unsigned long long)M > (unsigned long long)tcap) return;
-  tlo[off + i] = lo[i];
-  thi[off + i] = hi[i];
-  tobj[off + i] = obj[i];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    tlo[off + i] = lo[i];
+    thi[off + i] = hi[i];
+    tobj[off + i] = obj[i];
+  }
 }
 
 // the next round's count becomes the current one (at most the capacity; the
@@ -411,12 +447,32 @@ struct RfBuffers {
 
 static unsigned grid_of(int64_t n) { return (unsigned)((n + kRfThreads - 1) / kRfThreads); }
 
+// the grid of a round kernel over up to n items: the blocks that are
+// resident at once, or fewer (its threads loop over the round's count, read
+// on the device, so an almost empty round costs one short wave)
+static unsigned wave_of(int64_t n) {
+  static int wave = 0;
+  if (!wave) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    wave = std::max(1, sms) * (2048 / kRfThreads);
+  }
+  return std::min<unsigned>(grid_of(std::max<int64_t>(n, 1)), (unsigned)wave);
+}
+
 static int rf_read_state(RfBuffers &B, unsigned long long h[RF_WORDS]) {
   if (cudaMemcpyAsync(h, B.state.p, sizeof(unsigned long long) * RF_WORDS, cudaMemcpyDeviceToHost,
                       B.st) != cudaSuccess ||
       cudaStreamSynchronize(B.st) != cudaSuccess)
     return SCD_ERR_CUDA;
   return SCD_OK;
+}
+
+// the unit of rf_start_ticks: the scene's start fraction of a period times
+// the tick [s], 0 for whole-horizon first intervals
+static double rf_start_unit(const scd_scene *s) {
+  return s->tune.refine_start > 0.0f ? (double)s->tune.refine_start * s->tick_s : 0.0;
 }
 
 // The first intervals of the discrete rounds (rf_start_ticks): their counts
@@ -429,8 +485,8 @@ static int rf_start(scd_scene *s, RfBuffers &B, int &rounds) {
   if (cudaMemsetAsync(B.state.p, 0, sizeof(unsigned long long) * RF_WORDS, st) != cudaSuccess)
     return SCD_ERR_CUDA;
   if (n > 0) {
-    k_rf_start_count<<<grid_of(n), kRfThreads, 0, st>>>(s->d_par.p, n, (int32_t)s->T, s->tick_s,
-                                                        B.scnt.p, B.state.p);
+    k_rf_start_count<<<grid_of(n), kRfThreads, 0, st>>>(s->d_par.p, n, (int32_t)s->T,
+                                                        rf_start_unit(s), B.scnt.p, B.state.p);
     note_launch();
   }
   int rc = scan_exclusive_i64(B.scnt.p, B.soff.p, n, B.stmp, st);
@@ -472,9 +528,10 @@ static int rf_queue(scd_scene *s, RfBuffers &B, int64_t cap, int64_t ccap, int d
     k_rf_init<<<grid_of(n), kRfThreads, 0, st>>>(n, 1, B.obj[0].p, B.t0[0].p, B.t1[0].p,
                                                   B.state.p);
   else
-    k_rf_init_start<<<grid_of(cap), kRfThreads, 0, st>>>(s->d_par.p, n, (int32_t)s->T, s->tick_s,
-                                                          B.soff.p, cap, B.obj[0].p, B.t0[0].p,
-                                                          B.t1[0].p, B.state.p);
+    k_rf_init_start<<<wave_of(32 * n), kRfThreads, 0, st>>>(s->d_par.p, n, (int32_t)s->T,
+                                                             rf_start_unit(s), B.soff.p, cap,
+                                                             B.obj[0].p, B.t0[0].p, B.t1[0].p,
+                                                             B.state.p);
   note_launch();
   const float split = split_of(s->tune);
   const int kb = 4 * kRfMortonBits + (split != 0.0f);
@@ -489,17 +546,17 @@ static int rf_queue(scd_scene *s, RfBuffers &B, int64_t cap, int64_t ccap, int d
     RfBoxArgs ba{s->d_par.p, s->box_mode, B.obj[cur].p, B.t0[cur].p, B.t1[cur].p, cap,
                  B.state.p, B.rounds.p + r, unit, B.ctr.p, Tf, split, B.lo.p, B.hi.p,
                  B.key.p, B.idx.p, B.state.p + RF_ERR};
-    k_rf_boxes<<<grid_of(cap), kRfThreads, 0, st>>>(ba);
+    k_rf_boxes<<<wave_of(cap), kRfThreads, 0, st>>>(ba);
     note_launch();
     if (B.tcap > 0) {
-      k_rf_trace<<<grid_of(cap), kRfThreads, 0, st>>>(B.lo.p, B.hi.p, B.obj[cur].p, cap, B.state.p,
+      k_rf_trace<<<wave_of(cap), kRfThreads, 0, st>>>(B.lo.p, B.hi.p, B.obj[cur].p, cap, B.state.p,
                                                      B.rounds.p, r, B.tlo.p, B.thi.p, B.tobj.p,
                                                      B.tcap);
       note_launch();
     }
     int rc = radix_sort_u64_dev(B.key.p, B.idx.p, cap, dM, 0, kb, B.sc, st);
     if (rc != SCD_OK) return rc;
-    k_rf_gather<<<grid_of(cap), kRfThreads, 0, st>>>(B.idx.p, B.lo.p, B.hi.p, B.obj[cur].p, cap,
+    k_rf_gather<<<wave_of(cap), kRfThreads, 0, st>>>(B.idx.p, B.lo.p, B.hi.p, B.obj[cur].p, cap,
                                                      B.state.p, B.sbox.p, B.sobj.p);
     note_launch();
     rc = build_round_tree(B.key.p, B.sbox.p, cap, dM, B.nodes.p, B.parent_int.p,
@@ -518,11 +575,11 @@ static int rf_queue(scd_scene *s, RfBuffers &B, int64_t cap, int64_t ccap, int d
     if (rc != SCD_OK) return rc;
     if (spans) break;
     if (cont)
-      k_rf_split_cont<<<grid_of(cap), kRfThreads, 0, st>>>(B.obj[cur].p, B.t0[cur].p, B.flags.p,
+      k_rf_split_cont<<<wave_of(cap), kRfThreads, 0, st>>>(B.obj[cur].p, B.t0[cur].p, B.flags.p,
                                                           cap, B.obj[nx].p, B.t0[nx].p,
                                                           B.t1[nx].p, B.state.p);
     else
-      k_rf_split<<<grid_of(cap), kRfThreads, 0, st>>>(B.obj[cur].p, B.t0[cur].p, B.t1[cur].p,
+      k_rf_split<<<wave_of(cap), kRfThreads, 0, st>>>(B.obj[cur].p, B.t0[cur].p, B.t1[cur].p,
                                                      B.flags.p, cap, B.obj[nx].p, B.t0[nx].p,
                                                      B.t1[nx].p, B.state.p);
     k_rf_advance<<<1, 1, 0, st>>>(B.state.p, cap);
@@ -552,7 +609,7 @@ struct RfCache {
   cudaStream_t gst = nullptr;
   cudaEvent_t in = nullptr, out = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int64_t key[10] = {};
+  int64_t key[11] = {};
   unsigned long long nlaunch = 0;  // kernels in the graph
   explicit RfCache(cudaStream_t st) : B(st) {}
   ~RfCache() {
@@ -567,7 +624,7 @@ struct RfCache {
 };
 
 static void rf_key(const scd_scene *s, const RfBuffers &B, int64_t cap, int64_t ccap, int deep,
-                   int rounds, int levels, int64_t k[10]) {
+                   int rounds, int levels, int64_t k[11]) {
   k[0] = cap;
   k[1] = ccap;
   k[2] = deep;
@@ -580,6 +637,7 @@ static void rf_key(const scd_scene *s, const RfBuffers &B, int64_t cap, int64_t 
   int64_t tb;
   memcpy(&tb, &s->tick_s, sizeof(tb));
   k[9] = tb;
+  k[10] = (int64_t)(rf_start_unit(s) * 1e6);  // baked into the first round's launch
 }
 
 // queue the rounds: by the cached graph when its shape matches, else
@@ -587,7 +645,7 @@ static void rf_key(const scd_scene *s, const RfBuffers &B, int64_t cap, int64_t 
 static int rf_rounds(scd_scene *s, RfBuffers &B, RfCache *gc, int64_t cap, int64_t ccap,
                      int deep, int rounds, int levels, unsigned long long h[RF_WORDS],
                      unsigned long long *round_counts, unsigned int &trav_flags) {
-  int64_t k[10];
+  int64_t k[11];
   rf_key(s, B, cap, ccap, deep, rounds, levels, k);
   if (gc && gc->exec && memcmp(k, gc->key, sizeof(k)) == 0) {
     if (cudaEventRecord(gc->in, B.st) != cudaSuccess ||
@@ -692,7 +750,7 @@ static int rf_run(scd_scene *s, RfBuffers &B, RfCache *gc, int &rounds, int leve
       s->rf_ccap = ccap;
       s->rf_deep = deep;
       if (gc) {
-        int64_t k[10];
+        int64_t k[11];
         rf_key(s, B, cap, ccap, deep, rounds, levels, k);
         if (!gc->exec || memcmp(k, gc->key, sizeof(k)) != 0)
           rf_capture(s, *gc, cap, ccap, deep, rounds, levels);

@@ -1,6 +1,6 @@
 """Parity of the CUDA adaptive refinement (scd_refine_witnesses, through the
-C ABI) with the oracle (its rounds starting from period-bounded intervals,
-as the CUDA rounds do): the witness list is exact (Alg 1's test decides every
+C ABI) with the oracle (its rounds starting from the scene's period-bounded
+first intervals, as the CUDA rounds do): the witness list is exact (Alg 1's test decides every
 tick candidate), so it must equal the oracle's refinement and Alg 1 witness
 for witness, in Alg 1's order.  The rounds' interval counts come from
 overlap tests of FP32 boxes whose centres agree with the oracle's to 1e-7 km,
@@ -30,6 +30,11 @@ def _scene(scd, els, horizon_s, mode=0):
     return scd.Scene(els, horizon_s, 1.0, step=step, mode=mode).build_boxes()
 
 
+def _f(sc):
+    """the scene's refinement start fraction (the oracle takes the same)"""
+    return float(sc.tuning()["refine_start"])
+
+
 def _tuples(w):
     return [(int(a), int(b), int(c)) for a, b, c in w.tolist()]
 
@@ -42,7 +47,7 @@ def test_small_large_radii_equal_alg1_and_oracle(scd, seed):
     w, rb = sc.refine_witnesses()
     ref = O.alg1_witnesses(els, T, 1.0)
     assert _tuples(w) == _tuples(ref)
-    ow, orb, _ = O.refine_discrete(els, T, 1.0, O.BOX_SPEED, start=O.REFINE_START_PERIOD)
+    ow, orb, _ = O.refine_discrete(els, T, 1.0, O.BOX_SPEED, start_fraction=_f(sc))
     assert len(rb) <= math.ceil(math.log2(T + 1)) + 2
     assert abs(int(rb.sum()) - int(orb.sum())) <= 0.02 * orb.sum()
     sc.close()
@@ -55,7 +60,7 @@ def test_uniform_512_six_thousand_seconds(scd):
     els[511] = els[7]
     sc = _scene(scd, els, 6000.0)
     w, rb = sc.refine_witnesses()
-    ow, orb, _ = O.refine_discrete(els, 6000, 1.0, O.BOX_SPEED, start=O.REFINE_START_PERIOD)
+    ow, orb, _ = O.refine_discrete(els, 6000, 1.0, O.BOX_SPEED, start_fraction=_f(sc))
     assert _tuples(w) == _tuples(ow)
     mine = w[(w["i"] == 7) & (w["j"] == 511)]
     assert mine["t"].tolist() == list(range(6001))
@@ -65,8 +70,7 @@ def test_uniform_512_six_thousand_seconds(scd):
     # same witnesses (both exact), the oracle's rounds with its INTERVAL boxes
     sc2 = _scene(scd, els, 6000.0, mode=1)
     w2, rb2 = sc2.refine_witnesses()
-    ow2, orb2, _ = O.refine_discrete(els, 6000, 1.0, O.BOX_INTERVAL,
-                                     start=O.REFINE_START_PERIOD)
+    ow2, orb2, _ = O.refine_discrete(els, 6000, 1.0, O.BOX_INTERVAL, start_fraction=_f(sc2))
     assert _tuples(w2) == _tuples(w) == _tuples(ow2)
     assert len(rb2) == len(orb2)
     assert abs(int(rb2.sum()) - int(orb2.sum())) <= 0.02 * orb2.sum()
@@ -124,6 +128,27 @@ def test_catalog_mixture_crossings(scd):
     sc2.close()
 
 
+@pytest.mark.parametrize("frac", [0.0, 32.0, 1024.0])
+def test_start_fraction_follows_the_tuning(scd, frac):
+    """Another start fraction on a scene whose rounds were captured with the
+    default: the first round holds exactly the oracle's first intervals for
+    that fraction, and the witnesses stay Alg 1's."""
+    els = P.uniform_leo(10, seed=311, radius_km=400.0)
+    T = 300
+    sc = _scene(scd, els, float(T))
+    sc.refine_witnesses()
+    sc.refine_witnesses()
+    sc.set_tuning(dict(sc.tuning(), refine_start=frac))
+    w, rb = sc.refine_witnesses()
+    ow, orb, _ = O.refine_discrete(els, T, 1.0, O.BOX_SPEED, start_fraction=frac)
+    assert _tuples(w) == _tuples(ow) == _tuples(O.alg1_witnesses(els, T, 1.0))
+    assert rb[0] == orb[0]
+    assert abs(int(rb.sum()) - int(orb.sum())) <= 0.02 * orb.sum()
+    with pytest.raises(scd.ScdError):
+        sc.set_tuning(dict(sc.tuning(), refine_start=-1.0))
+    sc.close()
+
+
 def test_far_apart_orbits_and_errors(scd):
     els = np.array([[7000.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0],
                     [42164.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.0]])
@@ -134,7 +159,7 @@ def test_far_apart_orbits_and_errors(scd):
     assert e.value.status == scd.SCD_ERR_STATE
     sc.build_boxes()
     w, rb = sc.refine_witnesses()
-    _, orb, _ = O.refine_discrete(els, 86400, 1.0, O.BOX_SPEED, start=O.REFINE_START_PERIOD)
+    _, orb, _ = O.refine_discrete(els, 86400, 1.0, O.BOX_SPEED, start_fraction=_f(sc))
     assert len(w) == 0 and rb.tolist() == orb.tolist()
     sc.close()
     # a buffer too small reports the count needed and writes nothing
@@ -213,7 +238,7 @@ def test_every_round_follows_from_its_own_boxes(scd, mode):
     # the first round: every object's ticks cut by its own start length
     first = []
     for i in range(len(els)):
-        L = O.refine_start_ticks(els[i], 6000, 1.0)
+        L = O.refine_start_ticks(els[i], 6000, 1.0, _f(sc))
         first += [(i, a, min(a + L - 1, 6000)) for a in range(0, 6001, L)]
     assert _round_intervals(*tr[0]) == sorted(first)
     g = np.random.default_rng(mode)
