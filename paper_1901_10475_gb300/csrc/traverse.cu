@@ -974,6 +974,52 @@ static int unpack(scd_scene *s, UnpackArgs a, cudaStream_t st) {
   return SCD_OK;
 }
 
+// The record sorts skip the lowest w bits of the tick field when that
+// saves a whole 8-bit pass (w = the bits of the last, partial digit).  The
+// sort is stable, so the records then stand in the order of (i, j, tick >>
+// w), each group of equal prefixes in emission order; k_window_fix sorts
+// each group by the whole key.  Records are unique (a pair's runs do not
+// overlap) and holes are all ones, so the result is the full sort's order.
+static int window_bits(int bits, int t_bits) {
+  const int passes = (bits + 7) / 8;
+  const int w = bits - 8 * (passes - 1);
+  return passes >= 2 && w <= t_bits ? w : 0;
+}
+
+// Each group of equal key >> shift (in slots [0, n), n a device count when
+// d_n is set) sorted by its first slot's thread: insertion sort, the groups
+// hold the runs of one pair within 2^w ticks.  Threads of the group's other
+// slots see the same prefixes whatever the order, so only first slots sort.
+__global__ void __launch_bounds__(256) k_window_fix(unsigned long long *keys, int64_t n,
+                                                    const unsigned long long *d_n, int shift) {
+  if (d_n && *d_n < (unsigned long long)n) n = (int64_t)*d_n;
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const unsigned long long k = keys[p];
+  if (k == kHole) return;
+  const unsigned long long g = k >> shift;
+  if (p > 0 && (keys[p - 1] >> shift) == g) return;
+  int64_t q = p + 1;
+  while (q < n && (keys[q] >> shift) == g) ++q;
+  for (int64_t x = p + 1; x < q; ++x) {
+    const unsigned long long v = keys[x];
+    int64_t y = x - 1;
+    while (y >= p && keys[y] > v) {
+      keys[y + 1] = keys[y];
+      --y;
+    }
+    keys[y + 1] = v;
+  }
+}
+
+static int window_fix(unsigned long long *keys, int64_t n, const unsigned long long *d_n,
+                      int shift, cudaStream_t st) {
+  if (n < 2) return SCD_OK;
+  k_window_fix<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(keys, n, d_n, shift);
+  note_launch();
+  return cudaGetLastError() == cudaSuccess ? SCD_OK : SCD_ERR_CUDA;
+}
+
 int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits) {
   cudaStream_t st = s->stream;
   // slots to sort (records plus holes) and records to keep
@@ -983,12 +1029,16 @@ int canonicalize(scd_scene *s, int raw_mode, int obj_bits, int t_bits) {
   const int lo = a.packed ? t_bits : 0, bits = 2 * obj_bits + t_bits;
   if (!s->d_out.ensure(n > 0 ? n : 1, st)) return SCD_ERR_OOM;
   a.out = s->d_out.p;
-  int rc = radix_sort_u64(s->d_starts.p, a.packed ? nullptr : s->d_rawval.p, ns, lo, bits + lo,
-                          s->sort_sc, st);
+  // packed starts and the ends: one pass fewer, then the window fix-up
+  const int w = a.packed && !raw_mode ? window_bits(bits, t_bits) : 0;
+  int rc = radix_sort_u64(s->d_starts.p, a.packed ? nullptr : s->d_rawval.p, ns, lo + w,
+                          bits + lo, s->sort_sc, st);
   if (rc) return rc;
+  if (w && (rc = window_fix(s->d_starts.p, ns, nullptr, lo + w, st))) return rc;
   if (!raw_mode && s->h_ctr.v_ends > 0) {
-    rc = radix_sort_u64(s->d_ends.p, nullptr, (int64_t)s->h_ctr.n_ends, bits, s->sort_sc, st);
+    rc = radix_sort_u64(s->d_ends.p, nullptr, (int64_t)s->h_ctr.n_ends, w, bits, s->sort_sc, st);
     if (rc) return rc;
+    if (w && (rc = window_fix(s->d_ends.p, (int64_t)s->h_ctr.n_ends, nullptr, w, st))) return rc;
   }
   a.n = n;
   a.n_ends = raw_mode ? 0 : s->h_ctr.v_ends;
@@ -1098,11 +1148,14 @@ int canonicalize_dev(scd_scene *s, int obj_bits, int t_bits) {
   UnpackArgs a = unpack_args(s, 0, obj_bits, t_bits);
   const int lo = a.packed ? t_bits : 0, bits = 2 * obj_bits + t_bits;
   DevCounters *c = s->d_ctr.p;
+  const int w = a.packed ? window_bits(bits, t_bits) : 0;
   int rc = radix_sort_u64_dev(s->d_starts.p, a.packed ? nullptr : s->d_rawval.p, cap,
-                              &c->n_starts, lo, bits + lo, s->sort_sc, st);
+                              &c->n_starts, lo + w, bits + lo, s->sort_sc, st);
   if (rc) return rc;
-  rc = radix_sort_u64_dev(s->d_ends.p, nullptr, cap, &c->n_ends, 0, bits, s->sort_sc, st);
+  if (w && (rc = window_fix(s->d_starts.p, cap, &c->n_starts, lo + w, st))) return rc;
+  rc = radix_sort_u64_dev(s->d_ends.p, nullptr, cap, &c->n_ends, w, bits, s->sort_sc, st);
   if (rc) return rc;
+  if (w && (rc = window_fix(s->d_ends.p, cap, &c->n_ends, w, st))) return rc;
   a.n = cap;
   a.d_n = &c->v_starts;
   a.n_ends = (unsigned long long)cap;
