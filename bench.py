@@ -571,7 +571,8 @@ def run_refine(args, world, wl="refine512"):
     r = {"times": times, "clocks": clk.summary(), "unit": "ms", "higher_is_better": False,
          "value": slowest_rank(sum(times), world) / (args.steps * world),
          "launches": launches, "n": len(els)}
-    r["refine"] = {"rounds": int(len(rb)), "intervals_per_round": [int(x) for x in rb],
+    r["refine"] = {"start_fraction": float(sc.tuning()["refine_start"]),
+                   "rounds": int(len(rb)), "intervals_per_round": [int(x) for x in rb],
                    "boxes": int(rb.sum()), "witnesses": int(len(w)),
                    "earliest_witness": [int(x) for x in w[0]] if len(w) else None,
                    "fixed_step_ms": statistics.mean(ftimes),
