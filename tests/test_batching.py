@@ -43,3 +43,16 @@ def test_arrival_order_is_the_greedy_packing():
         batching.plan_batches(costs, 0)
     with pytest.raises(ValueError):
         batching.plan_batches(costs, 10, "longest_first")
+
+
+def test_estimated_boxes_equals_the_oracle_segments():
+    # the planner's box estimate is the screen's segment count under P/100
+    # steps: per object ceil((T + 1) / k_i), k_i from the oracle's step rule
+    import oracle as O
+    import population as P
+    els = P.catalog_mixture(1000, seed=17)
+    for horizon in (3600.0, 86400.0):
+        T = int(horizon)
+        k = O.step_ticks(els, 1, 1.0, frac=100.0)
+        want = int(np.sum((T + 1 + k - 1) // k))
+        assert batching.estimated_boxes(els, horizon) == want
