@@ -195,3 +195,20 @@ def test_both_starts_give_the_same_witnesses_on_a_crowded_shell(mode):
     # starting from intervals of 64 ticks skips the rounds in which nearly
     # every box meets every other
     assert len(rb1) < len(rb0)
+
+
+@pytest.mark.parametrize("frac", [0.0, 16.0, 64.0, 256.0])
+def test_rounds_within_the_budget_of_the_longest_first_interval(frac):
+    """The rounds end within 2 + ceil(log2(L_max)) rounds, L_max the longest
+    first interval: the halvings down to single ticks, one round to decide
+    them and one for single ticks that wait for a longer interval (the GPU
+    queues exactly that many rounds)."""
+    els = P.uniform_leo(24, seed=101, radius_km=300.0)
+    els[5] = els[3]  # a pair that meets at every tick
+    T = 400
+    _, rb, _ = O.refine_discrete(els, T, 1.0, O.BOX_SPEED, frac)
+    lmax = max(O.refine_start_ticks(e, T, 1.0, frac) for e in els)
+    budget = 2 + math.ceil(math.log2(lmax))
+    assert 0 < len(rb) <= budget
+    # the identical pair keeps single ticks alive to the last halving
+    assert len(rb) >= 1 + math.ceil(math.log2(lmax))
